@@ -1,0 +1,142 @@
+"""The paper's own masking construction, in PyTorch FP64 on the CPU, for small traces.
+
+Used only to pin the oracle (``oracle/``): it reaches the robustness trace by a different
+route -- unroll the padded child trace into a (T+P) x T array (Sec. IV-B, Steps 1-3) or a
+(T+P) x T x K array for Until (Sec. IV-C), fill the masked-out entries with +-inf and
+reduce -- and torch autograd differentiates it, independently of the oracle's hand-written
+adjoints.  P = b pad rows, so every read at j >= T sees the pad (reading R2).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+BIG = math.inf
+
+
+def _pad(x, P, pad):
+    if P <= 0:
+        return x
+    if pad is None:
+        tail = x[-1:].expand(P)
+    else:
+        tail = torch.full((P,), float(pad), dtype=x.dtype)
+    return torch.cat([x, tail])
+
+
+def _window(a, b, T):
+    ia = int(a)
+    ib = T - 1 if math.isinf(b) else int(b)
+    return ia, max(ib, ia)
+
+
+def _smin(v, dim, tau, hard):
+    if hard:
+        return v.amin(dim=dim)
+    return -torch.logsumexp(-tau * v, dim=dim) / tau
+
+
+def _smax(v, dim, tau, hard):
+    if hard:
+        return v.amax(dim=dim)
+    return torch.logsumexp(tau * v, dim=dim) / tau
+
+
+def eventually_always(x, a, b, pad, op, hard, tau):
+    """Sec. IV-B: unroll to S[j, t] = s_pad[j], keep t+a <= j <= t+b, reduce columns."""
+    T = x.shape[0]
+    ia, ib = _window(a, b, T)
+    xp = _pad(x, ib, pad)
+    R = xp.shape[0]
+    S = xp[:, None].expand(R, T)
+    j = torch.arange(R)[:, None]
+    t = torch.arange(T)[None, :]
+    keep = (j >= t) & (j >= t + ia) & (j <= t + ib)     # M_subsig + M_time
+    if op == "eventually":
+        return _smax(S.masked_fill(~keep, -BIG), 0, tau, hard)
+    return _smin(S.masked_fill(~keep, BIG), 0, tau, hard)
+
+
+def until(p, q, a, b, pad, hard, tau):
+    """Sec. IV-C: 3-D unroll, S1 = stack of masked mins, S2 = min, S3 = max over i."""
+    T = p.shape[0]
+    ia, ib = _window(a, b, T)
+    pp, qp = _pad(p, ib, pad), _pad(q, ib, pad)
+    R = pp.shape[0]
+    K = ib - ia + 1
+    j = torch.arange(R)[:, None, None]
+    t = torch.arange(T)[None, :, None]
+    i = ia + torch.arange(K)[None, None, :]
+    keep_p = (j >= t) & (j <= t + i)          # Always_[0,i] phi
+    keep_q = j == t + i                       # Always_[i,i] psi
+    Sp = pp[:, None, None].expand(R, T, K).masked_fill(~keep_p, BIG)
+    Sq = qp[:, None, None].expand(R, T, K).masked_fill(~keep_q, BIG)
+    S1 = torch.stack([_smin(Sp, 0, tau, hard), _smin(Sq, 0, tau, hard)], dim=0)
+    S2 = _smin(S1, 0, tau, hard)
+    return _smax(S2, 1, tau, hard)
+
+
+def evaluate(f, x, hard=True, tau=1.0):
+    """Robustness trace of formula tuple ``f`` on one trace ``x`` [T, D] (torch fp64)."""
+    op = f[0]
+    if op == "pred":
+        # predicate parameters are float32 numbers (the libraries store them as float)
+        _, rel, w, c = f
+        w = [float(np.float32(v)) for v in w]
+        c = float(np.float32(c))
+        mu = x @ torch.tensor(w, dtype=x.dtype)
+        return mu - c if rel == ">" else c - mu
+    if op == "true":
+        return torch.full((x.shape[0],), BIG, dtype=x.dtype)
+    if op == "not":
+        return -evaluate(f[1], x, hard, tau)
+    if op in ("and", "or"):
+        u = torch.stack([evaluate(f[1], x, hard, tau), evaluate(f[2], x, hard, tau)])
+        return _smin(u, 0, tau, hard) if op == "and" else _smax(u, 0, tau, hard)
+    a, b, slot, pad = f[1]
+    if op in ("eventually", "always"):
+        return eventually_always(evaluate(f[2], x, hard, tau), a, b, pad, op, hard, tau)
+    if op == "until":
+        return until(evaluate(f[2], x, hard, tau), evaluate(f[3], x, hard, tau), a, b, pad, hard, tau)
+    raise ValueError(op)
+
+
+def boolean(f, x, t, T=None):
+    """Boolean semantics (Sec. III-B, Eq. "boolean") of ``f`` at sub-trajectory start ``t``
+    on a numpy trace ``x`` [T, D]; reads past the end follow the pad reading R2."""
+    T = x.shape[0] if T is None else T
+    op = f[0]
+    if op == "pred":
+        _, rel, w, c = f
+        w = [float(np.float32(v)) for v in w]
+        c = float(np.float32(c))
+        mu = float(sum(wd * float(xd) for wd, xd in zip(w, x[min(t, T - 1)])))
+        return mu > c if rel == ">" else mu < c
+    if op == "true":
+        return True
+    if op == "not":
+        return not boolean(f[1], x, t, T)
+    if op == "and":
+        return boolean(f[1], x, t, T) and boolean(f[2], x, t, T)
+    if op == "or":
+        return boolean(f[1], x, t, T) or boolean(f[2], x, t, T)
+    a, b, slot, pad = f[1]
+    ia, ib = _window(a, b, T)
+
+    def child(g, j):
+        if j < T:
+            return boolean(g, x, j, T)
+        if pad is None:
+            return boolean(g, x, T - 1, T)
+        return pad > 0
+
+    if op == "eventually":
+        return any(child(f[2], t + i) for i in range(ia, ib + 1))
+    if op == "always":
+        return all(child(f[2], t + i) for i in range(ia, ib + 1))
+    if op == "until":
+        return any(child(f[3], t + i) and all(child(f[2], t + k) for k in range(0, i + 1))
+                   for i in range(ia, ib + 1))
+    raise ValueError(op)
