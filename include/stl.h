@@ -1,0 +1,174 @@
+/*
+ * stl.h -- C ABI of libstl: batched, differentiable Signal Temporal Logic robustness on one
+ * GB300 (sm_103a), after STLCG++ (Kapoor, Mizuta, Kang, Leung; arXiv 2501.04194).
+ *
+ * What is computed.  For every trace b and every sample t the library returns the
+ * robustness trace rho(x_t, phi) of a formula phi (Sec. III-D, Definition 1), i.e. the
+ * quantitative semantics of Sec. III-B (Eq. "quantitative") applied to the sub-trajectory
+ * that starts at t, together with its gradient with respect to the signal and to per-trace
+ * interval bounds.  Operators:
+ *   predicates     mu(x_t) - c  or  c - mu(x_t), mu(x) = sum_d w_d x_d      (Eq. quantitative)
+ *   True           +inf                                                       (Eq. STL grammar)
+ *   not / and / or -rho, min, max; smooth mode: logsumexp min / max         (Sec. III-B, III-C)
+ *   eventually / always over [a,b]: max / min of the child over t+a..t+b    (Sec. IV-B)
+ *   until over [a,b]: max_i min(min_{k<=i} phi_{t+k}, psi_{t+i})            (Sec. IV-C)
+ *   eventually_sm / always_sm: the window weighted by the sigmoid mask
+ *     m_i = max(sigma(c(i-a)) - sigma(c(i-b)) - eps, 0), entering the logsumexp as a weight,
+ *     with gradients to a and b                                             (Sec. V, Eq. smooth mask)
+ * Reads past the end of a trace return the pad (Sec. IV-B Step 1): the last sample
+ * (STL_PAD_LAST, its gradient goes to sample T-1) or a constant (STL_PAD_CONST).  Smooth
+ * windows count pad reads with multiplicity, as the padded unroll does.  Hard-mode ties:
+ * windows select the earliest sample, and/or the left operand, until the earliest maximising
+ * offset, then the running minimum over the psi value, then the earliest minimiser.
+ *
+ * Layout.  Dense signals are float32 [B, T, D], row-major (sample-major inside a trace).
+ * Robustness traces and their gradients are float32 [B, T].  Per-trace bounds are float32
+ * [B, n_slots, 2] holding (a, b) in time steps.  All array arguments are DEVICE pointers.
+ *
+ * Ownership and execution.  The caller owns every pointer; the library never allocates or
+ * frees device memory on the call path (only stl_compile_set, which uploads the program
+ * table of a formula set, allocates).  Calls are asynchronous on the given cudaStream_t
+ * (passed as void*; NULL = the legacy default stream) and fully overwrite their outputs.
+ * Argument errors are detected on the host before anything is launched and returned as a
+ * negative stl_status; the message is available from stl_last_error() (thread-local).
+ * Errors found on the device (per-trace bounds outside the compiled caps) are recorded in a
+ * sticky per-device status word read by stl_get_device_status().  Inputs must be finite.
+ */
+#ifndef STL_H
+#define STL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define STL_API __attribute__((visibility("default")))
+#else
+#define STL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  STL_OK = 0,
+  STL_ERR_INVALID_ARG = -1,  /* a host-side argument check failed */
+  STL_ERR_UNSUPPORTED = -2,  /* valid but outside what this build supports (see message) */
+  STL_ERR_CUDA = -3,         /* a CUDA runtime call failed (see message) */
+  STL_ERR_WORKSPACE = -4,    /* workspace missing or smaller than stl_workspace_size() */
+  STL_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
+  STL_ERR_DEVICE_CHECK = -6  /* the device found invalid per-trace data (bounds) */
+} stl_status;
+
+typedef enum { STL_HARD = 0, STL_SMOOTH = 1 } stl_mode;
+
+typedef enum {
+  STL_OP_PRED_GT = 0,       /* mu(x) - c */
+  STL_OP_PRED_LT = 1,       /* c - mu(x) */
+  STL_OP_TRUE = 2,          /* +inf */
+  STL_OP_NOT = 3,
+  STL_OP_AND = 4,
+  STL_OP_OR = 5,
+  STL_OP_EVENTUALLY = 6,    /* integer window [a, b] */
+  STL_OP_ALWAYS = 7,
+  STL_OP_UNTIL = 8,         /* child0 U_[a,b] child1 */
+  STL_OP_EVENTUALLY_SM = 9, /* sigmoid-masked window, real a < b */
+  STL_OP_ALWAYS_SM = 10
+} stl_op;
+
+typedef enum { STL_PAD_LAST = 0, STL_PAD_CONST = 1 } stl_pad;
+
+/* One node of a formula.  Nodes are listed children-before-parents; the root is the last
+ * node and every other node has exactly one parent (a tree). */
+typedef struct {
+  int32_t op;          /* stl_op */
+  int32_t child0;      /* index of the (first) child, -1 if none */
+  int32_t child1;      /* second child of and/or/until, -1 otherwise */
+  int32_t bound_slot;  /* -1: the interval is (a, b) below; k >= 0: per-trace bounds[:, k, :],
+                          and (a, b) below are the largest values they may take (caps) */
+  float a, b;          /* interval in time steps; b = +INFINITY means the whole trace (b = T-1);
+                          integers for EVENTUALLY/ALWAYS/UNTIL */
+  int32_t pad_mode;    /* stl_pad, for temporal nodes */
+  float pad_value;     /* STL_PAD_CONST value */
+  int32_t pred_offset; /* predicates: weights are pred_weights[pred_offset .. pred_offset+D) */
+  float pred_c;        /* predicates: the constant c */
+} stl_node;
+
+/* Per-call semantics. */
+typedef struct {
+  int32_t mode;     /* stl_mode */
+  float tau;        /* smooth-mode temperature, > 0 (Sec. III-C) */
+  float mask_c;     /* smooth-mask sharpness c, > 0 (Eq. smooth mask) */
+  float mask_eps;   /* smooth-mask tolerance epsilon, in (0, 1) */
+} stl_params;
+
+/* Launch shape.  Zero fields mean "choose automatically" (the autotuner's cached choice if
+ * one was registered with stl_set_launch, else a heuristic). */
+typedef struct {
+  int32_t tile;      /* samples advanced per streaming step (multiple of 32) */
+  int32_t threads;   /* CTA size: 128, 256 or 512 */
+  int32_t segment;   /* samples per work item (a trace is split into segments) */
+  int32_t reserved;
+} stl_launch;
+
+typedef struct stl_program *stl_handle;
+typedef struct stl_program_set *stl_set_handle;
+
+/* Validate and compile a formula (host only; no device allocation).
+ *   nodes[n_nodes]      the tree, children first, root last
+ *   pred_weights[n_w]   predicate weights (float32), D per predicate
+ *   D                   signal dimension (1..16)
+ *   n_slots             columns of the per-trace bounds array (0 if unused)
+ * Returns STL_ERR_INVALID_ARG for a malformed tree (see stl_last_error()). */
+STL_API stl_status stl_compile(const stl_node *nodes, int32_t n_nodes, const float *pred_weights,
+                       int32_t n_w, int32_t D, int32_t n_slots, stl_handle *out);
+
+STL_API void stl_destroy(stl_handle h);
+
+/* Override (or, with all-zero fields, reset) the launch shape used for this handle. */
+STL_API stl_status stl_set_launch(stl_handle h, const stl_launch *launch);
+
+/* Launch shape the library would use for this call shape (after heuristics/overrides). */
+STL_API stl_status stl_get_launch(stl_handle h, int64_t B, int64_t T, const stl_params *p,
+                          int32_t backward, stl_launch *out);
+
+/* Bytes of device workspace that stl_robustness (backward = 0) or stl_robustness_backward
+ * (backward = 1) needs for B traces of length T; 0 when everything fits on chip. */
+STL_API stl_status stl_workspace_size(stl_handle h, int64_t B, int64_t T, const stl_params *p,
+                              int32_t backward, size_t *bytes);
+
+/* Robustness traces.
+ *   sig      [B, T, D] float32 device
+ *   bounds   [B, n_slots, 2] float32 device, or NULL when the formula uses no slot
+ *   out      [B, T] float32 device, overwritten
+ *   workspace / workspace_bytes: device scratch of at least stl_workspace_size() bytes
+ *   stream   cudaStream_t */
+STL_API stl_status stl_robustness(stl_handle h, const float *sig, int64_t B, int64_t T,
+                          const float *bounds, const stl_params *p, float *out,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+/* Gradient of sum_{b,t} grad_out[b,t] * rho[b,t] (reverse mode; the forward pass is
+ * recomputed on chip, no intermediate traces are stored).
+ *   grad_out     [B, T] float32 device
+ *   grad_sig     [B, T, D] float32 device, overwritten
+ *   grad_bounds  [B, n_slots, 2] float32 device or NULL, overwritten (nonzero only for the
+ *                sigmoid-masked operators in smooth mode) */
+STL_API stl_status stl_robustness_backward(stl_handle h, const float *sig, int64_t B, int64_t T,
+                                   const float *bounds, const stl_params *p,
+                                   const float *grad_out, float *grad_sig, float *grad_bounds,
+                                   void *workspace, size_t workspace_bytes, void *stream);
+
+/* Sticky device-side status of the current device (STL_OK or STL_ERR_DEVICE_CHECK);
+ * synchronises `stream`, then reads and clears the word. */
+STL_API stl_status stl_get_device_status(void *stream, int32_t *status);
+
+STL_API const char *stl_status_string(int32_t status);
+STL_API const char *stl_last_error(void);
+
+/* Library version string. */
+STL_API const char *stl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STL_H */

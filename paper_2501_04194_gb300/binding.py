@@ -1,0 +1,205 @@
+"""ctypes binding of libstl (include/stl.h): argument marshalling only.
+
+Every step of the robustness path runs in the CUDA library; this module converts a formula
+given as nested tuples (the format documented in ``Formula``) into the C ABI's node array,
+passes device pointers and the current CUDA stream, and raises on any non-zero status.  There
+is no CPU fallback: if ``libstl.so`` is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstl.so")
+
+STL_HARD, STL_SMOOTH = 0, 1
+OPS = {"pred>": 0, "pred<": 1, "true": 2, "not": 3, "and": 4, "or": 5, "eventually": 6, "always": 7,
+       "until": 8, "eventually_sm": 9, "always_sm": 10}
+STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported", -3: "CUDA error", -4: "workspace too small",
+          -5: "device wait timed out", -6: "device-side data check failed"}
+
+EXPORTED = ["stl_compile", "stl_destroy", "stl_set_launch", "stl_get_launch", "stl_workspace_size",
+            "stl_robustness", "stl_robustness_backward", "stl_get_device_status", "stl_status_string",
+            "stl_last_error", "stl_version"]
+
+
+class StlNode(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("child0", ctypes.c_int32), ("child1", ctypes.c_int32),
+                ("bound_slot", ctypes.c_int32), ("a", ctypes.c_float), ("b", ctypes.c_float),
+                ("pad_mode", ctypes.c_int32), ("pad_value", ctypes.c_float),
+                ("pred_offset", ctypes.c_int32), ("pred_c", ctypes.c_float)]
+
+
+class StlParams(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("tau", ctypes.c_float), ("mask_c", ctypes.c_float),
+                ("mask_eps", ctypes.c_float)]
+
+
+class StlLaunch(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("threads", ctypes.c_int32), ("segment", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class StlError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"libstl: {STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libstl.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with `python -m paper_2501_04194_gb300.build` "
+                          "(or __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    lib.stl_compile.argtypes = [ctypes.POINTER(StlNode), i32, vp, i32, i32, i32, ctypes.POINTER(vp)]
+    lib.stl_destroy.argtypes = [vp]
+    lib.stl_destroy.restype = None
+    lib.stl_set_launch.argtypes = [vp, ctypes.POINTER(StlLaunch)]
+    lib.stl_get_launch.argtypes = [vp, i64, i64, ctypes.POINTER(StlParams), i32, ctypes.POINTER(StlLaunch)]
+    lib.stl_workspace_size.argtypes = [vp, i64, i64, ctypes.POINTER(StlParams), i32, ctypes.POINTER(sz)]
+    lib.stl_robustness.argtypes = [vp, vp, i64, i64, vp, ctypes.POINTER(StlParams), vp, vp, sz, vp]
+    lib.stl_robustness_backward.argtypes = [vp, vp, i64, i64, vp, ctypes.POINTER(StlParams), vp, vp, vp, vp,
+                                            sz, vp]
+    lib.stl_get_device_status.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.stl_status_string.argtypes = [i32]
+    lib.stl_status_string.restype = ctypes.c_char_p
+    lib.stl_last_error.restype = ctypes.c_char_p
+    lib.stl_version.restype = ctypes.c_char_p
+    for name in ("stl_compile", "stl_set_launch", "stl_get_launch", "stl_workspace_size", "stl_robustness",
+                 "stl_robustness_backward", "stl_get_device_status"):
+        getattr(lib, name).restype = ctypes.c_int32
+    _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != 0:
+        raise StlError(status, load().stl_last_error().decode())
+
+
+def flatten(tree, D):
+    """Nested-tuple formula -> (list of StlNode children-first with the root last, weights, n_slots).
+
+    Tuple format (Sec. III-B grammar plus the derived and smoothed operators):
+      ("pred", ">" | "<", weights[D], c), ("true",), ("not", f), ("and", f, g), ("or", f, g),
+      ("eventually" | "always" | "eventually_sm" | "always_sm", I, f), ("until", I, f, g)
+    with I = (a, b, slot, pad): b may be inf; slot None or a bounds column; pad None (repeat the
+    last sample) or a constant."""
+    nodes, weights = [], []
+    n_slots = 0
+
+    def add(f):
+        nonlocal n_slots
+        op = f[0]
+        nd = StlNode(op=0, child0=-1, child1=-1, bound_slot=-1, a=0.0, b=0.0, pad_mode=0, pad_value=0.0,
+                     pred_offset=0, pred_c=0.0)
+        if op == "pred":
+            _, rel, w, c = f
+            if len(w) != D:
+                raise ValueError(f"predicate has {len(w)} weights, signal has D={D}")
+            nd.op = OPS["pred>" if rel == ">" else "pred<"]
+            nd.pred_offset = len(weights)
+            weights.extend(float(v) for v in w)
+            nd.pred_c = float(c)
+        elif op == "true":
+            nd.op = OPS["true"]
+        elif op == "not":
+            nd.child0 = add(f[1])
+            nd.op = OPS["not"]
+        elif op in ("and", "or"):
+            nd.child0 = add(f[1])
+            nd.child1 = add(f[2])
+            nd.op = OPS[op]
+        elif op in ("eventually", "always", "until", "eventually_sm", "always_sm"):
+            a, b, slot, pad = f[1]
+            nd.child0 = add(f[2])
+            if op == "until":
+                nd.child1 = add(f[3])
+            nd.op = OPS[op]
+            nd.a = float(a)
+            nd.b = math.inf if math.isinf(b) else float(b)
+            if slot is not None:
+                nd.bound_slot = int(slot)
+                n_slots = max(n_slots, int(slot) + 1)
+            if pad is not None:
+                nd.pad_mode, nd.pad_value = 1, float(pad)
+        else:
+            raise ValueError(f"unknown operator {op!r}")
+        nodes.append(nd)
+        return len(nodes) - 1
+
+    add(tree)
+    return nodes, weights, n_slots
+
+
+def params(mode=STL_HARD, tau=1.0, mask_c=5.0, mask_eps=1e-3) -> StlParams:
+    if isinstance(mode, str):
+        mode = {"hard": STL_HARD, "smooth": STL_SMOOTH}[mode]
+    return StlParams(int(mode), float(tau), float(mask_c), float(mask_eps))
+
+
+class Formula:
+    """A compiled formula (host handle of the C library)."""
+
+    def __init__(self, tree, D: int, n_slots: int | None = None):
+        lib = load()
+        nodes, weights, ns = flatten(tree, D)
+        self.tree, self.D = tree, D
+        self.n_slots = ns if n_slots is None else int(n_slots)
+        arr = (StlNode * len(nodes))(*nodes)
+        w = (ctypes.c_float * max(1, len(weights)))(*weights)
+        h = ctypes.c_void_p()
+        check(lib.stl_compile(arr, len(nodes), ctypes.cast(w, ctypes.c_void_p), len(weights), D, self.n_slots,
+                              ctypes.byref(h)))
+        self._h = h
+        self.n_nodes = len(nodes)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_launch(self, tile=0, threads=0, segment=0):
+        check(load().stl_set_launch(self._h, ctypes.byref(StlLaunch(tile, threads, segment, 0))))
+
+    def get_launch(self, B, T, p: StlParams, backward=False):
+        out = StlLaunch()
+        check(load().stl_get_launch(self._h, B, T, ctypes.byref(p), int(backward), ctypes.byref(out)))
+        return dict(tile=out.tile, threads=out.threads, segment=out.segment, grid=out.reserved)
+
+    def workspace_size(self, B, T, p: StlParams, backward=False) -> int:
+        n = ctypes.c_size_t()
+        check(load().stl_workspace_size(self._h, B, T, ctypes.byref(p), int(backward), ctypes.byref(n)))
+        return int(n.value)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.stl_destroy(h)
+            self._h = None
+
+
+def robustness_raw(f: Formula, sig_ptr, B, T, bounds_ptr, p: StlParams, out_ptr, ws_ptr, ws_bytes, stream):
+    check(load().stl_robustness(f.handle, sig_ptr, B, T, bounds_ptr, ctypes.byref(p), out_ptr, ws_ptr, ws_bytes,
+                                stream))
+
+
+def robustness_backward_raw(f: Formula, sig_ptr, B, T, bounds_ptr, p: StlParams, gout_ptr, gsig_ptr, gb_ptr,
+                            ws_ptr, ws_bytes, stream):
+    check(load().stl_robustness_backward(f.handle, sig_ptr, B, T, bounds_ptr, ctypes.byref(p), gout_ptr,
+                                         gsig_ptr, gb_ptr, ws_ptr, ws_bytes, stream))
+
+
+def device_status(stream=None) -> int:
+    st = ctypes.c_int32()
+    check(load().stl_get_device_status(stream, ctypes.byref(st)))
+    return int(st.value)

@@ -1,0 +1,488 @@
+// stl_capi.cu -- host side of libstl: formula validation, per-call ring layout, launch shape
+// selection and the extern "C" entry points declared in include/stl.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/stl.h"
+#include "stl_internal.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+stl_status fail(stl_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+stl_status cuda_fail(int e, const char *what) {
+  return fail(STL_ERR_CUDA, "%s: %s", what, cudaGetErrorString((cudaError_t)e));
+}
+
+bool is_temporal(int op) {
+  return op == STL_OP_EVENTUALLY || op == STL_OP_ALWAYS || op == STL_OP_UNTIL ||
+         op == STL_OP_EVENTUALLY_SM || op == STL_OP_ALWAYS_SM;
+}
+bool is_sm(int op) { return op == STL_OP_EVENTUALLY_SM || op == STL_OP_ALWAYS_SM; }
+bool is_pred(int op) { return op == STL_OP_PRED_GT || op == STL_OP_PRED_LT; }
+int arity(int op) {
+  switch (op) {
+    case STL_OP_PRED_GT: case STL_OP_PRED_LT: case STL_OP_TRUE: return 0;
+    case STL_OP_NOT: case STL_OP_EVENTUALLY: case STL_OP_ALWAYS:
+    case STL_OP_EVENTUALLY_SM: case STL_OP_ALWAYS_SM: return 1;
+    case STL_OP_AND: case STL_OP_OR: case STL_OP_UNTIL: return 2;
+    default: return -1;
+  }
+}
+
+int round_up(long long v, int m) { return (int)(((v + m - 1) / m) * m); }
+
+}  // namespace
+
+struct stl_program {
+  std::vector<stl_node> nodes;
+  std::vector<float> w;
+  int D = 0, n_slots = 0;
+  bool has_sm = false, has_until = false;
+  stl_launch launch{};
+};
+
+namespace {
+
+struct Plan {
+  KProgram P;
+  int threads = 256;
+  int grid = 1;
+  size_t ws_bytes = 0;
+};
+
+// largest window span (b) a node can reach for this call
+int window_hi(const stl_node &nd, long long T, const stl_params &p) {
+  if (is_sm(nd.op)) {
+    const double L = std::log((1.0 - p.mask_eps) / p.mask_eps) / p.mask_c;
+    return (int)std::ceil((double)nd.b + L) + 2;
+  }
+  if (std::isinf(nd.b)) return (int)(T - 1);
+  return (int)nd.b;
+}
+int window_lo(const stl_node &nd) {
+  if (nd.bound_slot >= 0 || is_sm(nd.op)) return 0;
+  return (int)nd.a;
+}
+
+// Compute node geometry, ring layout and launch shape for one call.
+stl_status make_plan(const stl_program *h, long long B, long long T, const stl_params &p, bool bwd, Plan &pl) {
+  KProgram &P = pl.P;
+  std::memset(&P, 0, sizeof P);
+  const int n = (int)h->nodes.size();
+  P.n = n;
+  P.D = h->D;
+  P.n_slots = h->n_slots;
+  P.mode = p.mode;
+  P.tau = p.mode == STL_SMOOTH ? p.tau : 1.f;
+  P.inv_tau = 1.f / P.tau;
+  P.mask_c = p.mask_c;
+  P.mask_eps = p.mask_eps;
+  P.bwd = bwd ? 1 : 0;
+  P.T = T;
+  P.B = B;
+  std::copy(h->w.begin(), h->w.end(), P.w);
+
+  // offsets: values run ahead by hi, adjoints complete behind by lo (root: 0, 0)
+  std::vector<int> lo(n, 0), hi(n, 0);
+  int maxK = 1;
+  for (int i = n - 1; i >= 0; --i) {
+    const stl_node &nd = h->nodes[i];
+    const int a0 = window_lo(nd), b1 = window_hi(nd, T, p);
+    if (is_temporal(nd.op)) maxK = std::max(maxK, b1 - a0 + 1);
+    if (nd.child0 >= 0) {
+      const int c = nd.child0;
+      if (is_temporal(nd.op)) {
+        lo[c] = lo[i] + (nd.op == STL_OP_UNTIL ? 0 : a0);
+        hi[c] = hi[i] + b1;
+      } else { lo[c] = lo[i]; hi[c] = hi[i]; }
+    }
+    if (nd.child1 >= 0) {
+      const int c = nd.child1;
+      if (nd.op == STL_OP_UNTIL) { lo[c] = lo[i] + a0; hi[c] = hi[i] + b1; }
+      else { lo[c] = lo[i]; hi[c] = hi[i]; }
+    }
+  }
+  int lp = 1 << 30;
+  for (int i = 0; i < n; ++i) if (is_pred(h->nodes[i].op)) lp = std::min(lp, lo[i]);
+  if (lp == (1 << 30)) lp = 0;
+  for (int i = 0; i < n; ++i) if (is_pred(h->nodes[i].op)) lo[i] = lp;
+  int hmax = 0;
+  for (int i = 0; i < n; ++i) hmax = std::max(hmax, hi[i]);
+  P.hmax = hmax;
+  P.lp = lp;
+
+  int sms = 0, max_smem = 0;
+  int e = stl_num_sms(&sms);
+  if (e) return cuda_fail(e, "cudaDeviceGetAttribute(multiprocessors)");
+  e = stl_max_smem_optin(&max_smem);
+  if (e) return cuda_fail(e, "cudaDeviceGetAttribute(max shared memory)");
+
+  int threads = h->launch.threads ? h->launch.threads : 256;
+  int tile = h->launch.tile ? h->launch.tile : 2048;
+  tile = std::min(tile, round_up(T, 32));
+  tile = std::max(32, round_up(tile, 32));
+  const int win_r = maxK >= 64 ? 16 : 8;
+  P.win_r = win_r;
+
+  auto padded = [](int cap) { return cap + cap / 32 + 1; };
+  auto layout = [&](int tl, std::vector<int> &space_out, int &smem_words, int &gwords) {
+    // scratch for window run aggregates: (threads + maxK/R + 2) entries of up to 16 bytes
+    const int scratch_words = (threads + maxK / win_r + 4) * 4;
+    const int rt_words = (int)((n * sizeof(NodeRt) + 15) / 16 * 4);
+    std::vector<int> words(n);
+    for (int i = 0; i < n; ++i) {
+      const stl_node &nd = h->nodes[i];
+      const int cap = round_up((long long)tl + hi[i] - lo[i], 32);
+      int nrings = 1;
+      if (bwd) {
+        nrings += 1;
+        if (p.mode == STL_HARD && is_temporal(nd.op)) nrings += 1;
+      }
+      words[i] = nrings * padded(cap);
+    }
+    space_out.assign(n, 0);
+    smem_words = scratch_words + rt_words;
+    for (int i = 0; i < n; ++i) smem_words += words[i];
+    gwords = 0;
+    // spill the largest rings to the global workspace until the arena fits
+    while ((long long)smem_words * 4 > max_smem) {
+      int best = -1;
+      for (int i = 0; i < n; ++i)
+        if (space_out[i] == 0 && (best < 0 || words[i] > words[best])) best = i;
+      if (best < 0) break;
+      space_out[best] = 1;
+      smem_words -= words[best];
+      gwords += words[best];
+    }
+    return (long long)smem_words * 4 <= max_smem;
+  };
+  std::vector<int> space;
+  int smem_words = 0, gwords = 0;
+  // shrink the tile while rings would have to leave shared memory
+  for (;;) {
+    bool ok = layout(tile, space, smem_words, gwords);
+    if (!ok) return fail(STL_ERR_UNSUPPORTED, "formula scratch does not fit in shared memory");
+    if (gwords == 0 || tile <= 256) break;
+    tile = std::max(256, round_up(tile / 2, 32));
+  }
+  P.tile = tile;
+
+  // assign offsets
+  int off_s = 0, off_g = 0;
+  for (int i = 0; i < n; ++i) {
+    const stl_node &nd = h->nodes[i];
+    KNode &k = P.nd[i];
+    k.op = nd.op;
+    k.c0 = nd.child0;
+    k.c1 = nd.child1;
+    k.slot = nd.bound_slot;
+    k.parent = -1;
+    k.a = nd.a;
+    k.b = nd.b;
+    k.pad_const = nd.pad_mode == STL_PAD_CONST;
+    k.pad_value = nd.pad_value;
+    k.w_off = nd.pred_offset;
+    k.pc = nd.pred_c;
+    k.lo = lo[i];
+    k.hi = hi[i];
+    k.cap = round_up((long long)tile + hi[i] - lo[i], 32);
+    k.space = space[i];
+    int &off = space[i] ? off_g : off_s;
+    const int pw = padded(k.cap);
+    k.val_off = off; off += pw;
+    k.adj_off = -1;
+    k.aux_off = -1;
+    if (bwd) {
+      k.adj_off = off; off += pw;
+      if (p.mode == STL_HARD && is_temporal(nd.op)) { k.aux_off = off; off += pw; }
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    if (P.nd[i].c0 >= 0) P.nd[P.nd[i].c0].parent = i;
+    if (P.nd[i].c1 >= 0) P.nd[P.nd[i].c1].parent = i;
+  }
+  const int scratch_words = (threads + maxK / win_r + 4) * 4;
+  P.scratch_off = round_up(off_s, 4);
+  P.scratch_words = scratch_words;
+  P.rt_off = P.scratch_off + scratch_words;
+  P.smem_words = P.rt_off + (int)((n * sizeof(NodeRt) + 15) / 16 * 4);
+  P.gwords = round_up(off_g, 64);
+
+  // launch shape
+  int bps = 0;
+  e = stl_blocks_per_sm(threads, P.smem_words * 4, &bps);
+  if (e) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (bps < 1) return fail(STL_ERR_UNSUPPORTED, "kernel does not fit on an SM (%d B shared)", P.smem_words * 4);
+  const long long slots = (long long)sms * bps;
+  int segs = 1;
+  if (h->launch.segment > 0) {
+    segs = (int)((T + h->launch.segment - 1) / h->launch.segment);
+  } else if (B < 2 * slots) {
+    // split traces so that there are about two items per resident CTA, while keeping
+    // segments long compared with the backward warm-up
+    const long long want = (2 * slots + B - 1) / B;
+    const long long max_by_len = std::max(1LL, T / std::max(4LL * (hmax + tile), (long long)tile));
+    segs = (int)std::max(1LL, std::min(want, max_by_len));
+  }
+  P.seg = (int)((T + segs - 1) / segs);
+  P.segs_per_trace = (int)((T + P.seg - 1) / P.seg);
+  P.n_items = B * P.segs_per_trace;
+  pl.grid = (int)std::max(1LL, std::min(P.n_items, slots));
+  pl.threads = threads;
+
+  // smooth-until per-thread arrays
+  size_t ws_words = (size_t)P.gwords * pl.grid;
+  P.ut_len = 0;
+  P.ut_off = (long long)ws_words;
+  if (bwd && p.mode == STL_SMOOTH) {
+    int ut = 0;
+    for (int i = 0; i < n; ++i)
+      if (h->nodes[i].op == STL_OP_UNTIL) ut = std::max(ut, window_hi(h->nodes[i], T, p) + 1);
+    P.ut_len = ut;
+    ws_words += (size_t)ut * pl.grid * threads;
+  }
+  pl.ws_bytes = ws_words * 4;
+  return STL_OK;
+}
+
+stl_status check_params(const stl_program *h, const stl_params *p) {
+  if (!p) return fail(STL_ERR_INVALID_ARG, "params is NULL");
+  if (p->mode != STL_HARD && p->mode != STL_SMOOTH) return fail(STL_ERR_INVALID_ARG, "mode must be STL_HARD or STL_SMOOTH");
+  if (p->mode == STL_SMOOTH && !(p->tau > 0.f && std::isfinite(p->tau)))
+    return fail(STL_ERR_INVALID_ARG, "tau must be finite and > 0 in smooth mode");
+  if (h->has_sm) {
+    if (!(p->mask_c > 0.f && std::isfinite(p->mask_c))) return fail(STL_ERR_INVALID_ARG, "mask_c must be finite and > 0");
+    if (!(p->mask_eps > 0.f && p->mask_eps < 1.f)) return fail(STL_ERR_INVALID_ARG, "mask_eps must be in (0, 1)");
+  }
+  return STL_OK;
+}
+
+stl_status check_call(const stl_program *h, const float *sig, long long B, long long T, const float *bounds,
+                      const stl_params *p) {
+  if (!h) return fail(STL_ERR_INVALID_ARG, "handle is NULL");
+  if (B < 0) return fail(STL_ERR_INVALID_ARG, "B must be >= 0");
+  if (T < 1 || T > (1LL << 30)) return fail(STL_ERR_INVALID_ARG, "T must be in [1, 2^30]");
+  if (B > 0 && !sig) return fail(STL_ERR_INVALID_ARG, "signal pointer is NULL");
+  if (h->n_slots > 0 && B > 0 && !bounds) return fail(STL_ERR_INVALID_ARG, "formula uses per-trace bounds but bounds is NULL");
+  return check_params(h, p);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *stl_version(void) { return "libstl 0.1 (sm_103a)"; }
+
+const char *stl_status_string(int32_t s) {
+  switch (s) {
+    case STL_OK: return "ok";
+    case STL_ERR_INVALID_ARG: return "invalid argument";
+    case STL_ERR_UNSUPPORTED: return "unsupported";
+    case STL_ERR_CUDA: return "CUDA error";
+    case STL_ERR_WORKSPACE: return "workspace too small";
+    case STL_ERR_TIMEOUT: return "device wait timed out";
+    case STL_ERR_DEVICE_CHECK: return "device-side data check failed";
+    default: return "unknown status";
+  }
+}
+
+const char *stl_last_error(void) { return g_err.c_str(); }
+
+stl_status stl_compile(const stl_node *nodes, int32_t n_nodes, const float *pred_weights, int32_t n_w,
+                       int32_t D, int32_t n_slots, stl_handle *out) {
+  if (!out) return fail(STL_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!nodes || n_nodes < 1 || n_nodes > STL_MAX_NODES)
+    return fail(STL_ERR_INVALID_ARG, "n_nodes must be in [1, %d]", STL_MAX_NODES);
+  if (D < 1 || D > STL_MAX_D) return fail(STL_ERR_INVALID_ARG, "D must be in [1, %d]", STL_MAX_D);
+  if (n_w < 0 || n_w > STL_MAX_WEIGHTS || (n_w > 0 && !pred_weights))
+    return fail(STL_ERR_INVALID_ARG, "pred_weights: need 0 <= n_w <= %d and a pointer", STL_MAX_WEIGHTS);
+  if (n_slots < 0 || n_slots > 64) return fail(STL_ERR_INVALID_ARG, "n_slots must be in [0, 64]");
+  for (int i = 0; i < n_w; ++i)
+    if (!std::isfinite(pred_weights[i])) return fail(STL_ERR_INVALID_ARG, "predicate weight %d is not finite", i);
+  std::vector<int> parents(n_nodes, 0);
+  bool has_sm = false, has_until = false;
+  for (int i = 0; i < n_nodes; ++i) {
+    const stl_node &nd = nodes[i];
+    const int ar = arity(nd.op);
+    if (ar < 0) return fail(STL_ERR_INVALID_ARG, "node %d: unknown op %d", i, nd.op);
+    const int kids[2] = {nd.child0, nd.child1};
+    for (int k = 0; k < 2; ++k) {
+      if (k < ar) {
+        if (kids[k] < 0 || kids[k] >= i)
+          return fail(STL_ERR_INVALID_ARG, "node %d: child %d must be an earlier node", i, k);
+        parents[kids[k]]++;
+      } else if (kids[k] != -1) {
+        return fail(STL_ERR_INVALID_ARG, "node %d: unused child %d must be -1", i, k);
+      }
+    }
+    if (is_pred(nd.op)) {
+      if (nd.pred_offset < 0 || nd.pred_offset + D > n_w)
+        return fail(STL_ERR_INVALID_ARG, "node %d: predicate weights out of range", i);
+      if (!std::isfinite(nd.pred_c)) return fail(STL_ERR_INVALID_ARG, "node %d: predicate constant not finite", i);
+    }
+    if (is_temporal(nd.op)) {
+      if (nd.bound_slot < -1 || nd.bound_slot >= n_slots)
+        return fail(STL_ERR_INVALID_ARG, "node %d: bound_slot out of range", i);
+      if (!(nd.a >= 0.f) || !(nd.b >= nd.a) || std::isnan(nd.b))
+        return fail(STL_ERR_INVALID_ARG, "node %d: need 0 <= a <= b", i);
+      if (is_sm(nd.op)) {
+        if (std::isinf(nd.b)) return fail(STL_ERR_INVALID_ARG, "node %d: smooth-mask bounds must be finite", i);
+        has_sm = true;
+      } else {
+        if (nd.a != std::floor(nd.a) || (!std::isinf(nd.b) && nd.b != std::floor(nd.b)))
+          return fail(STL_ERR_INVALID_ARG, "node %d: interval bounds must be integers", i);
+      }
+      if (!std::isinf(nd.b) && nd.b > (float)(1 << 24)) return fail(STL_ERR_INVALID_ARG, "node %d: b too large", i);
+      if (nd.pad_mode != STL_PAD_LAST && nd.pad_mode != STL_PAD_CONST)
+        return fail(STL_ERR_INVALID_ARG, "node %d: pad_mode must be STL_PAD_LAST or STL_PAD_CONST", i);
+      if (nd.pad_mode == STL_PAD_CONST && !std::isfinite(nd.pad_value))
+        return fail(STL_ERR_INVALID_ARG, "node %d: pad_value not finite", i);
+      if (nd.op == STL_OP_UNTIL) has_until = true;
+    }
+  }
+  for (int i = 0; i < n_nodes - 1; ++i)
+    if (parents[i] != 1) return fail(STL_ERR_INVALID_ARG, "node %d must have exactly one parent (tree, root last)", i);
+  if (parents[n_nodes - 1] != 0) return fail(STL_ERR_INVALID_ARG, "the root (last node) cannot have a parent");
+  stl_program *h = new (std::nothrow) stl_program;
+  if (!h) return fail(STL_ERR_INVALID_ARG, "out of host memory");
+  h->nodes.assign(nodes, nodes + n_nodes);
+  h->w.assign(pred_weights, pred_weights + n_w);
+  h->D = D;
+  h->n_slots = n_slots;
+  h->has_sm = has_sm;
+  h->has_until = has_until;
+  *out = h;
+  return STL_OK;
+}
+
+void stl_destroy(stl_handle h) { delete h; }
+
+stl_status stl_set_launch(stl_handle h, const stl_launch *launch) {
+  if (!h || !launch) return fail(STL_ERR_INVALID_ARG, "NULL argument");
+  if (launch->threads && launch->threads != 128 && launch->threads != 256 && launch->threads != 512)
+    return fail(STL_ERR_INVALID_ARG, "threads must be 0, 128, 256 or 512");
+  if (launch->tile < 0 || (launch->tile && launch->tile % 32) || launch->segment < 0)
+    return fail(STL_ERR_INVALID_ARG, "tile must be a non-negative multiple of 32; segment >= 0");
+  h->launch = *launch;
+  return STL_OK;
+}
+
+stl_status stl_get_launch(stl_handle h, int64_t B, int64_t T, const stl_params *p, int32_t backward,
+                          stl_launch *out) {
+  if (!out) return fail(STL_ERR_INVALID_ARG, "out is NULL");
+  stl_status s = check_call(h, (const float *)1, B, T, (const float *)1, p);
+  if (s) return s;
+  Plan pl;
+  s = make_plan(h, B, T, *p, backward != 0, pl);
+  if (s) return s;
+  out->tile = pl.P.tile;
+  out->threads = pl.threads;
+  out->segment = pl.P.seg;
+  out->reserved = pl.grid;
+  return STL_OK;
+}
+
+stl_status stl_workspace_size(stl_handle h, int64_t B, int64_t T, const stl_params *p, int32_t backward,
+                              size_t *bytes) {
+  if (!bytes) return fail(STL_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = 0;
+  stl_status s = check_call(h, (const float *)1, B, T, (const float *)1, p);
+  if (s) return s;
+  if (B == 0) return STL_OK;
+  Plan pl;
+  s = make_plan(h, B, T, *p, backward != 0, pl);
+  if (s) return s;
+  *bytes = pl.ws_bytes;
+  return STL_OK;
+}
+
+stl_status stl_robustness(stl_handle h, const float *sig, int64_t B, int64_t T, const float *bounds,
+                          const stl_params *p, float *out, void *workspace, size_t workspace_bytes,
+                          void *stream) {
+  stl_status s = check_call(h, sig, B, T, bounds, p);
+  if (s) return s;
+  if (B > 0 && !out) return fail(STL_ERR_INVALID_ARG, "out is NULL");
+  if (B == 0) return STL_OK;
+  Plan pl;
+  s = make_plan(h, B, T, *p, false, pl);
+  if (s) return s;
+  if (pl.ws_bytes > 0 && (!workspace || workspace_bytes < pl.ws_bytes))
+    return fail(STL_ERR_WORKSPACE, "workspace of %zu bytes needed", pl.ws_bytes);
+  LaunchArgs A{};
+  int e0 = stl_status_ptr(&A.status);
+  if (e0) return cuda_fail(e0, "cudaGetSymbolAddress(status)");
+  A.sig = sig;
+  A.bounds = h->n_slots ? bounds : nullptr;
+  A.out = out;
+  A.ws = (float *)workspace;
+  A.grid = pl.grid;
+  A.threads = pl.threads;
+  A.stream = stream;
+  int e = stl_launch_main(pl.P, A);
+  if (e) return cuda_fail(e, "robustness kernel launch");
+  return STL_OK;
+}
+
+stl_status stl_robustness_backward(stl_handle h, const float *sig, int64_t B, int64_t T, const float *bounds,
+                                   const stl_params *p, const float *grad_out, float *grad_sig,
+                                   float *grad_bounds, void *workspace, size_t workspace_bytes, void *stream) {
+  stl_status s = check_call(h, sig, B, T, bounds, p);
+  if (s) return s;
+  if (B > 0 && (!grad_out || !grad_sig)) return fail(STL_ERR_INVALID_ARG, "grad_out / grad_sig is NULL");
+  if (B == 0) return STL_OK;
+  Plan pl;
+  s = make_plan(h, B, T, *p, true, pl);
+  if (s) return s;
+  if (pl.ws_bytes > 0 && (!workspace || workspace_bytes < pl.ws_bytes))
+    return fail(STL_ERR_WORKSPACE, "workspace of %zu bytes needed", pl.ws_bytes);
+  if (grad_bounds && h->n_slots > 0) {
+    cudaError_t e = cudaMemsetAsync(grad_bounds, 0, (size_t)B * h->n_slots * 2 * sizeof(float), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail((int)e, "cudaMemsetAsync(grad_bounds)");
+  }
+  LaunchArgs A{};
+  int e0 = stl_status_ptr(&A.status);
+  if (e0) return cuda_fail(e0, "cudaGetSymbolAddress(status)");
+  A.sig = sig;
+  A.bounds = h->n_slots ? bounds : nullptr;
+  A.gout = grad_out;
+  A.gsig = grad_sig;
+  A.gbounds = h->n_slots ? grad_bounds : nullptr;
+  A.ws = (float *)workspace;
+  A.grid = pl.grid;
+  A.threads = pl.threads;
+  A.stream = stream;
+  int e = stl_launch_main(pl.P, A);
+  if (e) return cuda_fail(e, "robustness backward kernel launch");
+  return STL_OK;
+}
+
+stl_status stl_get_device_status(void *stream, int32_t *status) {
+  if (!status) return fail(STL_ERR_INVALID_ARG, "status is NULL");
+  int st = 0;
+  int e = stl_read_clear_status(stream, &st);
+  if (e) return cuda_fail(e, "reading the device status");
+  *status = st ? STL_ERR_DEVICE_CHECK : STL_OK;
+  return STL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal program description of libstl, shared by the host-side compiler (stl_capi.cu)
+// and the device interpreter (stl_kernels.cu).  A compiled formula is passed BY VALUE as a
+// __grid_constant__ kernel parameter, so a launch needs no device allocation for it.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#define STL_MAX_NODES 32
+#define STL_MAX_WEIGHTS 256
+#define STL_MAX_D 16
+
+// Node layout after compilation (per launch: the ring geometry depends on tile and bounds).
+struct KNode {
+  int op, c0, c1, slot, parent;
+  float a, b;          // static interval, or the caps of a per-trace slot (b may be +inf)
+  int pad_const;       // 0: reads past T-1 repeat the last sample; 1: constant pad_value
+  float pad_value;
+  int w_off;           // predicate weights offset into KProgram::w
+  float pc;            // predicate constant
+  int lo, hi;          // live offsets relative to the root step [t0, t1): [t0+lo, t1+hi)
+  int cap;             // ring capacity in samples (>= tile + hi - lo, multiple of 32)
+  int val_off;         // word offsets of the rings (shared arena or per-CTA global slice)
+  int adj_off;         // -1 if the node keeps no adjoint ring
+  int aux_off;         // -1 if the node keeps no selected-source ring
+  int space;           // 0: shared memory, 1: global workspace
+};
+
+struct KProgram {
+  int n;               // nodes, children first, root = n-1
+  int D;
+  int n_slots;
+  int mode;            // 0 hard, 1 smooth
+  float tau, inv_tau, mask_c, mask_eps;
+  int bwd;             // 1: backward launch
+  int tile;            // samples per streaming step
+  int seg;             // samples per work item
+  int segs_per_trace;
+  long long n_items;
+  long long T;         // samples per trace
+  long long B;
+  int hmax;            // max hi over nodes (backward warm-up)
+  int lp;              // common adjoint offset of the predicates
+  int smem_words;      // dynamic shared memory words: rings + scratch + node table
+  int scratch_off;     // word offset of the window scratch in shared memory
+  int scratch_words;
+  int rt_off;          // word offset of the per-node runtime table
+  int gwords;          // global ring words per CTA
+  long long ut_off;    // word offset of the smooth-until per-thread arrays in the workspace
+  int ut_len;          // their length (max taps)
+  int win_r;           // samples per thread-run in the window reductions (8 or 16)
+  float w[STL_MAX_WEIGHTS];
+  KNode nd[STL_MAX_NODES];
+};
+
+// Per-node runtime state, one per node in shared memory.
+struct NodeRt {
+  float *val;
+  float *adj;
+  int *aux;
+  int ia, ib;          // integer window (or smooth-mask support) for this trace
+  float fa, fb;        // smooth-mask real bounds for this trace
+  int lo, hi, cap;
+  int base;            // ring base of the current step
+  float lastval;       // value at sample T-1 (pad reads)
+  int lastaux;         // recorded source at sample T-1
+  float padadj;        // adjoint accumulated for sample T-1
+  float ga, gb;        // smooth-mask bound-gradient accumulators
+};
+
+// Host-side launch entry points (stl_kernels.cu).
+struct LaunchArgs {
+  const float *sig;
+  const float *bounds;
+  const float *gout;
+  float *out;
+  float *gsig;
+  float *gbounds;
+  float *ws;
+  int *status;         // device status word (sticky error flag)
+  int grid;
+  int threads;
+  void *stream;
+};
+int stl_launch_main(const KProgram &P, const LaunchArgs &A);   // returns a cudaError_t
+int stl_max_smem_optin(int *bytes);
+int stl_blocks_per_sm(int threads, int smem_bytes, int *blocks);
+int stl_num_sms(int *sms);
+int stl_read_clear_status(void *stream, int *status);
+int stl_status_ptr(int **ptr);

@@ -1,0 +1,86 @@
+"""PyTorch front end: device tensors in, device tensors out, autograd through the CUDA adjoint.
+
+Torch is used only to allocate outputs/workspace on the current device and to name the
+current stream; the computation is the C library's.
+"""
+from __future__ import annotations
+
+import torch
+
+from .binding import Formula, StlParams, params as make_params, robustness_backward_raw, robustness_raw
+
+
+def _check_sig(f: Formula, sig: torch.Tensor):
+    if not sig.is_cuda:
+        raise ValueError("signal must be a CUDA tensor (libstl has no CPU path)")
+    if sig.dtype != torch.float32 or sig.dim() != 3 or sig.shape[2] != f.D:
+        raise ValueError(f"signal must be float32 [B, T, {f.D}]")
+    return sig.contiguous()
+
+
+def _bounds(f: Formula, bounds, sig):
+    if f.n_slots == 0:
+        return None
+    if bounds is None:
+        raise ValueError("formula uses per-trace bounds; pass bounds [B, n_slots, 2]")
+    b = bounds.to(device=sig.device, dtype=torch.float32).contiguous()
+    if b.shape != (sig.shape[0], f.n_slots, 2):
+        raise ValueError(f"bounds must be [B, {f.n_slots}, 2]")
+    return b
+
+
+def _ws(f, B, T, p, backward, device):
+    n = f.workspace_size(B, T, p, backward)
+    if n == 0:
+        return None, 0
+    return torch.empty(n // 4 + 1, dtype=torch.float32, device=device), n
+
+
+def robustness(f: Formula, sig: torch.Tensor, bounds=None, p: StlParams | None = None) -> torch.Tensor:
+    """Robustness trace [B, T] of formula ``f`` for signals ``sig`` [B, T, D] (no autograd)."""
+    p = p or make_params()
+    sig = _check_sig(f, sig)
+    B, T, _ = sig.shape
+    b = _bounds(f, bounds, sig)
+    out = torch.empty((B, T), dtype=torch.float32, device=sig.device)
+    ws, nws = _ws(f, B, T, p, False, sig.device)
+    stream = torch.cuda.current_stream(sig.device).cuda_stream
+    robustness_raw(f, sig.data_ptr(), B, T, None if b is None else b.data_ptr(), p, out.data_ptr(),
+                   None if ws is None else ws.data_ptr(), nws, stream)
+    return out
+
+
+def robustness_backward(f: Formula, sig: torch.Tensor, grad_out: torch.Tensor, bounds=None,
+                        p: StlParams | None = None):
+    """(grad_sig [B,T,D], grad_bounds [B,n_slots,2] or None) of sum(grad_out * rho)."""
+    p = p or make_params()
+    sig = _check_sig(f, sig)
+    B, T, D = sig.shape
+    b = _bounds(f, bounds, sig)
+    g = grad_out.to(device=sig.device, dtype=torch.float32).contiguous()
+    gsig = torch.empty((B, T, D), dtype=torch.float32, device=sig.device)
+    gb = torch.empty((B, f.n_slots, 2), dtype=torch.float32, device=sig.device) if f.n_slots else None
+    ws, nws = _ws(f, B, T, p, True, sig.device)
+    stream = torch.cuda.current_stream(sig.device).cuda_stream
+    robustness_backward_raw(f, sig.data_ptr(), B, T, None if b is None else b.data_ptr(), p, g.data_ptr(),
+                            gsig.data_ptr(), None if gb is None else gb.data_ptr(),
+                            None if ws is None else ws.data_ptr(), nws, stream)
+    return gsig, gb
+
+
+class STLRobustness(torch.autograd.Function):
+    """rho = STLRobustness.apply(formula, sig, bounds, params); differentiable w.r.t. sig and
+    bounds.  The backward recomputes the forward on chip (no stored intermediates)."""
+
+    @staticmethod
+    def forward(ctx, f: Formula, sig, bounds, p):
+        ctx.f, ctx.p = f, p
+        ctx.save_for_backward(sig, bounds if bounds is not None else torch.empty(0, device=sig.device))
+        ctx.has_bounds = bounds is not None
+        return robustness(f, sig, bounds, p)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        sig, bounds = ctx.saved_tensors
+        gsig, gb = robustness_backward(ctx.f, sig, grad_out, bounds if ctx.has_bounds else None, ctx.p)
+        return None, gsig, (gb if ctx.has_bounds else None), None

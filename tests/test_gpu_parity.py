@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Bars (per trace, relative to the trace's largest |reference| value):
+  hard-mode robustness   bit-exact float32 (selections; predicates without FMA)
+  smooth robustness      1e-5
+  gradients              1e-4
+Sizes span several streaming steps (tile forced to 256) and ragged tails, traces split into
+segments (backward warm-up), and the degenerate cases: T = 1, windows longer than the trace,
+constant pads, True, a = b, b = inf.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+VAL_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def stl():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2501_04194_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def per_trace_err(got, ref):
+    B = ref.shape[0]
+    g = np.asarray(got, dtype=np.float64).reshape(B, -1)
+    r = np.asarray(ref, dtype=np.float64).reshape(B, -1)
+    fin = np.isfinite(r)
+    assert np.array_equal(fin, np.isfinite(g)) and np.array_equal(g[~fin], r[~fin])
+    scale = np.where(fin, np.abs(r), 0).max(axis=1, keepdims=True)
+    scale = np.maximum(scale, 1e-30)
+    d = np.where(fin, np.abs(g - r), 0) / scale
+    return d.max()
+
+
+def run(stl, tree, sig, bounds=None, mode="hard", tau=1.0, mask_c=5.0, mask_eps=1e-3, launch=None, gout=None):
+    D = sig.shape[2]
+    f = stl.Formula(tree, D=D, n_slots=None if bounds is None else bounds.shape[1])
+    if launch:
+        f.set_launch(**launch)
+    p = stl.params(mode, tau=tau, mask_c=mask_c, mask_eps=mask_eps)
+    x = torch.from_numpy(np.ascontiguousarray(sig)).cuda()
+    bt = None if bounds is None else torch.from_numpy(bounds).cuda()
+    rho = stl.robustness(f, x, bt, p).cpu().numpy()
+    gs = gb = None
+    if gout is not None:
+        g = torch.from_numpy(gout.astype(np.float32)).cuda()
+        gs, gb = stl.robustness_backward(f, x, g, bt, p)
+        gs = gs.cpu().numpy()
+        gb = None if gb is None else gb.cpu().numpy()
+    torch.cuda.synchronize()
+    return rho, gs, gb
+
+
+def check(stl, tree, sig, bounds=None, mode="hard", tau=1.0, mask_c=5.0, mask_eps=1e-3, launch=None, seed=0,
+          grad=True):
+    rng = np.random.default_rng(seed)
+    B, T, _ = sig.shape
+    gout = rng.normal(size=(B, T)).astype(np.float32) if grad else None
+    rho, gs, gb = run(stl, tree, sig, bounds, mode, tau, mask_c, mask_eps, launch, gout)
+    om = oracle.HARD if mode == "hard" else oracle.SMOOTH
+    ref = oracle.robustness(tree, sig, bounds=bounds, mode=om, tau=tau, mask_c=mask_c, mask_eps=mask_eps)
+    if mode == "hard":
+        np.testing.assert_array_equal(rho, ref.astype(np.float32))
+    else:
+        assert per_trace_err(rho, ref) <= VAL_TOL
+    if grad:
+        gref, gbref = oracle.robustness_grad(tree, sig, gout.astype(np.float64), bounds=bounds, mode=om, tau=tau,
+                                             mask_c=mask_c, mask_eps=mask_eps)
+        assert per_trace_err(gs, gref) <= GRAD_TOL
+        if gbref is not None and mode == "smooth":
+            assert per_trace_err(gb, gbref) <= GRAD_TOL
+        elif gb is not None:
+            assert np.all(gb == 0)
+
+
+# ------------------------------------------------------------------ configs
+def test_config0(stl):
+    sig = W.config0_inputs()
+    check(stl, W.config0_formula(), sig)
+    check(stl, W.config0_formula(), sig, mode="smooth", tau=5.0)
+
+
+@pytest.mark.parametrize("mode,tau", [("hard", 1.0), ("smooth", 10.0)])
+@pytest.mark.parametrize("T", [1000, 2345])
+def test_config1_small_batch(stl, mode, tau, T):
+    sig = W.config1_inputs(B=6, T=T, seed=3)
+    check(stl, W.config1_formula(), sig, mode=mode, tau=tau)
+
+
+@pytest.mark.parametrize("launch", [dict(tile=256), dict(tile=256, segment=700), dict(tile=512, threads=128),
+                                    dict(tile=1024, threads=512, segment=1500)])
+@pytest.mark.parametrize("mode,tau", [("hard", 1.0), ("smooth", 10.0)])
+def test_config1_streaming_and_segments(stl, launch, mode, tau):
+    sig = W.config1_inputs(B=5, T=3001, seed=4)
+    check(stl, W.config1_formula(), sig, mode=mode, tau=tau, launch=launch, seed=1)
+
+
+def test_config2_smooth_mask(stl):
+    sig, bounds = W.config2_inputs(B=32, T=2000, seed=0)
+    check(stl, W.config2_formula(), sig, bounds=bounds, mode="smooth", tau=10.0, mask_c=5.0, mask_eps=1e-3)
+    check(stl, W.config2_formula(), sig, bounds=bounds, mode="hard", mask_c=5.0, mask_eps=1e-3)
+
+
+@pytest.mark.parametrize("mode", ["hard", "smooth"])
+def test_always_sm_small_sharpness(stl, mode):
+    rng = np.random.default_rng(7)
+    sig = rng.normal(size=(6, 700, 1)).astype(np.float32)
+    a = rng.uniform(0, 30, size=6)
+    bounds = np.stack([a, a + rng.uniform(5, 60, size=6)], 1).astype(np.float32)[:, None, :]
+    tree = W.AlwaysSm(40, 100, W.lt([1.0], 0.3), slot=0)
+    check(stl, tree, sig, bounds=bounds, mode=mode, tau=3.0, mask_c=0.7, mask_eps=1e-2, launch=dict(tile=256))
+
+
+# ------------------------------------------------------------------ formula families
+TABLE3 = W.table3_formulas(D=2, I=(2, 37))
+
+
+@pytest.mark.parametrize("k", range(6))
+@pytest.mark.parametrize("mode,tau", [("hard", 1.0), ("smooth", 4.0)])
+def test_table3_formulas(stl, k, mode, tau):
+    T = 300 if k < 3 else 1100
+    sig = W.random_walk(3, T, 2, seed=10 + k)
+    check(stl, TABLE3[k], sig, mode=mode, tau=tau, launch=dict(tile=256))
+
+
+def _random_ragged_bounds(rng, B, n_slots, cap):
+    a = rng.integers(0, cap // 2 + 1, size=(B, n_slots))
+    b = a + rng.integers(0, cap // 2 + 1, size=(B, n_slots))
+    return np.stack([a, b], axis=2).astype(np.float32)
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("mode,tau", [("hard", 1.0), ("smooth", 3.0)])
+def test_random_formulas_per_trace_bounds(stl, seed, mode, tau):
+    rng = np.random.default_rng(100 + seed)
+    ctr = [0]
+    tree = W.random_formula(rng, 3, 3 if seed % 2 else 4, ctr, b_cap=60.0)
+    n_slots = max(1, ctr[0])
+    B, T = 4, int(rng.integers(150, 1300))
+    sig = W.random_walk(B, T, 3, seed=seed)
+    bounds = _random_ragged_bounds(rng, B, n_slots, 60)
+    check(stl, tree, sig, bounds=bounds, mode=mode, tau=tau, launch=dict(tile=256, segment=400 if seed % 3 == 0 else 0))
+
+
+# ------------------------------------------------------------------ degenerate cases
+EDGE = [
+    ("T1", W.config1_formula(), 3, 1),
+    ("T2", W.Until(0, 3, W.gt([1, 0], 0.0), W.lt([0, 1], 0.2)), 2, 2),
+    ("window_longer_than_trace", W.Always(3, 90, W.gt([1], 0.1)), 1, 17),
+    ("const_pad", W.Eventually(2, 40, W.gt([1, 0], 0.0), pad=-0.25), 2, 33),
+    ("const_pad_until", W.Until(1, 30, W.gt([1, 0], 0.0), W.lt([0, 1], 0.3), pad=0.1), 2, 45),
+    ("true_until", W.Until(2, 9, W.true(), W.gt([1], 0.0)), 1, 50),
+    ("a_eq_b", W.And(W.Eventually(4, 4, W.gt([1, 0], 0.0)), W.Until(3, 3, W.gt([1, 0], 0.1), W.gt([0, 1], 0.0))), 2, 64),
+    ("unbounded", W.Eventually(0, math.inf, W.Always(0, math.inf, W.gt([1], 0.0))), 1, 300),
+    ("unbounded_until", W.Until(0, math.inf, W.gt([1, 0], -0.5), W.gt([0, 1], 0.5)), 2, 260),
+    ("not_chain", W.Not(W.Or(W.Not(W.gt([1], 0.0)), W.Always(1, 5, W.Not(W.lt([1], 0.2))))), 1, 77),
+]
+
+
+@pytest.mark.parametrize("name,tree,D,T", EDGE, ids=[e[0] for e in EDGE])
+@pytest.mark.parametrize("mode,tau", [("hard", 1.0), ("smooth", 2.0)])
+def test_degenerate(stl, name, tree, D, T, mode, tau):
+    sig = W.random_walk(3, T, D, seed=5)
+    if name == "true_until" and mode == "smooth":
+        tau = 6.0
+    check(stl, tree, sig, mode=mode, tau=tau, launch=dict(tile=32) if T > 40 else None)
+
+
+def test_ties_follow_the_oracle(stl):
+    """Integer-valued signals make exact ties everywhere; hard gradients must still land on
+    the same samples as the oracle's tie rule."""
+    rng = np.random.default_rng(9)
+    sig = rng.integers(-3, 4, size=(8, 400, 3)).astype(np.float32)
+    for tree in (W.config1_formula(), W.Until(2, 25, W.gt([1, 0, 0], 0), W.gt([0, 1, 0], 0)),
+                 W.Always(0, 40, W.Eventually(3, 19, W.lt([0, 0, 1], 0.0)))):
+        check(stl, tree, sig, launch=dict(tile=64))
+
+
+def test_empty_batch(stl):
+    f = stl.Formula(W.config0_formula(), D=2)
+    x = torch.zeros((0, 10, 2), device="cuda")
+    out = stl.robustness(f, x)
+    assert out.shape == (0, 10)
+
+
+def test_bounds_outside_caps_set_the_device_status(stl):
+    from paper_2501_04194_gb300.binding import device_status
+    device_status()
+    tree = W.Eventually(0, 10, W.gt([1], 0.0), slot=0)
+    sig = W.random_walk(2, 50, 1, seed=0)
+    bounds = np.array([[[0, 5]], [[2, 30]]], dtype=np.float32)   # 30 > cap 10
+    run(stl, tree, sig, bounds=bounds)
+    assert device_status() == -6
+    assert device_status() == 0
+
+
+# ------------------------------------------------------------------ full-size spot checks
+def test_config1_full_size_sampled(stl):
+    """B=1024, T=50000 (the benchmark launch): sampled traces checked against the oracle."""
+    B, T = 1024, 50000
+    sig = W.config1_inputs(B=B, T=T, seed=0)
+    tree = W.config1_formula()
+    f = stl.Formula(tree, D=3)
+    p = stl.params("hard")
+    x = torch.from_numpy(sig).cuda()
+    rho = stl.robustness(f, x, p=p)
+    gout = torch.from_numpy(np.random.default_rng(2).normal(size=(B, T)).astype(np.float32)).cuda()
+    gs, _ = stl.robustness_backward(f, x, gout, p=p)
+    torch.cuda.synchronize()
+    idx = [0, 511, 1023]
+    sub = sig[idx]
+    ref = oracle.robustness(tree, sub)
+    np.testing.assert_array_equal(rho[idx].cpu().numpy(), ref.astype(np.float32))
+    gref, _ = oracle.robustness_grad(tree, sub, gout[idx].cpu().numpy().astype(np.float64))
+    assert per_trace_err(gs[idx].cpu().numpy(), gref) <= GRAD_TOL
