@@ -1,0 +1,335 @@
+"""Benchmark: STL robustness forward + backward throughput on GB300.
+
+Workload (N=1): B=1024 random-walk traces of T=50000 samples, D=3, the nested formula
+  (Always_[0,500]((s_x > 0) Until_[5,200] (s_y + s_z < 0.2))) OR Eventually_[0,1000](s_z > 1)
+in hard mode.  One step = forward robustness trace of every trace + the hand-written backward
+(gradient of sum(g * rho) w.r.t. the signal) through the C ABI.  Inputs (614 MB signal, 205 MB
+upstream gradient) are resident in HBM and larger than L2, so no flush is needed.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "STL robustness fwd+bwd trace-steps/s & % HBM peak; warm vs cold solve time"
+UNIT = "trace-steps/s"
+B_DEFAULT, T_DEFAULT, D = 1024, 50000, 3
+
+
+def workload_name(B, T, mode):
+    return (f"nested Until/Always/Eventually (config 1), {mode}, B={B} T={T} D={D}, random-walk signals, "
+            f"fwd+bwd")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2501_04194_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, B, T):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernels."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d.get(kernel)
+        if not e or e.get("source_sha") != kernel_source_sha():
+            return None
+        # captured on a smaller case: scale by trace-steps
+        return float(e["dram_bytes"]) * (B * T) / float(e["trace_steps"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        loaded = [r for r in rows if r["power"] > 200] or rows
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                            ("pcap", "sw_power_cap")):
+                if r[k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median([r["sm"] for r in loaded])), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def oracle_sample(B, T, tree, n_traces, seed=0):
+    """Time the FP64 oracle (as it stands) for fwd+bwd on a bounded sample of traces."""
+    import workloads as W
+    import oracle
+    sig = W.random_walk(n_traces, T, D, seed=seed)
+    gout = np.random.default_rng(seed + 1).normal(size=(n_traces, T))
+    t = time.perf_counter()
+    oracle.robustness(tree, sig)
+    oracle.robustness_grad(tree, sig, gout)
+    dt = time.perf_counter() - t
+    return n_traces * T / dt, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import workloads as W
+    tree = W.config1_formula()
+    n = args.ref_traces
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(B_DEFAULT, args.T, tree, max(1, n // 4))
+    for _ in range(args.steps):
+        v, dt, cores = oracle_sample(B_DEFAULT, args.T, tree, n)
+        vals.append(v)
+    v = float(np.median(vals))
+    sample = f"{n} traces x T={args.T} per step (of B={B_DEFAULT}), fwd+bwd, FP64 oracle, {cores} threads"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": B_DEFAULT * args.T / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(B_DEFAULT, args.T, "hard"), "B": B_DEFAULT, "T": args.T, "D": D},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--T", type=int, default=T_DEFAULT)
+    ap.add_argument("--B", type=int, default=B_DEFAULT)
+    ap.add_argument("--mode", default="hard", choices=["hard", "smooth"])
+    ap.add_argument("--tau", type=float, default=10.0)
+    ap.add_argument("--ref-traces", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2501_04194_gb300 as stl
+    import workloads as W
+
+    B, T = args.B, args.T
+    tree = W.config1_formula()
+    f = stl.Formula(tree, D=D)
+    p = stl.params(args.mode, tau=args.tau)
+    # every rank owns B independent traces (weak scaling); seeds differ per rank
+    sig_np = W.random_walk(B, T, D, seed=rank)
+    x = torch.from_numpy(sig_np).to(dev)
+    g = torch.randn((B, T), generator=torch.Generator(device=dev).manual_seed(rank), device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ws_f = f.workspace_size(B, T, p, False)
+    ws_b = f.workspace_size(B, T, p, True)
+    wsf = torch.empty(max(1, ws_f // 4 + 1), device=dev)
+    wsb = torch.empty(max(1, ws_b // 4 + 1), device=dev)
+    rho = torch.empty((B, T), device=dev)
+    gsig = torch.empty((B, T, D), device=dev)
+    from paper_2501_04194_gb300.binding import robustness_backward_raw, robustness_raw
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        robustness_raw(f, x.data_ptr(), B, T, None, p, rho.data_ptr(), wsf.data_ptr(), ws_f, stream.cuda_stream)
+        if ev:
+            ev[1].record(stream)
+        robustness_backward_raw(f, x.data_ptr(), B, T, None, p, g.data_ptr(), gsig.data_ptr(), None,
+                                wsb.data_ptr(), ws_b, stream.cuda_stream)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local if world > 1 else 0) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop() if clocks else None
+    ms_total = t_start.elapsed_time(t_end)
+    fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    bwd_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * B * T / (ms_step * 1e-3)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hsig = torch.from_numpy(sig_np).pin_memory()
+        hg = g.cpu().pin_memory()
+        hrho = torch.empty((B, T)).pin_memory()
+        hgs = torch.empty((B, T, D)).pin_memory()
+        xs = torch.empty_like(x)
+        gs_in = torch.empty_like(g)
+
+        def e2e_step():
+            xs.copy_(hsig, non_blocking=True)
+            gs_in.copy_(hg, non_blocking=True)
+            robustness_raw(f, xs.data_ptr(), B, T, None, p, rho.data_ptr(), wsf.data_ptr(), ws_f, stream.cuda_stream)
+            robustness_backward_raw(f, xs.data_ptr(), B, T, None, p, gs_in.data_ptr(), gsig.data_ptr(), None,
+                                    wsb.data_ptr(), ws_b, stream.cuda_stream)
+            hrho.copy_(rho, non_blocking=True)
+            hgs.copy_(gsig, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        n_e2e = max(3, min(args.steps, 5))
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n_e2e):
+            e2e_step()
+        b_.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = a.elapsed_time(b_) / n_e2e
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * B * T / (e2e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(hsig.numel() * 4 + hg.numel() * 4),
+               "d2h_bytes_per_step": int(hrho.numel() * 4 + hgs.numel() * 4)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    # algorithmic bytes per trace-step: forward reads the signal (4D) and writes rho (4);
+    # backward reads the signal (4D) and g (4) and writes the gradient (4D)
+    fwd_bytes = (4 * D + 4) * B * T
+    bwd_bytes = (8 * D + 4) * B * T
+    dom = "backward" if bwd_ms >= fwd_ms else "forward"
+    dom_bytes, dom_ms = (bwd_bytes, bwd_ms) if dom == "backward" else (fwd_bytes, fwd_ms)
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(f"stl_main_{dom}", B, T)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": f"stl_main ({dom})", "peak_kind": peak_kind,
+            "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+            "step_frac": (fwd_bytes + bwd_bytes) / (ms_step * 1e-3) / 1e9 / peak}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        n = 128
+        v, dt, cores = oracle_sample(B, T, tree, n, seed=0)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} of {B} traces x T={T}, fwd+bwd, FP64 oracle ({dt:.1f} s)"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(B, T, args.mode), "B": B, "T": T, "D": D, "mode": args.mode,
+                       "tau": args.tau if args.mode == "smooth" else None,
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "clocks": ck}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

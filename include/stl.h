@@ -79,7 +79,7 @@ typedef enum {
 typedef enum { STL_PAD_LAST = 0, STL_PAD_CONST = 1 } stl_pad;
 
 /* One node of a formula.  Nodes are listed children-before-parents; the root is the last
- * node and every other node has exactly one parent (a tree). */
+ * node and every other node has exactly one parent (a tree); at most 64 nodes. */
 typedef struct {
   int32_t op;          /* stl_op */
   int32_t child0;      /* index of the (first) child, -1 if none */

@@ -5,7 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 
-#define STL_MAX_NODES 32
+#define STL_MAX_NODES 64
 #define STL_MAX_WEIGHTS 256
 #define STL_MAX_D 16
 

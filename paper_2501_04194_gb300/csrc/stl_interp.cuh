@@ -779,6 +779,12 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
         j1 = j1 < s1 ? j1 : s1;
         j1 = j1 < T - 1 ? j1 : T - 1;
         const int D = P.D;
+        if (t0 == R0) {
+          // samples before the first predicate offset are read by no predicate: zero gradient
+          const int z1 = j0 < T - 1 ? j0 : T - 1;
+          for (int idx = threadIdx.x; idx < (z1 - s0) * D; idx += NT)
+            A.gsig[((size_t)C.b * T + s0) * D + idx] = 0.f;
+        }
         for (int idx = threadIdx.x; idx < (j1 - j0) * D; idx += NT) {
           const int j = j0 + idx / D, d = idx - (idx / D) * D;
           float acc = 0.f;

@@ -60,6 +60,8 @@ def run(stl, tree, sig, bounds=None, mode="hard", tau=1.0, mask_c=5.0, mask_eps=
         gs = gs.cpu().numpy()
         gb = None if gb is None else gb.cpu().numpy()
     torch.cuda.synchronize()
+    from paper_2501_04194_gb300.binding import device_status
+    assert device_status() == 0, "per-trace bounds outside the compiled caps"
     return rho, gs, gb
 
 

@@ -197,7 +197,7 @@ def random_formula(rng, D, depth, slot_counter, b_cap):
             return (op, build(d - 1), build(int(rng.integers(0, d))))
         slot = slot_counter[0]
         slot_counter[0] += 1
-        iv = interval(0.0, b_cap, slot, None)
+        iv = interval(b_cap, b_cap, slot, None)   # caps for the per-trace (a, b)
         if op == "until":
             return ("until", iv, build(d - 1), build(int(rng.integers(0, d))))
         return (op, iv, build(d - 1))
