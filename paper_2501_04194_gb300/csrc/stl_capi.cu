@@ -136,12 +136,14 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
   e = stl_max_smem_optin(&max_smem);
   if (e) return cuda_fail(e, "cudaDeviceGetAttribute(max shared memory)");
 
-  int threads = h->launch.threads ? h->launch.threads : 256;
-  int tile = h->launch.tile ? h->launch.tile : 2048;
-  tile = std::min(tile, round_up(T, 32));
-  tile = std::max(32, round_up(tile, 32));
+  // A window pass covers threads x R outputs; by default the tile equals one pass and is the
+  // largest that keeps every ring in shared memory.
   const int win_r = maxK >= 64 ? 16 : 8;
   P.win_r = win_r;
+  int threads = h->launch.threads ? h->launch.threads : 256;
+  int tile = h->launch.tile ? h->launch.tile : threads * win_r;
+  tile = std::min(tile, round_up(T, 32));
+  tile = std::max(32, round_up(tile, 32));
 
   auto padded = [](int cap) { return cap + cap / 32 + 1; };
   auto layout = [&](int tl, std::vector<int> &space_out, int &smem_words, int &gwords) {
@@ -181,8 +183,9 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
   for (;;) {
     bool ok = layout(tile, space, smem_words, gwords);
     if (!ok) return fail(STL_ERR_UNSUPPORTED, "formula scratch does not fit in shared memory");
-    if (gwords == 0 || tile <= 256) break;
+    if (gwords == 0 || tile <= 256 || h->launch.tile) break;
     tile = std::max(256, round_up(tile / 2, 32));
+    if (!h->launch.threads) threads = std::max(128, std::min(512, tile / win_r));
   }
   P.tile = tile;
 
@@ -219,6 +222,15 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
   for (int i = 0; i < n; ++i) {
     if (P.nd[i].c0 >= 0) P.nd[P.nd[i].c0].parent = i;
     if (P.nd[i].c1 >= 0) P.nd[P.nd[i].c1].parent = i;
+  }
+  P.npred = 0;
+  for (int i = 0; i < n; ++i) {
+    const stl_node &nd = h->nodes[i];
+    if (!is_pred(nd.op)) continue;
+    const int k = P.npred++;
+    P.pred[k] = i;
+    for (int d = 0; d < h->D; ++d)
+      P.pw[k * STL_MAX_D + d] = nd.op == STL_OP_PRED_GT ? h->w[nd.pred_offset + d] : -h->w[nd.pred_offset + d];
   }
   const int scratch_words = (threads + maxK / win_r + 4) * 4;
   P.scratch_off = round_up(off_s, 4);
@@ -360,6 +372,9 @@ stl_status stl_compile(const stl_node *nodes, int32_t n_nodes, const float *pred
       if (nd.op == STL_OP_UNTIL) has_until = true;
     }
   }
+  int npred = 0;
+  for (int i = 0; i < n_nodes; ++i) npred += is_pred(nodes[i].op);
+  if (npred > STL_MAX_PRED) return fail(STL_ERR_INVALID_ARG, "at most %d predicates per formula", STL_MAX_PRED);
   for (int i = 0; i < n_nodes - 1; ++i)
     if (parents[i] != 1) return fail(STL_ERR_INVALID_ARG, "node %d must have exactly one parent (tree, root last)", i);
   if (parents[n_nodes - 1] != 0) return fail(STL_ERR_INVALID_ARG, "the root (last node) cannot have a parent");

@@ -8,6 +8,7 @@
 #define STL_MAX_NODES 64
 #define STL_MAX_WEIGHTS 256
 #define STL_MAX_D 16
+#define STL_MAX_PRED 32
 
 // Node layout after compilation (per launch: the ring geometry depends on tile and bounds).
 struct KNode {
@@ -48,6 +49,9 @@ struct KProgram {
   long long ut_off;    // word offset of the smooth-until per-thread arrays in the workspace
   int ut_len;          // their length (max taps)
   int win_r;           // samples per thread-run in the window reductions (8 or 16)
+  int npred;           // predicate nodes
+  int pred[STL_MAX_PRED];
+  float pw[STL_MAX_PRED * STL_MAX_D];   // +w (mu - c) or -w (c - mu) per predicate
   float w[STL_MAX_WEIGHTS];
   KNode nd[STL_MAX_NODES];
 };

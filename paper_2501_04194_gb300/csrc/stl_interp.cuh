@@ -41,16 +41,6 @@ enum {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// ------------------------------------------------------------------ ring access
-// Positions of the live range map to pos mod cap.  The clamp keeps any position outside the
-// live range inside the ring, so a logic error cannot address memory beyond it.
-__device__ __forceinline__ int ring_slot(const NodeRt &r, int pos) {
-  int s = pos - r.base;
-  s = (s >= r.cap) ? s - r.cap : s;
-  s = s < 0 ? 0 : (s >= r.cap ? r.cap - 1 : s);
-  return s + (s >> 5);   // one pad word per 32: stride-R thread runs avoid bank conflicts
-}
-
 // ------------------------------------------------------------------ combine monoids
 struct VI { float v; int i; };
 struct MaxM {
@@ -118,19 +108,24 @@ __device__ __forceinline__ void window_reduce(int q0, int q1, int ia, int ib, co
   const int rho = K - (nf + 1) * R;   // lead of the trailing prefix
   for (int p0 = q0; p0 < q1; p0 += NT * R) {
     const int u = p0 + tid * R;
+    // threads that own outputs in this pass; the runs after them come from the extra loop
+    const int nv = min(NT, (q1 - p0 + R - 1) / R);
+    // every thread's first run is also run aggregate number tid; runs past the CTA come
+    // from the extra loop (only when nv + nf > NT)
     T hv[R];
     hv[R - 1] = elem(u + ia + R - 1);
 #pragma unroll
     for (int k = R - 2; k >= 0; --k) hv[k] = M::comb(elem(u + ia + k), hv[k + 1]);
     runagg[tid] = hv[0];
-    for (int e = tid; e < nf; e += NT) {
-      const int s = p0 + ia + (NT + e) * R;
+    for (int e = NT + tid; e < nv + nf; e += NT) {
+      const int s = p0 + ia + e * R;
       T acc = elem(s);
 #pragma unroll
       for (int k = 1; k < R; ++k) acc = M::comb(acc, elem(s + k));
-      runagg[NT + e] = acc;
+      runagg[e] = acc;
     }
     __syncthreads();
+    if (tid < nv) {
     T mid = runagg[tid + 1];
     for (int j = 2; j <= nf; ++j) mid = M::comb(mid, runagg[tid + j]);
     const int gs = u + ia + (nf + 1) * R;
@@ -152,6 +147,7 @@ __device__ __forceinline__ void window_reduce(int q0, int q1, int ia, int ib, co
         acc = have ? M::comb(acc, e) : e;
         have = true;
       }
+    }
     }
     __syncthreads();
   }
@@ -182,46 +178,146 @@ __device__ __forceinline__ int frontier(const Cta &C, int n) {
   return e < C.T ? e : C.T;
 }
 
-// value of child c read by parent node p at sample j (pads past T-1); src = gradient target
-__device__ __forceinline__ float child_val(const Cta &C, const KNode &p, int c, int j, int &src) {
-  const NodeRt &r = C.rt[c];
-  if (j >= C.T) {
-    if (p.pad_const) { src = -1; return p.pad_value; }
-    src = C.T - 1;
-    return r.lastval;
+// Register copies of the ring addressing: built once per operator call, so the inner loops
+// do not re-read node metadata from shared memory.
+struct Ring {
+  float *p;
+  int base, cap;
+  __device__ __forceinline__ int slot(int pos) const {
+    int s = pos - base;
+    s = (s >= cap) ? s - cap : s;
+    s = s < 0 ? 0 : (s >= cap ? cap - 1 : s);
+    return s + (s >> 5);
   }
-  int f = frontier(C, c) - 1;
-  j = j < f ? j : f;
-  src = j;
-  if (j == C.T - 1) return r.lastval;
-  return r.val[ring_slot(r, j)];
+};
+
+// a parent's read access to child values (pads past T-1, clamp at the child's frontier)
+struct ChildView {
+  Ring v;
+  int fmax, T;
+  float lastval, padv;
+  bool padc;
+  __device__ __forceinline__ float get(int j, int &src) const {
+    if (j >= T) {
+      src = padc ? -1 : T - 1;
+      return padc ? padv : lastval;
+    }
+    j = j < fmax ? j : fmax;
+    src = j;
+    return j == T - 1 ? lastval : v.p[v.slot(j)];
+  }
+  __device__ __forceinline__ float get(int j) const { int s; return get(j, s); }
+};
+
+__device__ __forceinline__ ChildView child_view(const Cta &C, const KNode &p, int c) {
+  const NodeRt &r = C.rt[c];
+  ChildView cv;
+  cv.v.p = r.val;
+  cv.v.base = r.base;
+  cv.v.cap = r.cap;
+  cv.fmax = frontier(C, c) - 1;
+  cv.T = C.T;
+  cv.lastval = r.lastval;
+  cv.padv = p.pad_value;
+  cv.padc = p.pad_const != 0;
+  return cv;
 }
 
-// node m's own value / recorded source at sample q (sample T-1 lives in per-node cells,
-// because at the end of a trace it can lie below the live range of the last step)
-__device__ __forceinline__ float val_at(const Cta &C, int m, int q) {
-  const NodeRt &r = C.rt[m];
-  return q >= C.T - 1 ? r.lastval : r.val[ring_slot(r, q)];
-}
-__device__ __forceinline__ int aux_at(const Cta &C, int m, int q) {
-  const NodeRt &r = C.rt[m];
-  return q >= C.T - 1 ? r.lastaux : r.aux[ring_slot(r, q)];
+// a node's own values / sources (sample T-1 lives in per-node cells, because at the end of
+// a trace it can lie below the live range of the last step)
+struct OwnView {
+  Ring v;
+  int *aux;
+  float *adj;
+  int T;
+  float lastval;
+  int lastaux;
+  float padadj;
+  __device__ __forceinline__ float val(int q) const { return q >= T - 1 ? lastval : v.p[v.slot(q)]; }
+  __device__ __forceinline__ int src(int q) const { return q >= T - 1 ? lastaux : aux[v.slot(q)]; }
+  __device__ __forceinline__ float g(int q) const { return q >= T - 1 ? padadj : adj[v.slot(q)]; }
+};
+
+__device__ __forceinline__ OwnView own_view(const Cta &C, int n) {
+  const NodeRt &r = C.rt[n];
+  OwnView o;
+  o.v.p = r.val;
+  o.v.base = r.base;
+  o.v.cap = r.cap;
+  o.aux = r.aux;
+  o.adj = r.adj;
+  o.T = C.T;
+  o.lastval = r.lastval;
+  o.lastaux = r.lastaux;
+  o.padadj = r.padadj;
+  return o;
 }
 
-// store node n's value at sample q (and clear its adjoint slot for the backward)
-__device__ __forceinline__ void put(const Cta &C, int n, int q, float v) {
+// writer of node n's values (and the zeroing of its adjoint slots in backward launches)
+struct NodeOut {
+  Ring v;
+  float *adj;
+  int *aux;
+  float *out_row;
+  NodeRt *rt;
+  int T;
+  __device__ __forceinline__ void put(int q, float val) const {
+    const int s = v.slot(q);
+    v.p[s] = val;
+    if (adj) adj[s] = 0.f;
+    if (q == T - 1) rt->lastval = val;
+    if (out_row) out_row[q] = val;
+  }
+  __device__ __forceinline__ void put(int q, float val, int src) const {
+    const int s = v.slot(q);
+    v.p[s] = val;
+    if (adj) adj[s] = 0.f;
+    if (aux) aux[s] = src;
+    if (q == T - 1) { rt->lastval = val; rt->lastaux = src; }
+    if (out_row) out_row[q] = val;
+  }
+};
+
+__device__ __forceinline__ NodeOut node_out(const Cta &C, int n) {
   NodeRt &r = C.rt[n];
-  const int s = ring_slot(r, q);
-  r.val[s] = v;
-  if (r.adj) r.adj[s] = 0.f;
-  if (q == C.T - 1) r.lastval = v;
-  if (n == C.root && C.out_row) C.out_row[q] = v;
+  NodeOut o;
+  o.v.p = r.val;
+  o.v.base = r.base;
+  o.v.cap = r.cap;
+  o.adj = r.adj;
+  o.aux = r.aux;
+  o.out_row = (n == C.root) ? C.out_row : nullptr;
+  o.rt = &r;
+  o.T = C.T;
+  return o;
 }
 
-__device__ __forceinline__ void put_aux(const Cta &C, int n, int q, int src) {
-  NodeRt &r = C.rt[n];
-  if (r.aux) r.aux[ring_slot(r, q)] = src;
-  if (q == C.T - 1) r.lastaux = src;
+// a parent's write access to a child's adjoint (sample T-1 and pads go to the per-node cell)
+struct ChildAdj {
+  Ring a;
+  float *padadj;
+  int T;
+  __device__ __forceinline__ void add_atomic(int j, float g) const {
+    if (j < 0 || g == 0.f) return;
+    if (j >= T - 1) atomicAdd(padadj, g);
+    else atomicAdd(&a.p[a.slot(j)], g);
+  }
+  __device__ __forceinline__ void add_owned(int j, float g) const {
+    if (j < 0) return;
+    if (j >= T - 1) { if (g != 0.f) atomicAdd(padadj, g); }
+    else a.p[a.slot(j)] += g;
+  }
+};
+
+__device__ __forceinline__ ChildAdj child_adj(const Cta &C, int c) {
+  NodeRt &r = C.rt[c];
+  ChildAdj o;
+  o.a.p = r.adj;
+  o.a.base = r.base;
+  o.a.cap = r.cap;
+  o.padadj = &r.padadj;
+  o.T = C.T;
+  return o;
 }
 
 // ------------------------------------------------------------------ forward ops
@@ -231,54 +327,60 @@ __device__ void eval_pred(const Cta &C, int n, int F, int E) {
   const int D = P.D;
   const float *w = P.w + nd.w_off;
   const float *xs = C.sig + (size_t)C.b * (size_t)C.T * D;
+  const NodeOut out = node_out(C, n);
+  const bool gt = nd.op == OP_PGT;
+  const float pc = nd.pc;
   for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
     const float *x = xs + (size_t)q * D;
-    float s = __fmul_rn(w[0], x[0]);
-    for (int d = 1; d < D; ++d) s = __fadd_rn(s, __fmul_rn(w[d], x[d]));
-    put(C, n, q, nd.op == OP_PGT ? __fsub_rn(s, nd.pc) : __fsub_rn(nd.pc, s));
+    float s = __fmul_rn(w[0], __ldg(x));
+    for (int d = 1; d < D; ++d) s = __fadd_rn(s, __fmul_rn(w[d], __ldg(x + d)));
+    out.put(q, gt ? __fsub_rn(s, pc) : __fsub_rn(pc, s));
   }
 }
 
 __device__ void eval_elementwise(const Cta &C, int n, int F, int E) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
+  const NodeOut out = node_out(C, n);
+  const int op = nd.op;
+  if (op == OP_TRUE) {
+    for (int q = F + threadIdx.x; q < E; q += blockDim.x) out.put(q, INFINITY);
+    return;
+  }
+  const ChildView x = child_view(C, nd, nd.c0);
+  if (op == OP_NOT) {
+    for (int q = F + threadIdx.x; q < E; q += blockDim.x) out.put(q, -x.get(q));
+    return;
+  }
+  const ChildView y = child_view(C, nd, nd.c1);
   const bool smooth = P.mode == 1;
   const float tau = P.tau, itau = P.inv_tau;
+  const float sg = op == OP_AND ? 1.f : -1.f;
   for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
+    const float a = x.get(q), b = y.get(q);
     float v;
-    if (nd.op == OP_TRUE) {
-      v = INFINITY;
-    } else if (nd.op == OP_NOT) {
-      const NodeRt &a = C.rt[nd.c0];
-      v = -a.val[ring_slot(a, q)];
+    if (!smooth) {
+      v = op == OP_AND ? (a <= b ? a : b) : (a >= b ? a : b);
     } else {
-      const NodeRt &a = C.rt[nd.c0], &bq = C.rt[nd.c1];
-      const float x = a.val[ring_slot(a, q)], y = bq.val[ring_slot(bq, q)];
-      if (!smooth) {
-        v = nd.op == OP_AND ? (x <= y ? x : y) : (x >= y ? x : y);
-      } else {
-        // two-term logsumexp min / max: min(x,y) - log1p(e^{-tau|x-y|}) / tau
-        const float sg = nd.op == OP_AND ? 1.f : -1.f;
-        const float xs = sg * x, ys = sg * y;
-        const float m = xs < ys ? xs : ys;
-        float dlt = fabsf(xs - ys);
-        float corr = (xs == ys) ? 0.69314718f * itau : log1pf(expf(-tau * dlt)) * itau;
-        if (isinf(xs) || isinf(ys)) corr = 0.f;
-        v = sg * (m - corr);
-      }
+      // two-term logsumexp min / max: min(x,y) - log1p(e^{-tau|x-y|}) / tau
+      const float xs = sg * a, ys = sg * b;
+      const float m = xs < ys ? xs : ys;
+      float corr = (xs == ys) ? 0.69314718f * itau : log1pf(expf(-tau * fabsf(xs - ys))) * itau;
+      if (isinf(xs) || isinf(ys)) corr = 0.f;
+      v = sg * (m - corr);
     }
-    put(C, n, q, v);
+    out.put(q, v);
   }
 }
 
-// hard window of node n over its child with offsets [ia, ib] (max for sgn>0, min otherwise)
+// hard window of node n over its child with offsets [ia, ib] (max or min, earliest sample)
 __device__ void eval_hard_window(const Cta &C, int n, int F, int E, int ia, int ib) {
   const KNode &nd = C.P->nd[n];
-  const int c = nd.c0;
-  auto elem = [&](int j) { VI r; r.v = child_val(C, nd, c, j, r.i); return r; };
-  auto out = [&](int q, VI r) { put(C, n, q, r.v); put_aux(C, n, q, r.i); };
-  const bool mx = nd.op == OP_EV || nd.op == OP_EVSM;
-  if (mx) window_reduce_r<MaxM>(C.P->win_r, F, E, ia, ib, elem, out, C.scratch);
+  const ChildView cv = child_view(C, nd, nd.c0);
+  const NodeOut o = node_out(C, n);
+  auto elem = [&](int j) { VI r; r.v = cv.get(j, r.i); return r; };
+  auto out = [&](int q, VI r) { o.put(q, r.v, r.i); };
+  if (nd.op == OP_EV || nd.op == OP_EVSM) window_reduce_r<MaxM>(C.P->win_r, F, E, ia, ib, elem, out, C.scratch);
   else window_reduce_r<MinM>(C.P->win_r, F, E, ia, ib, elem, out, C.scratch);
 }
 
@@ -286,11 +388,12 @@ __device__ void eval_hard_window(const Cta &C, int n, int F, int E, int ia, int 
 __device__ void eval_smooth_window(const Cta &C, int n, int F, int E, int ia, int ib) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
-  const int c = nd.c0;
-  const float st = (nd.op == OP_EV ? 1.f : -1.f) * P.tau;
+  const ChildView cv = child_view(C, nd, nd.c0);
+  const NodeOut o = node_out(C, n);
   const float sgn = nd.op == OP_EV ? 1.f : -1.f;
-  auto elem = [&](int j) { int s; LS r; r.m = st * child_val(C, nd, c, j, s); r.s = 1.f; return r; };
-  auto out = [&](int q, LS r) { put(C, n, q, sgn * (r.m + logf(r.s)) * P.inv_tau); };
+  const float st = sgn * P.tau, sit = sgn * P.inv_tau;
+  auto elem = [&](int j) { LS r; r.m = st * cv.get(j); r.s = 1.f; return r; };
+  auto out = [&](int q, LS r) { o.put(q, (r.m + logf(r.s)) * sit); };
   window_reduce_r<LseM>(P.win_r, F, E, ia, ib, elem, out, C.scratch);
 }
 
@@ -298,18 +401,20 @@ __device__ void eval_smooth_window(const Cta &C, int n, int F, int E, int ia, in
 // composes the clamps over [a, b] and keeps min(A_q, V_{q+a}) with A winning ties.
 __device__ void eval_hard_until(const Cta &C, int n, int F, int E, int ia, int ib) {
   const KNode &nd = C.P->nd[n];
-  const int cp = nd.c0, cq = nd.c1;
+  const ChildView cp = child_view(C, nd, nd.c0);
+  const ChildView cq = child_view(C, nd, nd.c1);
+  const NodeOut o = node_out(C, n);
   {
-    auto elem = [&](int j) { VI r; int s; r.v = child_val(C, nd, cp, j, s); r.i = s < 0 ? -1 : 2 * s; return r; };
-    auto out = [&](int q, VI r) { put(C, n, q, r.v); put_aux(C, n, q, r.i); };
+    auto elem = [&](int j) { VI r; int s; r.v = cp.get(j, s); r.i = s < 0 ? -1 : 2 * s; return r; };
+    auto out = [&](int q, VI r) { o.put(q, r.v, r.i); };
     window_reduce_r<MinM>(C.P->win_r, F, E, 0, ia, elem, out, C.scratch);
   }
   __syncthreads();
   auto elem = [&](int j) {
     CC r;
     int sp, sq;
-    const float p = child_val(C, nd, cp, j, sp);
-    const float q = child_val(C, nd, cq, j, sq);
+    const float p = cp.get(j, sp);
+    const float q = cq.get(j, sq);
     const int ep = sp < 0 ? -1 : 2 * sp, eq = sq < 0 ? -1 : 2 * sq + 1;
     const bool pl = p <= q;
     r.c = pl ? p : q;
@@ -319,14 +424,13 @@ __device__ void eval_hard_until(const Cta &C, int n, int F, int E, int ia, int i
     return r;
   };
   auto out = [&](int q, CC r) {
-    NodeRt &me = C.rt[n];
-    const int s = ring_slot(me, q);
-    const float A = me.val[s];
+    const int s = o.v.slot(q);
+    const float A = o.v.p[s];
     if (!(A <= r.c)) {
-      me.val[s] = r.c;
-      if (me.aux) me.aux[s] = r.cs;
-      if (q == C.T - 1) { me.lastval = r.c; me.lastaux = r.cs; }
-      if (n == C.root && C.out_row) C.out_row[q] = r.c;
+      o.v.p[s] = r.c;
+      if (o.aux) o.aux[s] = r.cs;
+      if (q == o.T - 1) { o.rt->lastval = r.c; o.rt->lastaux = r.cs; }
+      if (o.out_row) o.out_row[q] = r.c;
     }
   };
   window_reduce_r<ClampM>(C.P->win_r, F, E, ia, ib, elem, out, C.scratch);
@@ -336,20 +440,22 @@ __device__ void eval_hard_until(const Cta &C, int n, int F, int E, int ia, int i
 __device__ void eval_smooth_until(const Cta &C, int n, int F, int E, int ia, int ib) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
+  const ChildView cp = child_view(C, nd, nd.c0);
+  const ChildView cq = child_view(C, nd, nd.c1);
+  const NodeOut o = node_out(C, n);
   const float tau = P.tau, itau = P.inv_tau;
   for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
     float M1 = -INFINITY, S1 = 0.f;   // sum_k e^{-tau phi}: (max exponent, scaled sum)
     float M2 = -INFINITY, S2 = 0.f;   // sum_i e^{tau z_i}
     for (int i = 0; i <= ib; ++i) {
-      int s;
-      const float zp = -tau * child_val(C, nd, nd.c0, q + i, s);
+      const float zp = -tau * cp.get(q + i);
       if (zp != -INFINITY) {
         if (zp > M1) { S1 = fmaf(S1, expf(M1 - zp), 1.f); M1 = zp; }
         else S1 += expf(zp - M1);
       }
       if (i >= ia) {
         const float Pv = M1 == -INFINITY ? INFINITY : -(M1 + logf(S1)) * itau;
-        const float qv = child_val(C, nd, nd.c1, q + i, s);
+        const float qv = cq.get(q + i);
         float z;
         if (isinf(Pv) || isinf(qv)) z = Pv < qv ? Pv : qv;
         else z = fminf(Pv, qv) - log1pf(expf(-tau * fabsf(Pv - qv))) * itau;
@@ -360,7 +466,7 @@ __device__ void eval_smooth_until(const Cta &C, int n, int F, int E, int ia, int
         }
       }
     }
-    put(C, n, q, M2 == -INFINITY ? -INFINITY : (M2 + logf(S2)) * itau);
+    o.put(q, M2 == -INFINITY ? -INFINITY : (M2 + logf(S2)) * itau);
   }
 }
 
@@ -376,19 +482,22 @@ __device__ void eval_smooth_mask(const Cta &C, int n, int F, int E) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
   const NodeRt &me = C.rt[n];
+  const ChildView cv = child_view(C, nd, nd.c0);
+  const NodeOut o = node_out(C, n);
+  const int ia = me.ia, ib = me.ib;
+  const float fa = me.fa, fb = me.fb, mc = P.mask_c, me_eps = P.mask_eps;
   const float sgn = nd.op == OP_EVSM ? 1.f : -1.f;
   const float st = sgn * P.tau;
   for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
     float M = -INFINITY, S = 0.f;
-    for (int i = me.ia; i <= me.ib; ++i) {
-      const float m = smask((float)i, me.fa, me.fb, P.mask_c, P.mask_eps);
+    for (int i = ia; i <= ib; ++i) {
+      const float m = smask((float)i, fa, fb, mc, me_eps);
       if (m <= 0.f) continue;
-      int s;
-      const float z = st * child_val(C, nd, nd.c0, q + i, s);
+      const float z = st * cv.get(q + i);
       if (z > M) { S = fmaf(S, expf(M - z), m); M = z; }
       else S = fmaf(m, expf(z - M), S);
     }
-    put(C, n, q, M == -INFINITY ? sgn * -INFINITY : sgn * (M + logf(S)) * P.inv_tau);
+    o.put(q, M == -INFINITY ? sgn * -INFINITY : sgn * (M + logf(S)) * P.inv_tau);
   }
 }
 
@@ -422,28 +531,10 @@ __device__ void eval_node(const Cta &C, int n, int F, int E) {
 }
 
 // ------------------------------------------------------------------ adjoint helpers
-__device__ __forceinline__ float adj_at(const Cta &C, int n, int q) {
-  const NodeRt &r = C.rt[n];
-  return q >= C.T - 1 ? r.padadj : r.adj[ring_slot(r, q)];
-}
-
-// add g to child c's adjoint at sample j (j already mapped to a real sample, or -1)
-__device__ __forceinline__ void add_adj_atomic(const Cta &C, int c, int j, float g) {
-  if (j < 0 || g == 0.f) return;
-  NodeRt &r = C.rt[c];
-  if (j >= C.T - 1) atomicAdd(&r.padadj, g);
-  else atomicAdd(&r.adj[ring_slot(r, j)], g);
-}
-__device__ __forceinline__ void add_adj_owned(const Cta &C, int c, int j, float g) {
-  if (j < 0) return;
-  NodeRt &r = C.rt[c];
-  if (j >= C.T - 1) { if (g != 0.f) atomicAdd(&r.padadj, g); }
-  else r.adj[ring_slot(r, j)] += g;
-}
-
 // warp-aggregated scatter: lanes hold (key, g); runs of equal keys in consecutive lanes are
-// summed first, then one atomic per run.  key encodes child*(2^30) + sample, or -1.
-__device__ __forceinline__ void scatter_run(const Cta &C, int c_even, int c_odd, int key, float g, bool even_odd) {
+// summed first, then one atomic per run.  key = sample (or 2*sample + child for Until), -1 none.
+__device__ __forceinline__ void scatter_run(const ChildAdj &a0, const ChildAdj &a1, int key, float g,
+                                            bool even_odd) {
   const int lane = threadIdx.x & 31;
   const int up = __shfl_up_sync(FULL, key, 1);
   const bool head = lane == 0 || up != key;
@@ -457,13 +548,12 @@ __device__ __forceinline__ void scatter_run(const Cta &C, int c_even, int c_odd,
     if (lane + off < 32 && rv == rid) s += sv;
   }
   if (head && key >= 0) {
-    if (even_odd) add_adj_atomic(C, (key & 1) ? c_odd : c_even, key >> 1, s);
-    else add_adj_atomic(C, c_even, key, s);
+    if (even_odd) ((key & 1) ? a1 : a0).add_atomic(key >> 1, s);
+    else a0.add_atomic(key, s);
   }
 }
 
 __device__ __forceinline__ void accumulate_shared(float *dst, float v) {
-  // warp reduction then one shared atomic
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
   if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(dst, v);
@@ -471,87 +561,84 @@ __device__ __forceinline__ void accumulate_shared(float *dst, float v) {
 
 // ------------------------------------------------------------------ adjoint ops
 // Adjoint of node n over its complete samples [A0, A1): adds into the children.
+// [own0, own1) are the samples whose bound gradients this work item owns.
 __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int own1) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
-  NodeRt &me = C.rt[n];
   const bool smooth = P.mode == 1;
   const float tau = P.tau;
   const int NT = blockDim.x;
-  switch (nd.op) {
-    case OP_PGT:
-    case OP_PLT:
-    case OP_TRUE:
-      return;
-    case OP_NOT:
-      for (int q = A0 + threadIdx.x; q < A1; q += NT) add_adj_owned(C, nd.c0, q, -adj_at(C, n, q));
-      return;
-    case OP_AND:
-    case OP_OR: {
-      for (int q = A0 + threadIdx.x; q < A1; q += NT) {
-        const float g = adj_at(C, n, q);
-        const float x = val_at(C, nd.c0, q), y = val_at(C, nd.c1, q);
-        if (!smooth) {
-          const bool left = nd.op == OP_AND ? x <= y : x >= y;
-          add_adj_owned(C, left ? nd.c0 : nd.c1, q, g);
-        } else {
-          const float sg = nd.op == OP_AND ? 1.f : -1.f;
-          float wx, wy;
-          if (isinf(x) && isinf(y)) { wx = 1.f; wy = 0.f; }
-          else {
-            wx = 1.f / (1.f + expf(-sg * tau * (y - x)));
-            wy = 1.f / (1.f + expf(-sg * tau * (x - y)));
-          }
-          add_adj_owned(C, nd.c0, q, g * wx);
-          add_adj_owned(C, nd.c1, q, g * wy);
-        }
-      }
-      return;
-    }
-    case OP_EV:
-    case OP_ALW:
-    case OP_EVSM:
-    case OP_ALWSM:
-    case OP_UNTIL:
-      break;
+  const int op = nd.op;
+  if (op == OP_PGT || op == OP_PLT || op == OP_TRUE) return;
+  const OwnView me = own_view(C, n);
+  const ChildAdj a0 = child_adj(C, nd.c0);
+  if (op == OP_NOT) {
+    for (int q = A0 + threadIdx.x; q < A1; q += NT) a0.add_owned(q, -me.g(q));
+    return;
   }
-  const bool is_until = nd.op == OP_UNTIL;
-  const bool is_sm = nd.op == OP_EVSM || nd.op == OP_ALWSM;
+  if (op == OP_AND || op == OP_OR) {
+    const ChildAdj a1 = child_adj(C, nd.c1);
+    const ChildView x = child_view(C, nd, nd.c0), y = child_view(C, nd, nd.c1);
+    const float sg = op == OP_AND ? 1.f : -1.f;
+    for (int q = A0 + threadIdx.x; q < A1; q += NT) {
+      const float g = me.g(q);
+      const float a = x.get(q), b = y.get(q);
+      if (!smooth) {
+        const bool left = op == OP_AND ? a <= b : a >= b;
+        (left ? a0 : a1).add_owned(q, g);
+      } else {
+        float wx, wy;
+        if (isinf(a) && isinf(b)) { wx = 1.f; wy = 0.f; }
+        else {
+          wx = 1.f / (1.f + expf(-sg * tau * (b - a)));
+          wy = 1.f / (1.f + expf(-sg * tau * (a - b)));
+        }
+        a0.add_owned(q, g * wx);
+        a1.add_owned(q, g * wy);
+      }
+    }
+    return;
+  }
+  const bool is_until = op == OP_UNTIL;
   if (!smooth) {
     // hard: every complete sample sends its adjoint to the recorded source
+    const ChildAdj a1 = is_until ? child_adj(C, nd.c1) : a0;
     for (int qb = A0; qb < A1; qb += NT) {
       const int q = qb + threadIdx.x;
       int key = -1;
       float g = 0.f;
       if (q < A1) {
-        g = adj_at(C, n, q);
-        key = aux_at(C, n, q);
+        g = me.g(q);
+        key = me.src(q);
       }
-      scatter_run(C, nd.c0, nd.c1, key, g, is_until);
+      scatter_run(a0, a1, key, g, is_until);
     }
     return;
   }
-  if (is_sm) {
+  const ChildView cv = child_view(C, nd, nd.c0);
+  if (op == OP_EVSM || op == OP_ALWSM) {
     // smooth-mask window: direct scatter over the support, plus bound gradients
-    const float sgn = nd.op == OP_EVSM ? 1.f : -1.f;
-    const float c = P.mask_c, eps = P.mask_eps;
+    NodeRt &rt = C.rt[n];
+    const float sgn = op == OP_EVSM ? 1.f : -1.f;
+    const float c = P.mask_c, eps = P.mask_eps, fa = rt.fa, fb = rt.fb;
+    const int ia = rt.ia, ib = rt.ib;
     float ga = 0.f, gbv = 0.f;
     for (int qb = A0; qb < A1; qb += NT) {
       const int q = qb + threadIdx.x;
       if (q < A1) {
-        const float g = adj_at(C, n, q);
-        const float y = val_at(C, n, q);
+        const float g = me.g(q);
+        const float y = me.val(q);
         const bool own = q >= own0 && q < own1;
         if (g != 0.f) {
-          for (int i = me.ia; i <= me.ib; ++i) {
+          for (int i = ia; i <= ib; ++i) {
             const float fi = (float)i;
-            const float sa = sigmoidf_(c * (fi - me.fa)), sb = sigmoidf_(c * (fi - me.fb));
+            const float sa = sigmoidf_(c * (fi - fa)), sb = sigmoidf_(c * (fi - fb));
             const float m = sa - sb - eps;
             if (m <= 0.f) continue;
             int src;
-            const float x = child_val(C, nd, nd.c0, q + i, src);
+            const float x = cv.get(q + i, src);
             const float e = expf(sgn * tau * (x - y));
-            add_adj_atomic(C, nd.c0, src, g * m * e);
+            a0.add_atomic(src, g * m * e);
             if (own) {
               ga += g * sgn * P.inv_tau * (-c * sa * (1.f - sa)) * e;
               gbv += g * sgn * P.inv_tau * (c * sb * (1.f - sb)) * e;
@@ -560,29 +647,29 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
         }
       }
     }
-    accumulate_shared(&me.ga, ga);
-    accumulate_shared(&me.gb, gbv);
+    accumulate_shared(&rt.ga, ga);
+    accumulate_shared(&rt.gb, gbv);
     return;
   }
   // smooth Eventually / Always: transposed window over the parent samples,
   // x̄_j += e^{sgn tau x_j} sum_{q in [j-b, j-a] ∩ [A0,A1)} g_q e^{-sgn tau y_q}
   {
-    const float st = (nd.op == OP_EV ? 1.f : -1.f) * tau;
-    const int ia = me.ia, ib = me.ib;
+    const float st = (op == OP_EV ? 1.f : -1.f) * tau;
+    const NodeRt &rt = C.rt[n];
+    const int ia = rt.ia, ib = rt.ib;
     auto elem = [&](int q) {
       LS r;
       if (q < A0 || q >= A1) { r.m = -INFINITY; r.s = 0.f; return r; }
-      const float g = adj_at(C, n, q);
-      r.m = -st * val_at(C, n, q);
-      r.s = g;
+      r.m = -st * me.val(q);
+      r.s = me.g(q);
       return r;
     };
     auto out = [&](int j, LS r) {
       if (r.m == -INFINITY || r.s == 0.f) return;
       int src;
-      const float x = child_val(C, nd, nd.c0, j, src);
+      const float x = cv.get(j, src);
       if (src < 0) return;
-      add_adj_owned(C, nd.c0, src, r.s * expf(st * x + r.m));
+      a0.add_owned(src, r.s * expf(st * x + r.m));
     };
     window_reduce_r<LseM>(P.win_r, A0 + ia, A1 + ib, -ib, -ia, elem, out, C.scratch);
   }
@@ -592,18 +679,19 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
 __device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, float *Pk, long long pstride) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
-  NodeRt &me = C.rt[n];
+  const OwnView me = own_view(C, n);
+  const ChildView cp = child_view(C, nd, nd.c0), cq = child_view(C, nd, nd.c1);
+  const ChildAdj ap = child_adj(C, nd.c0), aq = child_adj(C, nd.c1);
   const float tau = P.tau, itau = P.inv_tau;
-  const int ia = me.ia, ib = me.ib;
+  const int ia = C.rt[n].ia, ib = C.rt[n].ib;
   for (int q = A0 + threadIdx.x; q < A1; q += blockDim.x) {
-    const float g = adj_at(C, n, q);
+    const float g = me.g(q);
     if (g == 0.f) continue;
-    const float U = val_at(C, n, q);
+    const float U = me.val(q);
     float M1 = -INFINITY, S1 = 0.f;
     // forward pass: P_k for k = 0..ib; psi adjoint on the fly
     for (int k = 0; k <= ib; ++k) {
-      int s;
-      const float zp = -tau * child_val(C, nd, nd.c0, q + k, s);
+      const float zp = -tau * cp.get(q + k);
       if (zp != -INFINITY) {
         if (zp > M1) { S1 = fmaf(S1, expf(M1 - zp), 1.f); M1 = zp; }
         else S1 += expf(zp - M1);
@@ -612,34 +700,33 @@ __device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, float 
       Pk[k * pstride] = Pv;
       if (k >= ia) {
         int sq;
-        const float qv = child_val(C, nd, nd.c1, q + k, sq);
+        const float qv = cq.get(q + k, sq);
         float z;
         if (isinf(Pv) || isinf(qv)) z = Pv < qv ? Pv : qv;
         else z = fminf(Pv, qv) - log1pf(expf(-tau * fabsf(Pv - qv))) * itau;
         const float alpha = expf(tau * (z - U));
         const float gq = isinf(qv) ? 0.f : 1.f / (1.f + expf(-tau * (Pv - qv)));
-        add_adj_atomic(C, nd.c1, sq, g * alpha * gq);
+        aq.add_atomic(sq, g * alpha * gq);
       }
     }
-    // backward pass over k: D_k recursion
+    // backward pass over k: D_k = [k>=a] alpha_k beta_k + e^{tau (P_{k+1}-P_k)} D_{k+1}
     float Dn = 0.f, Pnext = 0.f;
     for (int k = ib; k >= 0; --k) {
       const float Pv = Pk[k * pstride];
-      float D = (k < ib && !isinf(Pv)) ? expf(tau * (Pnext - Pv)) * Dn : 0.f;
+      float Dk = (k < ib && !isinf(Pv)) ? expf(tau * (Pnext - Pv)) * Dn : 0.f;
       if (k >= ia) {
-        int sq;
-        const float qv = child_val(C, nd, nd.c1, q + k, sq);
+        const float qv = cq.get(q + k);
         float z;
         if (isinf(Pv) || isinf(qv)) z = Pv < qv ? Pv : qv;
         else z = fminf(Pv, qv) - log1pf(expf(-tau * fabsf(Pv - qv))) * itau;
         const float alpha = expf(tau * (z - U));
         const float beta = isinf(Pv) ? 0.f : 1.f / (1.f + expf(-tau * (qv - Pv)));
-        D += alpha * beta;
+        Dk += alpha * beta;
       }
       int sp;
-      const float pv = child_val(C, nd, nd.c0, q + k, sp);
-      if (!isinf(pv) && !isinf(Pv)) add_adj_atomic(C, nd.c0, sp, g * expf(tau * (Pv - pv)) * D);
-      Dn = D;
+      const float pv = cp.get(q + k, sp);
+      if (!isinf(pv) && !isinf(Pv)) ap.add_atomic(sp, g * expf(tau * (Pv - pv)) * Dk);
+      Dn = Dk;
       Pnext = Pv;
     }
   }
@@ -752,10 +839,12 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
       // backward: root adjoint for [t0, t1), then nodes in reverse order
       {
         NodeRt &r = C.rt[C.root];
+        const Ring ra{r.adj, r.base, r.cap};
         const float *g = A.gout + (size_t)C.b * T;
         for (int q = t0 + threadIdx.x; q < t1; q += NT) {
-          if (q == T - 1) r.padadj += g[q];
-          else r.adj[ring_slot(r, q)] = g[q];
+          const float v = __ldg(g + q);
+          if (q == T - 1) r.padadj += v;
+          else ra.p[ra.slot(q)] = v;
         }
       }
       __syncthreads();
@@ -785,16 +874,14 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
           for (int idx = threadIdx.x; idx < (z1 - s0) * D; idx += NT)
             A.gsig[((size_t)C.b * T + s0) * D + idx] = 0.f;
         }
+        // sum over predicates of (+-w_p) * pbar_p[j]
         for (int idx = threadIdx.x; idx < (j1 - j0) * D; idx += NT) {
           const int j = j0 + idx / D, d = idx - (idx / D) * D;
           float acc = 0.f;
-          for (int n = 0; n < P.n; ++n) {
-            const KNode &nd = P.nd[n];
-            if (nd.op != OP_PGT && nd.op != OP_PLT) continue;
-            const NodeRt &r = C.rt[n];
-            const float w = P.w[nd.w_off + d];
-            const float g = r.adj[ring_slot(r, j)];
-            acc = fmaf(nd.op == OP_PGT ? w : -w, g, acc);
+          for (int k = 0; k < P.npred; ++k) {
+            const NodeRt &r = C.rt[P.pred[k]];
+            const Ring pr{r.adj, r.base, r.cap};
+            acc = fmaf(P.pw[k * STL_MAX_D + d], pr.p[pr.slot(j)], acc);
           }
           A.gsig[((size_t)C.b * T + j) * D + d] = acc;
         }
@@ -814,12 +901,7 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
         const int D = P.D;
         for (int d = threadIdx.x; d < D; d += NT) {
           float acc = 0.f;
-          for (int n = 0; n < P.n; ++n) {
-            const KNode &nd = P.nd[n];
-            if (nd.op != OP_PGT && nd.op != OP_PLT) continue;
-            const float w = P.w[nd.w_off + d];
-            acc = fmaf(nd.op == OP_PGT ? w : -w, C.rt[n].padadj, acc);
-          }
+          for (int k = 0; k < P.npred; ++k) acc = fmaf(P.pw[k * STL_MAX_D + d], C.rt[P.pred[k]].padadj, acc);
           A.gsig[((size_t)C.b * T + (T - 1)) * D + d] = acc;
         }
       }

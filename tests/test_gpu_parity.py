@@ -44,7 +44,8 @@ def per_trace_err(got, ref):
     return d.max()
 
 
-def run(stl, tree, sig, bounds=None, mode="hard", tau=1.0, mask_c=5.0, mask_eps=1e-3, launch=None, gout=None):
+def run(stl, tree, sig, bounds=None, mode="hard", tau=1.0, mask_c=5.0, mask_eps=1e-3, launch=None, gout=None,
+        expect_clean_status=True):
     D = sig.shape[2]
     f = stl.Formula(tree, D=D, n_slots=None if bounds is None else bounds.shape[1])
     if launch:
@@ -60,8 +61,9 @@ def run(stl, tree, sig, bounds=None, mode="hard", tau=1.0, mask_c=5.0, mask_eps=
         gs = gs.cpu().numpy()
         gb = None if gb is None else gb.cpu().numpy()
     torch.cuda.synchronize()
-    from paper_2501_04194_gb300.binding import device_status
-    assert device_status() == 0, "per-trace bounds outside the compiled caps"
+    if expect_clean_status:
+        from paper_2501_04194_gb300.binding import device_status
+        assert device_status() == 0, "per-trace bounds outside the compiled caps"
     return rho, gs, gb
 
 
@@ -203,7 +205,7 @@ def test_bounds_outside_caps_set_the_device_status(stl):
     tree = W.Eventually(0, 10, W.gt([1], 0.0), slot=0)
     sig = W.random_walk(2, 50, 1, seed=0)
     bounds = np.array([[[0, 5]], [[2, 30]]], dtype=np.float32)   # 30 > cap 10
-    run(stl, tree, sig, bounds=bounds)
+    run(stl, tree, sig, bounds=bounds, expect_clean_status=False)
     assert device_status() == -6
     assert device_status() == 0
 
