@@ -138,22 +138,27 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
 
   // A window pass covers threads x R outputs; by default the tile equals one pass and is the
   // largest that keeps every ring in shared memory.
-  const int win_r = maxK >= 64 ? 16 : 8;
+  const int win_r = 15;   // thread-run length of the long windows (odd: conflict-free strides)
   P.win_r = win_r;
   int threads = h->launch.threads ? h->launch.threads : 256;
   int tile = h->launch.tile ? h->launch.tile : threads * win_r;
   tile = std::min(tile, round_up(T, 32));
   tile = std::max(32, round_up(tile, 32));
 
-  auto padded = [](int cap) { return cap + cap / 32 + 1; };
+  auto padded = [](int cap) { return cap; };
+  // window scratch: run aggregates (threads + K/7) and their blocks of 8, 16 bytes each
+  auto scratch_for = [&](int nt) {
+    const int runs = nt + maxK / 7 + 4;
+    return (runs + runs / 8 + 8) * 4;
+  };
   auto layout = [&](int tl, std::vector<int> &space_out, int &smem_words, int &gwords) {
     // scratch for window run aggregates: (threads + maxK/R + 2) entries of up to 16 bytes
-    const int scratch_words = (threads + maxK / win_r + 4) * 4;
+    const int scratch_words = scratch_for(threads);
     const int rt_words = (int)((n * sizeof(NodeRt) + 15) / 16 * 4);
     std::vector<int> words(n);
     for (int i = 0; i < n; ++i) {
       const stl_node &nd = h->nodes[i];
-      const int cap = round_up((long long)tl + hi[i] - lo[i], 32);
+      const int cap = round_up((long long)tl + hi[i] - lo[i], 4);
       int nrings = 1;
       if (bwd) {
         nrings += 1;
@@ -185,7 +190,7 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
     if (!ok) return fail(STL_ERR_UNSUPPORTED, "formula scratch does not fit in shared memory");
     if (gwords == 0 || tile <= 256 || h->launch.tile) break;
     tile = std::max(256, round_up(tile / 2, 32));
-    if (!h->launch.threads) threads = std::max(128, std::min(512, tile / win_r));
+    if (!h->launch.threads) threads = tile >= 256 * win_r ? 256 : 128;
   }
   P.tile = tile;
 
@@ -207,7 +212,7 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
     k.pc = nd.pred_c;
     k.lo = lo[i];
     k.hi = hi[i];
-    k.cap = round_up((long long)tile + hi[i] - lo[i], 32);
+    k.cap = round_up((long long)tile + hi[i] - lo[i], 4);
     k.space = space[i];
     int &off = space[i] ? off_g : off_s;
     const int pw = padded(k.cap);
@@ -232,7 +237,7 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
     for (int d = 0; d < h->D; ++d)
       P.pw[k * STL_MAX_D + d] = nd.op == STL_OP_PRED_GT ? h->w[nd.pred_offset + d] : -h->w[nd.pred_offset + d];
   }
-  const int scratch_words = (threads + maxK / win_r + 4) * 4;
+  const int scratch_words = scratch_for(threads);
   P.scratch_off = round_up(off_s, 4);
   P.scratch_words = scratch_words;
   P.rt_off = P.scratch_off + scratch_words;
@@ -241,7 +246,7 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
 
   // launch shape
   int bps = 0;
-  e = stl_blocks_per_sm(threads, P.smem_words * 4, &bps);
+  e = stl_blocks_per_sm(threads, bwd ? 1 : 0, p.mode == STL_SMOOTH ? 1 : 0, P.smem_words * 4, &bps);
   if (e) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (bps < 1) return fail(STL_ERR_UNSUPPORTED, "kernel does not fit on an SM (%d B shared)", P.smem_words * 4);
   const long long slots = (long long)sms * bps;
@@ -394,8 +399,8 @@ void stl_destroy(stl_handle h) { delete h; }
 
 stl_status stl_set_launch(stl_handle h, const stl_launch *launch) {
   if (!h || !launch) return fail(STL_ERR_INVALID_ARG, "NULL argument");
-  if (launch->threads && launch->threads != 128 && launch->threads != 256 && launch->threads != 512)
-    return fail(STL_ERR_INVALID_ARG, "threads must be 0, 128, 256 or 512");
+  if (launch->threads && launch->threads != 128 && launch->threads != 256)
+    return fail(STL_ERR_INVALID_ARG, "threads must be 0, 128 or 256");
   if (launch->tile < 0 || (launch->tile && launch->tile % 32) || launch->segment < 0)
     return fail(STL_ERR_INVALID_ARG, "tile must be a non-negative multiple of 32; segment >= 0");
   h->launch = *launch;

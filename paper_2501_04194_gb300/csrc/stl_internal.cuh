@@ -19,10 +19,10 @@ struct KNode {
   int w_off;           // predicate weights offset into KProgram::w
   float pc;            // predicate constant
   int lo, hi;          // live offsets relative to the root step [t0, t1): [t0+lo, t1+hi)
-  int cap;             // ring capacity in samples (>= tile + hi - lo, multiple of 32)
-  int val_off;         // word offsets of the rings (shared arena or per-CTA global slice)
-  int adj_off;         // -1 if the node keeps no adjoint ring
-  int aux_off;         // -1 if the node keeps no selected-source ring
+  int cap;             // buffer length in samples (>= tile + hi - lo, multiple of 4)
+  int val_off;         // word offsets of the buffers (shared arena or per-CTA global slice)
+  int adj_off;         // -1 if the node keeps no adjoint buffer
+  int aux_off;         // -1 if the node keeps no selected-source buffer
   int space;           // 0: shared memory, 1: global workspace
 };
 
@@ -41,14 +41,14 @@ struct KProgram {
   long long B;
   int hmax;            // max hi over nodes (backward warm-up)
   int lp;              // common adjoint offset of the predicates
-  int smem_words;      // dynamic shared memory words: rings + scratch + node table
+  int smem_words;      // dynamic shared memory words: buffers + scratch + node table
   int scratch_off;     // word offset of the window scratch in shared memory
   int scratch_words;
   int rt_off;          // word offset of the per-node runtime table
-  int gwords;          // global ring words per CTA
+  int gwords;          // global buffer words per CTA
   long long ut_off;    // word offset of the smooth-until per-thread arrays in the workspace
   int ut_len;          // their length (max taps)
-  int win_r;           // samples per thread-run in the window reductions (8 or 16)
+  int win_r;           // samples per thread-run of the largest windows (15)
   int npred;           // predicate nodes
   int pred[STL_MAX_PRED];
   float pw[STL_MAX_PRED * STL_MAX_D];   // +w (mu - c) or -w (c - mu) per predicate
@@ -64,7 +64,7 @@ struct NodeRt {
   int ia, ib;          // integer window (or smooth-mask support) for this trace
   float fa, fb;        // smooth-mask real bounds for this trace
   int lo, hi, cap;
-  int base;            // ring base of the current step
+  int base;            // unused
   float lastval;       // value at sample T-1 (pad reads)
   int lastaux;         // recorded source at sample T-1
   float padadj;        // adjoint accumulated for sample T-1
@@ -87,7 +87,7 @@ struct LaunchArgs {
 };
 int stl_launch_main(const KProgram &P, const LaunchArgs &A);   // returns a cudaError_t
 int stl_max_smem_optin(int *bytes);
-int stl_blocks_per_sm(int threads, int smem_bytes, int *blocks);
+int stl_blocks_per_sm(int threads, int bwd, int smooth, int smem_bytes, int *blocks);
 int stl_num_sms(int *sms);
 int stl_read_clear_status(void *stream, int *status);
 int stl_status_ptr(int **ptr);

@@ -2,22 +2,25 @@
 // on sm_103a.
 //
 // One CTA owns one work item (trace b, segment [s0, s1)) at a time and walks it in steps of
-// `tile` samples.  Every node of the formula keeps its robustness trace in a ring buffer
-// (shared memory when it fits) covering the live range [t0 + lo, t1 + hi) of the step, so
-// that intermediate traces never touch HBM: only the signal is read and only the root trace
-// (forward) or the signal gradient (backward) is written.
+// `tile` samples.  Every node of the formula keeps its robustness trace in a linear buffer
+// (shared memory when it fits) covering the live range [t0 + lo, t1 + hi) of the step:
+// sample p sits at index p - (t0 + lo).  Between steps the `hi - lo` samples that stay live
+// are moved down by one tile.  Intermediate traces therefore never touch HBM: only the
+// signal is read and only the root trace (forward) or the signal gradient (backward) is
+// written.
 //
 // Temporal operators use a "thread-run" sliding-window decomposition: a thread owns R
 // consecutive outputs; each output window is the combination of a suffix of the thread's
-// first run, a fixed set of whole runs (shared through a small scratch array) and a prefix
-// of a trailing run.  This is O(1) work per output for any window length and works for every
-// associative combine used here:
-//   max/min with the earliest selected sample                (hard Eventually / Always)
-//   composition of clamp functions f_j(v) = min(phi_j, max(psi_j, v))  (hard Until)
-//   (max, scaled sum) pairs of logsumexp                     (smooth windows and adjoints)
+// first run, a fixed set of whole runs (shared through a small scratch array, combined
+// directly or through blocks of 8 runs) and a prefix of a trailing run.  This is O(1) work
+// per output for any window length and works for every associative combine used here:
+//   max/min, with the earliest selected sample when gradients are needed (Eventually, Always)
+//   composition of clamp functions f_j(v) = min(phi_j, max(psi_j, v))       (hard Until)
+//   (max, scaled sum) pairs of logsumexp                  (smooth windows and their adjoint)
 // The hard Until rests on  rho_t = min( min_{k<=a} phi_{t+k},
 //                                       (f_{t+a} o ... o f_{t+b})(-inf) ),
-// which follows from min distributing over max in the definition of Sec. IV-C.
+// which follows from min distributing over max in the definition of Sec. IV-C.  R is odd,
+// so the strided runs of a warp fall in distinct shared-memory banks.
 //
 // Backward launches recompute the forward trace of every node step by step (values run
 // ahead of the root by `hi`), and propagate adjoints in reverse order over the samples whose
@@ -40,33 +43,54 @@ enum {
 };
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int L2B = 8;   // runs per level-2 block in the window middle
 
 // ------------------------------------------------------------------ combine monoids
+struct MaxV {
+  using T = float;
+  static __device__ __forceinline__ T comb(T a, T b) { return b > a ? b : a; }
+};
+struct MinV {
+  using T = float;
+  static __device__ __forceinline__ T comb(T a, T b) { return b < a ? b : a; }
+};
 struct VI { float v; int i; };
-struct MaxM {
+struct MaxI {
   using T = VI;
   static __device__ __forceinline__ T comb(T a, T b) { return b.v > a.v ? b : a; }
 };
-struct MinM {
+struct MinI {
   using T = VI;
   static __device__ __forceinline__ T comb(T a, T b) { return b.v < a.v ? b : a; }
 };
 
-// clamp function v -> min(d, max(c, v)), with the samples that supply c and d.  comb(L, R) is
-// L o R (L covers the earlier samples).  Ties: max keeps L's bound, min keeps d.
+// clamp function v -> min(d, max(c, v)); comb(L, R) = L o R (L covers the earlier samples)
+struct C2 { float c, d; };
+struct ClampV {
+  using T = C2;
+  static __device__ __forceinline__ T comb(T L, T R) {
+    T o;
+    o.c = fminf(L.d, fmaxf(L.c, R.c));
+    o.d = fminf(L.d, fmaxf(L.c, R.d));
+    return o;
+  }
+};
+// with the samples that supply c and d; ties: max keeps L's bound, min keeps d
 struct CC { float c, d; int cs, ds; };
-struct ClampM {
+struct ClampI {
   using T = CC;
   static __device__ __forceinline__ T comb(T L, T R) {
     T o;
-    float m = R.c > L.c ? R.c : L.c;
-    int ms = R.c > L.c ? R.cs : L.cs;
-    bool dl = L.d <= m;
+    const bool rc = R.c > L.c;
+    const float m = rc ? R.c : L.c;
+    const int ms = rc ? R.cs : L.cs;
+    const bool dl = L.d <= m;
     o.c = dl ? L.d : m;
     o.cs = dl ? L.ds : ms;
-    float m2 = R.d > L.c ? R.d : L.c;
-    int ms2 = R.d > L.c ? R.ds : L.cs;
-    bool dl2 = L.d <= m2;
+    const bool rd = R.d > L.c;
+    const float m2 = rd ? R.d : L.c;
+    const int ms2 = rd ? R.ds : L.cs;
+    const bool dl2 = L.d <= m2;
     o.d = dl2 ? L.d : m2;
     o.ds = dl2 ? L.ds : ms2;
     return o;
@@ -88,10 +112,37 @@ struct LseM {
 };
 
 // ------------------------------------------------------------------ window framework
+// middle combine of runagg[l .. r] (inclusive, in order), directly or via level-2 blocks
+template <class M>
+__device__ __forceinline__ typename M::T middle(const typename M::T *ra, const typename M::T *a2, int l, int r,
+                                               bool two_level) {
+  using T = typename M::T;
+  if (!two_level) {
+    T acc = ra[l];
+    for (int j = l + 1; j <= r; ++j) acc = M::comb(acc, ra[j]);
+    return acc;
+  }
+  const int ml = (l + L2B - 1) / L2B;   // first whole block
+  const int mr = (r + 1) / L2B - 1;     // last whole block (ml <= mr since r - l + 1 >= 2*L2B)
+  T acc;
+  int j = l;
+  if (j < ml * L2B) {
+    acc = ra[j++];
+    for (; j < ml * L2B; ++j) acc = M::comb(acc, ra[j]);
+    acc = M::comb(acc, a2[ml]);
+  } else {
+    acc = a2[ml];
+  }
+  for (int m = ml + 1; m <= mr; ++m) acc = M::comb(acc, a2[m]);
+  for (j = (mr + 1) * L2B; j <= r; ++j) acc = M::comb(acc, ra[j]);
+  return acc;
+}
+
 // out(q, reduce_{i in [ia, ib]} elem(q + i)) for q in [q0, q1), combining in sample order.
+// scratch holds the run aggregates (max(NT, nv + nf) entries) then the level-2 aggregates.
 template <class M, int R, class Elem, class Out>
 __device__ __forceinline__ void window_reduce(int q0, int q1, int ia, int ib, const Elem &elem,
-                                              const Out &out, typename M::T *runagg) {
+                                              const Out &out, void *scratch) {
   using T = typename M::T;
   const int K = ib - ia + 1;
   const int tid = threadIdx.x, NT = blockDim.x;
@@ -104,14 +155,15 @@ __device__ __forceinline__ void window_reduce(int q0, int q1, int ia, int ib, co
     }
     return;
   }
+  T *runagg = reinterpret_cast<T *>(scratch);
   const int nf = K / R - 1;           // whole runs strictly inside every window (>= 1)
   const int rho = K - (nf + 1) * R;   // lead of the trailing prefix
+  const bool two = nf >= 3 * L2B;
   for (int p0 = q0; p0 < q1; p0 += NT * R) {
     const int u = p0 + tid * R;
-    // threads that own outputs in this pass; the runs after them come from the extra loop
-    const int nv = min(NT, (q1 - p0 + R - 1) / R);
-    // every thread's first run is also run aggregate number tid; runs past the CTA come
-    // from the extra loop (only when nv + nf > NT)
+    const int nv = min(NT, (q1 - p0 + R - 1) / R);   // threads that own outputs in this pass
+    const int nruns = max(NT, nv + nf);
+    T *agg2 = runagg + nruns;
     T hv[R];
     hv[R - 1] = elem(u + ia + R - 1);
 #pragma unroll
@@ -125,39 +177,48 @@ __device__ __forceinline__ void window_reduce(int q0, int q1, int ia, int ib, co
       runagg[e] = acc;
     }
     __syncthreads();
-    if (tid < nv) {
-    T mid = runagg[tid + 1];
-    for (int j = 2; j <= nf; ++j) mid = M::comb(mid, runagg[tid + j]);
-    const int gs = u + ia + (nf + 1) * R;
-    T acc = mid;
-    bool have = rho > 0;
-    if (have) {
-      acc = elem(gs);
-      for (int e = 1; e < rho; ++e) acc = M::comb(acc, elem(gs + e));
-    }
+    if (two) {
+      const int nb = (nv + nf) / L2B;
+      for (int m = tid; m < nb; m += NT) {
+        T acc = runagg[m * L2B];
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-      if (u + k < q1) {
-        T r = M::comb(hv[k], mid);
-        if (have) r = M::comb(r, acc);
-        out(u + k, r);
+        for (int k = 1; k < L2B; ++k) acc = M::comb(acc, runagg[m * L2B + k]);
+        agg2[m] = acc;
       }
-      if (k + 1 < R) {
-        T e = elem(gs + rho + k);
-        acc = have ? M::comb(acc, e) : e;
-        have = true;
-      }
+      __syncthreads();
     }
+    if (tid < nv) {
+      const T mid = middle<M>(runagg, agg2, tid + 1, tid + nf, two);
+      const int gs = u + ia + (nf + 1) * R;
+      T acc = mid;
+      bool have = rho > 0;
+      if (have) {
+        acc = elem(gs);
+        for (int e = 1; e < rho; ++e) acc = M::comb(acc, elem(gs + e));
+      }
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        if (u + k < q1) {
+          T r = M::comb(hv[k], mid);
+          if (have) r = M::comb(r, acc);
+          out(u + k, r);
+        }
+        if (k + 1 < R) {
+          T e = elem(gs + rho + k);
+          acc = have ? M::comb(acc, e) : e;
+          have = true;
+        }
+      }
     }
     __syncthreads();
   }
 }
 
 template <class M, class Elem, class Out>
-__device__ __forceinline__ void window_reduce_r(int R, int q0, int q1, int ia, int ib, const Elem &elem,
-                                                const Out &out, void *scratch) {
-  if (R == 16) window_reduce<M, 16>(q0, q1, ia, ib, elem, out, (typename M::T *)scratch);
-  else window_reduce<M, 8>(q0, q1, ia, ib, elem, out, (typename M::T *)scratch);
+__device__ __forceinline__ void window_any(int K, int q0, int q1, int ia, int ib, const Elem &elem,
+                                           const Out &out, void *scratch) {
+  if (K >= 64) window_reduce<M, 15>(q0, q1, ia, ib, elem, out, scratch);
+  else window_reduce<M, 7>(q0, q1, ia, ib, elem, out, scratch);
 }
 
 // ------------------------------------------------------------------ interpreter state
@@ -168,43 +229,37 @@ struct Cta {
   const float *sig;
   long long b;
   int T;
-  int t1;              // end of the current root step
+  int t0, t1;          // current root step [t0, t1)
   int root;
   float *out_row;      // forward: out + b*T
 };
 
 __device__ __forceinline__ int frontier(const Cta &C, int n) {
-  int e = C.t1 + C.rt[n].hi;
+  const int e = C.t1 + C.rt[n].hi;
   return e < C.T ? e : C.T;
 }
 
-// Register copies of the ring addressing: built once per operator call, so the inner loops
-// do not re-read node metadata from shared memory.
-struct Ring {
-  float *p;
-  int base, cap;
-  __device__ __forceinline__ int slot(int pos) const {
-    int s = pos - base;
-    s = (s >= cap) ? s - cap : s;
-    s = s < 0 ? 0 : (s >= cap ? cap - 1 : s);
-    return s + (s >> 5);
-  }
-};
-
-// a parent's read access to child values (pads past T-1, clamp at the child's frontier)
+// A parent's read access to child values: a single compare decides the common case; pads,
+// sample T-1 and positions past the child's frontier take the cold path.
 struct ChildView {
-  Ring v;
-  int fmax, T;
+  const float *p;
+  int start, span, T, fmax;
   float lastval, padv;
   bool padc;
   __device__ __forceinline__ float get(int j, int &src) const {
+    if ((unsigned)(j - start) < (unsigned)span) { src = j; return p[j - start]; }
+    return slow(j, src);
+  }
+  __device__ __noinline__ float slow(int j, int &src) const {
     if (j >= T) {
       src = padc ? -1 : T - 1;
       return padc ? padv : lastval;
     }
-    j = j < fmax ? j : fmax;
+    if (j >= T - 1) { src = T - 1; return lastval; }
+    j = j > fmax ? fmax : j;
+    j = j < start ? start : j;
     src = j;
-    return j == T - 1 ? lastval : v.p[v.slot(j)];
+    return p[j - start];
   }
   __device__ __forceinline__ float get(int j) const { int s; return get(j, s); }
 };
@@ -212,40 +267,40 @@ struct ChildView {
 __device__ __forceinline__ ChildView child_view(const Cta &C, const KNode &p, int c) {
   const NodeRt &r = C.rt[c];
   ChildView cv;
-  cv.v.p = r.val;
-  cv.v.base = r.base;
-  cv.v.cap = r.cap;
-  cv.fmax = frontier(C, c) - 1;
+  cv.p = r.val;
+  cv.start = C.t0 + r.lo;
+  const int f = frontier(C, c);
+  const int lim = f < C.T - 1 ? f : C.T - 1;   // fast path: [start, lim)
+  cv.span = lim - cv.start;
   cv.T = C.T;
+  cv.fmax = f - 1;
   cv.lastval = r.lastval;
   cv.padv = p.pad_value;
   cv.padc = p.pad_const != 0;
   return cv;
 }
 
-// a node's own values / sources (sample T-1 lives in per-node cells, because at the end of
-// a trace it can lie below the live range of the last step)
+// a node's own values / sources / adjoint (sample T-1 lives in per-node cells, because at
+// the end of a trace it can lie below the live range of the last step)
 struct OwnView {
-  Ring v;
-  int *aux;
-  float *adj;
-  int T;
-  float lastval;
+  const float *v;
+  const int *aux;
+  const float *adj;
+  int start, T;
+  float lastval, padadj;
   int lastaux;
-  float padadj;
-  __device__ __forceinline__ float val(int q) const { return q >= T - 1 ? lastval : v.p[v.slot(q)]; }
-  __device__ __forceinline__ int src(int q) const { return q >= T - 1 ? lastaux : aux[v.slot(q)]; }
-  __device__ __forceinline__ float g(int q) const { return q >= T - 1 ? padadj : adj[v.slot(q)]; }
+  __device__ __forceinline__ float val(int q) const { return q >= T - 1 ? lastval : v[q - start]; }
+  __device__ __forceinline__ int src(int q) const { return q >= T - 1 ? lastaux : aux[q - start]; }
+  __device__ __forceinline__ float g(int q) const { return q >= T - 1 ? padadj : adj[q - start]; }
 };
 
 __device__ __forceinline__ OwnView own_view(const Cta &C, int n) {
   const NodeRt &r = C.rt[n];
   OwnView o;
-  o.v.p = r.val;
-  o.v.base = r.base;
-  o.v.cap = r.cap;
+  o.v = r.val;
   o.aux = r.aux;
   o.adj = r.adj;
+  o.start = C.t0 + r.lo;
   o.T = C.T;
   o.lastval = r.lastval;
   o.lastaux = r.lastaux;
@@ -253,26 +308,21 @@ __device__ __forceinline__ OwnView own_view(const Cta &C, int n) {
   return o;
 }
 
-// writer of node n's values (and the zeroing of its adjoint slots in backward launches)
+// writer of node n's values (and recorded sources in hard backward launches)
 struct NodeOut {
-  Ring v;
-  float *adj;
+  float *v;
   int *aux;
   float *out_row;
   NodeRt *rt;
-  int T;
+  int start, T;
   __device__ __forceinline__ void put(int q, float val) const {
-    const int s = v.slot(q);
-    v.p[s] = val;
-    if (adj) adj[s] = 0.f;
+    v[q - start] = val;
     if (q == T - 1) rt->lastval = val;
     if (out_row) out_row[q] = val;
   }
   __device__ __forceinline__ void put(int q, float val, int src) const {
-    const int s = v.slot(q);
-    v.p[s] = val;
-    if (adj) adj[s] = 0.f;
-    if (aux) aux[s] = src;
+    v[q - start] = val;
+    if (aux) aux[q - start] = src;
     if (q == T - 1) { rt->lastval = val; rt->lastaux = src; }
     if (out_row) out_row[q] = val;
   }
@@ -281,41 +331,38 @@ struct NodeOut {
 __device__ __forceinline__ NodeOut node_out(const Cta &C, int n) {
   NodeRt &r = C.rt[n];
   NodeOut o;
-  o.v.p = r.val;
-  o.v.base = r.base;
-  o.v.cap = r.cap;
-  o.adj = r.adj;
+  o.v = r.val;
   o.aux = r.aux;
   o.out_row = (n == C.root) ? C.out_row : nullptr;
   o.rt = &r;
+  o.start = C.t0 + r.lo;
   o.T = C.T;
   return o;
 }
 
 // a parent's write access to a child's adjoint (sample T-1 and pads go to the per-node cell)
 struct ChildAdj {
-  Ring a;
+  float *a;
   float *padadj;
-  int T;
+  int start, T;
   __device__ __forceinline__ void add_atomic(int j, float g) const {
     if (j < 0 || g == 0.f) return;
     if (j >= T - 1) atomicAdd(padadj, g);
-    else atomicAdd(&a.p[a.slot(j)], g);
+    else atomicAdd(&a[j - start], g);
   }
   __device__ __forceinline__ void add_owned(int j, float g) const {
     if (j < 0) return;
     if (j >= T - 1) { if (g != 0.f) atomicAdd(padadj, g); }
-    else a.p[a.slot(j)] += g;
+    else a[j - start] += g;
   }
 };
 
 __device__ __forceinline__ ChildAdj child_adj(const Cta &C, int c) {
   NodeRt &r = C.rt[c];
   ChildAdj o;
-  o.a.p = r.adj;
-  o.a.base = r.base;
-  o.a.cap = r.cap;
+  o.a = r.adj;
   o.padadj = &r.padadj;
+  o.start = C.t0 + r.lo;
   o.T = C.T;
   return o;
 }
@@ -338,6 +385,7 @@ __device__ void eval_pred(const Cta &C, int n, int F, int E) {
   }
 }
 
+template <bool SMOOTH>
 __device__ void eval_elementwise(const Cta &C, int n, int F, int E) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
@@ -353,13 +401,12 @@ __device__ void eval_elementwise(const Cta &C, int n, int F, int E) {
     return;
   }
   const ChildView y = child_view(C, nd, nd.c1);
-  const bool smooth = P.mode == 1;
   const float tau = P.tau, itau = P.inv_tau;
   const float sg = op == OP_AND ? 1.f : -1.f;
   for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
     const float a = x.get(q), b = y.get(q);
     float v;
-    if (!smooth) {
+    if constexpr (!SMOOTH) {
       v = op == OP_AND ? (a <= b ? a : b) : (a >= b ? a : b);
     } else {
       // two-term logsumexp min / max: min(x,y) - log1p(e^{-tau|x-y|}) / tau
@@ -373,15 +420,25 @@ __device__ void eval_elementwise(const Cta &C, int n, int F, int E) {
   }
 }
 
-// hard window of node n over its child with offsets [ia, ib] (max or min, earliest sample)
+// hard window of node n over its child with offsets [ia, ib] (max or min)
+template <bool BWD>
 __device__ void eval_hard_window(const Cta &C, int n, int F, int E, int ia, int ib) {
   const KNode &nd = C.P->nd[n];
   const ChildView cv = child_view(C, nd, nd.c0);
   const NodeOut o = node_out(C, n);
-  auto elem = [&](int j) { VI r; r.v = cv.get(j, r.i); return r; };
-  auto out = [&](int q, VI r) { o.put(q, r.v, r.i); };
-  if (nd.op == OP_EV || nd.op == OP_EVSM) window_reduce_r<MaxM>(C.P->win_r, F, E, ia, ib, elem, out, C.scratch);
-  else window_reduce_r<MinM>(C.P->win_r, F, E, ia, ib, elem, out, C.scratch);
+  const bool mx = nd.op == OP_EV || nd.op == OP_EVSM;
+  const int K = ib - ia + 1;
+  if constexpr (BWD) {
+    auto elem = [&](int j) { VI r; r.v = cv.get(j, r.i); return r; };
+    auto out = [&](int q, VI r) { o.put(q, r.v, r.i); };
+    if (mx) window_any<MaxI>(K, F, E, ia, ib, elem, out, C.scratch);
+    else window_any<MinI>(K, F, E, ia, ib, elem, out, C.scratch);
+  } else {
+    auto elem = [&](int j) { return cv.get(j); };
+    auto out = [&](int q, float r) { o.put(q, r); };
+    if (mx) window_any<MaxV>(K, F, E, ia, ib, elem, out, C.scratch);
+    else window_any<MinV>(K, F, E, ia, ib, elem, out, C.scratch);
+  }
 }
 
 // smooth window: (sgn/tau) log sum_i e^{sgn tau x_{q+i}}
@@ -394,46 +451,62 @@ __device__ void eval_smooth_window(const Cta &C, int n, int F, int E, int ia, in
   const float st = sgn * P.tau, sit = sgn * P.inv_tau;
   auto elem = [&](int j) { LS r; r.m = st * cv.get(j); r.s = 1.f; return r; };
   auto out = [&](int q, LS r) { o.put(q, (r.m + logf(r.s)) * sit); };
-  window_reduce_r<LseM>(P.win_r, F, E, ia, ib, elem, out, C.scratch);
+  window_any<LseM>(ib - ia + 1, F, E, ia, ib, elem, out, C.scratch);
 }
 
 // hard Until: pass 1 stores A_q = min_{k in [0,a]} phi_{q+k} (with its sample), pass 2
 // composes the clamps over [a, b] and keeps min(A_q, V_{q+a}) with A winning ties.
+template <bool BWD>
 __device__ void eval_hard_until(const Cta &C, int n, int F, int E, int ia, int ib) {
   const KNode &nd = C.P->nd[n];
   const ChildView cp = child_view(C, nd, nd.c0);
   const ChildView cq = child_view(C, nd, nd.c1);
   const NodeOut o = node_out(C, n);
-  {
-    auto elem = [&](int j) { VI r; int s; r.v = cp.get(j, s); r.i = s < 0 ? -1 : 2 * s; return r; };
-    auto out = [&](int q, VI r) { o.put(q, r.v, r.i); };
-    window_reduce_r<MinM>(C.P->win_r, F, E, 0, ia, elem, out, C.scratch);
-  }
-  __syncthreads();
-  auto elem = [&](int j) {
-    CC r;
-    int sp, sq;
-    const float p = cp.get(j, sp);
-    const float q = cq.get(j, sq);
-    const int ep = sp < 0 ? -1 : 2 * sp, eq = sq < 0 ? -1 : 2 * sq + 1;
-    const bool pl = p <= q;
-    r.c = pl ? p : q;
-    r.cs = pl ? ep : eq;
-    r.d = p;
-    r.ds = ep;
-    return r;
-  };
-  auto out = [&](int q, CC r) {
-    const int s = o.v.slot(q);
-    const float A = o.v.p[s];
-    if (!(A <= r.c)) {
-      o.v.p[s] = r.c;
-      if (o.aux) o.aux[s] = r.cs;
-      if (q == o.T - 1) { o.rt->lastval = r.c; o.rt->lastaux = r.cs; }
-      if (o.out_row) o.out_row[q] = r.c;
+  if constexpr (BWD) {
+    {
+      auto elem = [&](int j) { VI r; int s; r.v = cp.get(j, s); r.i = s < 0 ? -1 : 2 * s; return r; };
+      auto out = [&](int q, VI r) { o.put(q, r.v, r.i); };
+      window_any<MinI>(ia + 1, F, E, 0, ia, elem, out, C.scratch);
     }
-  };
-  window_reduce_r<ClampM>(C.P->win_r, F, E, ia, ib, elem, out, C.scratch);
+    __syncthreads();
+    auto elem = [&](int j) {
+      CC r;
+      int sp, sq;
+      const float p = cp.get(j, sp);
+      const float q = cq.get(j, sq);
+      const int ep = sp < 0 ? -1 : 2 * sp, eq = sq < 0 ? -1 : 2 * sq + 1;
+      const bool pl = p <= q;
+      r.c = pl ? p : q;
+      r.cs = pl ? ep : eq;
+      r.d = p;
+      r.ds = ep;
+      return r;
+    };
+    auto out = [&](int q, CC r) {
+      const float A = o.v[q - o.start];
+      if (!(A <= r.c)) o.put(q, r.c, r.cs);
+    };
+    window_reduce<ClampI, 15>(F, E, ia, ib, elem, out, C.scratch);
+  } else {
+    {
+      auto elem = [&](int j) { return cp.get(j); };
+      auto out = [&](int q, float r) { o.put(q, r); };
+      window_any<MinV>(ia + 1, F, E, 0, ia, elem, out, C.scratch);
+    }
+    __syncthreads();
+    auto elem = [&](int j) {
+      C2 r;
+      const float p = cp.get(j), q = cq.get(j);
+      r.c = fminf(p, q);
+      r.d = p;
+      return r;
+    };
+    auto out = [&](int q, C2 r) {
+      const float A = o.v[q - o.start];
+      if (!(A <= r.c)) o.put(q, r.c);
+    };
+    window_reduce<ClampV, 15>(F, E, ia, ib, elem, out, C.scratch);
+  }
 }
 
 // smooth Until (nested logsumexp, Sec. IV-C with Sec. III-C), one output per thread
@@ -485,13 +558,13 @@ __device__ void eval_smooth_mask(const Cta &C, int n, int F, int E) {
   const ChildView cv = child_view(C, nd, nd.c0);
   const NodeOut o = node_out(C, n);
   const int ia = me.ia, ib = me.ib;
-  const float fa = me.fa, fb = me.fb, mc = P.mask_c, me_eps = P.mask_eps;
+  const float fa = me.fa, fb = me.fb, mc = P.mask_c, meps = P.mask_eps;
   const float sgn = nd.op == OP_EVSM ? 1.f : -1.f;
   const float st = sgn * P.tau;
   for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
     float M = -INFINITY, S = 0.f;
     for (int i = ia; i <= ib; ++i) {
-      const float m = smask((float)i, fa, fb, mc, me_eps);
+      const float m = smask((float)i, fa, fb, mc, meps);
       if (m <= 0.f) continue;
       const float z = st * cv.get(q + i);
       if (z > M) { S = fmaf(S, expf(M - z), m); M = z; }
@@ -501,31 +574,31 @@ __device__ void eval_smooth_mask(const Cta &C, int n, int F, int E) {
   }
 }
 
+template <bool BWD, bool SMOOTH>
 __device__ void eval_node(const Cta &C, int n, int F, int E) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
   const NodeRt &r = C.rt[n];
-  const bool smooth = P.mode == 1;
   switch (nd.op) {
     case OP_PGT:
     case OP_PLT: eval_pred(C, n, F, E); break;
     case OP_TRUE:
     case OP_NOT:
     case OP_AND:
-    case OP_OR: eval_elementwise(C, n, F, E); break;
+    case OP_OR: eval_elementwise<SMOOTH>(C, n, F, E); break;
     case OP_EV:
     case OP_ALW:
-      if (smooth) eval_smooth_window(C, n, F, E, r.ia, r.ib);
-      else eval_hard_window(C, n, F, E, r.ia, r.ib);
+      if constexpr (SMOOTH) eval_smooth_window(C, n, F, E, r.ia, r.ib);
+      else eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
       break;
     case OP_EVSM:
     case OP_ALWSM:
-      if (smooth) eval_smooth_mask(C, n, F, E);
-      else if (r.ia <= r.ib) eval_hard_window(C, n, F, E, r.ia, r.ib);
+      if constexpr (SMOOTH) eval_smooth_mask(C, n, F, E);
+      else if (r.ia <= r.ib) eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
       break;
     case OP_UNTIL:
-      if (smooth) eval_smooth_until(C, n, F, E, r.ia, r.ib);
-      else eval_hard_until(C, n, F, E, r.ia, r.ib);
+      if constexpr (SMOOTH) eval_smooth_until(C, n, F, E, r.ia, r.ib);
+      else eval_hard_until<BWD>(C, n, F, E, r.ia, r.ib);
       break;
   }
 }
@@ -562,10 +635,10 @@ __device__ __forceinline__ void accumulate_shared(float *dst, float v) {
 // ------------------------------------------------------------------ adjoint ops
 // Adjoint of node n over its complete samples [A0, A1): adds into the children.
 // [own0, own1) are the samples whose bound gradients this work item owns.
+template <bool SMOOTH>
 __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int own1) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
-  const bool smooth = P.mode == 1;
   const float tau = P.tau;
   const int NT = blockDim.x;
   const int op = nd.op;
@@ -583,7 +656,7 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
     for (int q = A0 + threadIdx.x; q < A1; q += NT) {
       const float g = me.g(q);
       const float a = x.get(q), b = y.get(q);
-      if (!smooth) {
+      if constexpr (!SMOOTH) {
         const bool left = op == OP_AND ? a <= b : a >= b;
         (left ? a0 : a1).add_owned(q, g);
       } else {
@@ -600,7 +673,7 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
     return;
   }
   const bool is_until = op == OP_UNTIL;
-  if (!smooth) {
+  if constexpr (!SMOOTH) {
     // hard: every complete sample sends its adjoint to the recorded source
     const ChildAdj a1 = is_until ? child_adj(C, nd.c1) : a0;
     for (int qb = A0; qb < A1; qb += NT) {
@@ -614,46 +687,45 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
       scatter_run(a0, a1, key, g, is_until);
     }
     return;
-  }
-  const ChildView cv = child_view(C, nd, nd.c0);
-  if (op == OP_EVSM || op == OP_ALWSM) {
-    // smooth-mask window: direct scatter over the support, plus bound gradients
-    NodeRt &rt = C.rt[n];
-    const float sgn = op == OP_EVSM ? 1.f : -1.f;
-    const float c = P.mask_c, eps = P.mask_eps, fa = rt.fa, fb = rt.fb;
-    const int ia = rt.ia, ib = rt.ib;
-    float ga = 0.f, gbv = 0.f;
-    for (int qb = A0; qb < A1; qb += NT) {
-      const int q = qb + threadIdx.x;
-      if (q < A1) {
-        const float g = me.g(q);
-        const float y = me.val(q);
-        const bool own = q >= own0 && q < own1;
-        if (g != 0.f) {
-          for (int i = ia; i <= ib; ++i) {
-            const float fi = (float)i;
-            const float sa = sigmoidf_(c * (fi - fa)), sb = sigmoidf_(c * (fi - fb));
-            const float m = sa - sb - eps;
-            if (m <= 0.f) continue;
-            int src;
-            const float x = cv.get(q + i, src);
-            const float e = expf(sgn * tau * (x - y));
-            a0.add_atomic(src, g * m * e);
-            if (own) {
-              ga += g * sgn * P.inv_tau * (-c * sa * (1.f - sa)) * e;
-              gbv += g * sgn * P.inv_tau * (c * sb * (1.f - sb)) * e;
+  } else {
+    const ChildView cv = child_view(C, nd, nd.c0);
+    if (op == OP_EVSM || op == OP_ALWSM) {
+      // smooth-mask window: direct scatter over the support, plus bound gradients
+      NodeRt &rt = C.rt[n];
+      const float sgn = op == OP_EVSM ? 1.f : -1.f;
+      const float c = P.mask_c, eps = P.mask_eps, fa = rt.fa, fb = rt.fb;
+      const int ia = rt.ia, ib = rt.ib;
+      float ga = 0.f, gbv = 0.f;
+      for (int qb = A0; qb < A1; qb += NT) {
+        const int q = qb + threadIdx.x;
+        if (q < A1) {
+          const float g = me.g(q);
+          const float y = me.val(q);
+          const bool own = q >= own0 && q < own1;
+          if (g != 0.f) {
+            for (int i = ia; i <= ib; ++i) {
+              const float fi = (float)i;
+              const float sa = sigmoidf_(c * (fi - fa)), sb = sigmoidf_(c * (fi - fb));
+              const float m = sa - sb - eps;
+              if (m <= 0.f) continue;
+              int src;
+              const float x = cv.get(q + i, src);
+              const float e = expf(sgn * tau * (x - y));
+              a0.add_atomic(src, g * m * e);
+              if (own) {
+                ga += g * sgn * P.inv_tau * (-c * sa * (1.f - sa)) * e;
+                gbv += g * sgn * P.inv_tau * (c * sb * (1.f - sb)) * e;
+              }
             }
           }
         }
       }
+      accumulate_shared(&rt.ga, ga);
+      accumulate_shared(&rt.gb, gbv);
+      return;
     }
-    accumulate_shared(&rt.ga, ga);
-    accumulate_shared(&rt.gb, gbv);
-    return;
-  }
-  // smooth Eventually / Always: transposed window over the parent samples,
-  // x̄_j += e^{sgn tau x_j} sum_{q in [j-b, j-a] ∩ [A0,A1)} g_q e^{-sgn tau y_q}
-  {
+    // smooth Eventually / Always: transposed window over the parent samples,
+    // x̄_j += e^{sgn tau x_j} sum_{q in [j-b, j-a] ∩ [A0,A1)} g_q e^{-sgn tau y_q}
     const float st = (op == OP_EV ? 1.f : -1.f) * tau;
     const NodeRt &rt = C.rt[n];
     const int ia = rt.ia, ib = rt.ib;
@@ -671,7 +743,7 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
       if (src < 0) return;
       a0.add_owned(src, r.s * expf(st * x + r.m));
     };
-    window_reduce_r<LseM>(P.win_r, A0 + ia, A1 + ib, -ib, -ia, elem, out, C.scratch);
+    window_any<LseM>(ib - ia + 1, A0 + ia, A1 + ib, -ib, -ia, elem, out, C.scratch);
   }
 }
 
@@ -792,8 +864,63 @@ __device__ void setup_geometry(Cta &C, const float *bounds, float *ws_cta, char 
   __syncthreads();
 }
 
+// zero words [w0, w1) of a buffer (16-byte aligned base; vector stores for the bulk)
+__device__ __forceinline__ void zero_words(float *p, int w0, int w1) {
+  int a = (w0 + 3) & ~3;
+  if (a > w1) a = w1;
+  for (int i = w0 + threadIdx.x; i < a; i += blockDim.x) p[i] = 0.f;
+  const int nv = (w1 - a) >> 2;
+  float4 *p4 = reinterpret_cast<float4 *>(p + a);
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) p4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = a + 4 * nv + threadIdx.x; i < w1; i += blockDim.x) p[i] = 0.f;
+}
+
+// move words [src, src+len) of p to [0, len); the two ranges are disjoint (len <= src)
+__device__ __forceinline__ void move_down(float *p, int src, int len) {
+  if ((src & 3) == 0 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+    const int nv = len >> 2;
+    float4 *d4 = reinterpret_cast<float4 *>(p);
+    const float4 *s4 = reinterpret_cast<const float4 *>(p + src);
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) d4[i] = s4[i];
+    for (int i = 4 * nv + threadIdx.x; i < len; i += blockDim.x) p[i] = p[src + i];
+  } else {
+    for (int i = threadIdx.x; i < len; i += blockDim.x) p[i] = p[src + i];
+  }
+}
+
+// end of a step: keep the live samples [t1 + lo, t1 + hi) at the front of every buffer
+template <bool BWD>
+__device__ void shift_buffers(const Cta &C, int tile) {
+  const KProgram &P = *C.P;
+  int max_span = 0;
+  for (int n = 0; n < P.n; ++n) max_span = max(max_span, C.rt[n].hi - C.rt[n].lo);
+  // rounds of at most `tile` words keep every source chunk disjoint from its destination
+  for (int c0 = 0; c0 < max_span; c0 += tile) {
+    for (int n = 0; n < P.n; ++n) {
+      const NodeRt &r = C.rt[n];
+      const int span = r.hi - r.lo;
+      if (c0 >= span) continue;
+      const int len = min(tile, span - c0);
+      move_down(r.val + c0, tile, len);
+      if (BWD) {
+        move_down(r.adj + c0, tile, len);
+        if (r.aux) move_down(reinterpret_cast<float *>(r.aux) + c0, tile, len);
+      }
+    }
+    __syncthreads();
+  }
+  if (BWD) {
+    // the next step's new samples start with a zero adjoint
+    for (int n = 0; n < P.n; ++n) {
+      const NodeRt &r = C.rt[n];
+      zero_words(r.adj, r.hi - r.lo, r.cap);
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ main kernel
-template <int NT>
+template <int NT, bool BWD, bool SMOOTH>
 __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram P, LaunchArgs A) {
   extern __shared__ float4 smem4[];
   char *smem = reinterpret_cast<char *>(smem4);
@@ -814,88 +941,87 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
     const int sidx = (int)(item % P.segs_per_trace);
     const int s0 = sidx * P.seg;
     const int s1 = (s0 + P.seg < T) ? s0 + P.seg : T;
-    C.out_row = P.bwd ? nullptr : A.out + (size_t)C.b * T;
+    C.out_row = BWD ? nullptr : A.out + (size_t)C.b * T;
     setup_geometry(C, A.bounds, ws_cta, smem, A.status);
-    const int R0 = P.bwd ? (s0 - P.hmax > 0 ? s0 - P.hmax : 0) : s0;
+    if (BWD) {
+      for (int n = 0; n < P.n; ++n) zero_words(C.rt[n].adj, 0, C.rt[n].cap);
+      __syncthreads();
+    }
+    const int R0 = BWD ? (s0 - P.hmax > 0 ? s0 - P.hmax : 0) : s0;
     for (int t0 = R0; t0 < s1; t0 += P.tile) {
       const int t1 = (t0 + P.tile < s1) ? t0 + P.tile : s1;
+      C.t0 = t0;
       C.t1 = t1;
-      if (threadIdx.x < P.n) {
-        NodeRt &r = C.rt[threadIdx.x];
-        const int L = t0 + r.lo;
-        r.base = (L / r.cap) * r.cap;
-      }
-      __syncthreads();
       // forward: values of every node on its new samples
       for (int n = 0; n < P.n; ++n) {
         const NodeRt &r = C.rt[n];
         const int F0 = (t0 == R0) ? R0 + r.lo : t0 + r.hi;
         const int F = F0 < T ? F0 : T;
         const int E = frontier(C, n);
-        if (F < E) eval_node(C, n, F, E);
+        if (F < E) eval_node<BWD, SMOOTH>(C, n, F, E);
         __syncthreads();
       }
-      if (!P.bwd) continue;
-      // backward: root adjoint for [t0, t1), then nodes in reverse order
-      {
-        NodeRt &r = C.rt[C.root];
-        const Ring ra{r.adj, r.base, r.cap};
-        const float *g = A.gout + (size_t)C.b * T;
-        for (int q = t0 + threadIdx.x; q < t1; q += NT) {
-          const float v = __ldg(g + q);
-          if (q == T - 1) r.padadj += v;
-          else ra.p[ra.slot(q)] = v;
-        }
-      }
-      __syncthreads();
-      for (int n = P.n - 1; n >= 0; --n) {
-        const NodeRt &r = C.rt[n];
-        const int A0 = t0 + r.lo;
-        int A1 = t1 + r.lo;
-        A1 = A1 < T - 1 ? A1 : T - 1;
-        if (A0 < A1) {
-          if (P.mode == 1 && P.nd[n].op == OP_UNTIL)
-            adjoint_smooth_until(C, n, A0, A1, ut, ut_stride);
-          else
-            adjoint_node(C, n, A0, A1, s0 + r.lo, s1 + r.lo);
-        }
-        __syncthreads();
-      }
-      // signal gradient for the samples whose predicate adjoints are complete
-      {
-        int j0 = t0 + P.lp, j1 = t1 + P.lp;
-        j0 = j0 > s0 ? j0 : s0;
-        j1 = j1 < s1 ? j1 : s1;
-        j1 = j1 < T - 1 ? j1 : T - 1;
-        const int D = P.D;
-        if (t0 == R0) {
-          // samples before the first predicate offset are read by no predicate: zero gradient
-          const int z1 = j0 < T - 1 ? j0 : T - 1;
-          for (int idx = threadIdx.x; idx < (z1 - s0) * D; idx += NT)
-            A.gsig[((size_t)C.b * T + s0) * D + idx] = 0.f;
-        }
-        // sum over predicates of (+-w_p) * pbar_p[j]
-        for (int idx = threadIdx.x; idx < (j1 - j0) * D; idx += NT) {
-          const int j = j0 + idx / D, d = idx - (idx / D) * D;
-          float acc = 0.f;
-          for (int k = 0; k < P.npred; ++k) {
-            const NodeRt &r = C.rt[P.pred[k]];
-            const Ring pr{r.adj, r.base, r.cap};
-            acc = fmaf(P.pw[k * STL_MAX_D + d], pr.p[pr.slot(j)], acc);
+      if constexpr (BWD) {
+        // root adjoint for [t0, t1), then nodes in reverse order
+        {
+          NodeRt &r = C.rt[C.root];
+          float *ra = r.adj;
+          const int st = t0 + r.lo;
+          const float *g = A.gout + (size_t)C.b * T;
+          for (int q = t0 + threadIdx.x; q < t1; q += NT) {
+            const float v = __ldg(g + q);
+            if (q == T - 1) r.padadj += v;
+            else ra[q - st] = v;
           }
-          A.gsig[((size_t)C.b * T + j) * D + d] = acc;
         }
-      }
-      __syncthreads();
-    }
-    if (P.bwd) {
-      if (s1 == T) {
-        // finish sample T-1 of every node, parents first
+        __syncthreads();
         for (int n = P.n - 1; n >= 0; --n) {
-          if (P.mode == 1 && P.nd[n].op == OP_UNTIL)
+          const NodeRt &r = C.rt[n];
+          const int A0 = t0 + r.lo;
+          int A1 = t1 + r.lo;
+          A1 = A1 < T - 1 ? A1 : T - 1;
+          if (A0 < A1) {
+            if (SMOOTH && P.nd[n].op == OP_UNTIL)
+              adjoint_smooth_until(C, n, A0, A1, ut, ut_stride);
+            else
+              adjoint_node<SMOOTH>(C, n, A0, A1, s0 + r.lo, s1 + r.lo);
+          }
+          __syncthreads();
+        }
+        // signal gradient for the samples whose predicate adjoints are complete
+        {
+          int j0 = t0 + P.lp, j1 = t1 + P.lp;
+          j0 = j0 > s0 ? j0 : s0;
+          j1 = j1 < s1 ? j1 : s1;
+          j1 = j1 < T - 1 ? j1 : T - 1;
+          const int D = P.D;
+          if (t0 == R0) {
+            // samples before the first predicate offset are read by no predicate: zero gradient
+            const int z1 = j0 < T - 1 ? j0 : T - 1;
+            for (int idx = threadIdx.x; idx < (z1 - s0) * D; idx += NT)
+              A.gsig[((size_t)C.b * T + s0) * D + idx] = 0.f;
+          }
+          const int pst = t0 + P.lp;   // every predicate buffer starts at t0 + lp
+          for (int idx = threadIdx.x; idx < (j1 - j0) * D; idx += NT) {
+            const int j = j0 + idx / D, d = idx - (idx / D) * D;
+            float acc = 0.f;
+            for (int k = 0; k < P.npred; ++k)
+              acc = fmaf(P.pw[k * STL_MAX_D + d], C.rt[P.pred[k]].adj[j - pst], acc);
+            A.gsig[((size_t)C.b * T + j) * D + d] = acc;
+          }
+        }
+        __syncthreads();
+      }
+      if (t1 < s1) shift_buffers<BWD>(C, P.tile);
+    }
+    if constexpr (BWD) {
+      if (s1 == T) {
+        // finish sample T-1 of every node, parents first (all reads go to the T-1 cells)
+        for (int n = P.n - 1; n >= 0; --n) {
+          if (SMOOTH && P.nd[n].op == OP_UNTIL)
             adjoint_smooth_until(C, n, T - 1, T, ut, ut_stride);
           else
-            adjoint_node(C, n, T - 1, T, T - 1, T);
+            adjoint_node<SMOOTH>(C, n, T - 1, T, T - 1, T);
           __syncthreads();
         }
         const int D = P.D;
@@ -922,3 +1048,21 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
 }
 
 }  // namespace
+
+// instantiation helpers used by the per-variant translation units
+#define STL_DEFINE_VARIANT(NT, BWD, SM, NAME)                                                     \
+  int stl_launch_##NAME(const KProgram &P, const LaunchArgs &A) {                                \
+    const size_t smem = (size_t)P.smem_words * 4;                                                 \
+    cudaError_t e = cudaFuncSetAttribute(stl_main<NT, BWD, SM>,                                   \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (e != cudaSuccess) return (int)e;                                                          \
+    stl_main<NT, BWD, SM><<<A.grid, NT, smem, (cudaStream_t)A.stream>>>(P, A);                    \
+    return (int)cudaGetLastError();                                                               \
+  }                                                                                               \
+  int stl_occupancy_##NAME(int smem_bytes, int *blocks) {                                         \
+    cudaError_t e = cudaFuncSetAttribute(stl_main<NT, BWD, SM>,                                   \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes); \
+    if (e != cudaSuccess) return (int)e;                                                          \
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, stl_main<NT, BWD, SM>, NT,  \
+                                                              smem_bytes);                        \
+  }

@@ -3,12 +3,22 @@
 
 #include "stl_internal.cuh"
 
-int stl_launch_nt128(const KProgram &P, const LaunchArgs &A);
-int stl_launch_nt256(const KProgram &P, const LaunchArgs &A);
-int stl_launch_nt512(const KProgram &P, const LaunchArgs &A);
-int stl_occupancy_nt128(int smem_bytes, int *blocks);
-int stl_occupancy_nt256(int smem_bytes, int *blocks);
-int stl_occupancy_nt512(int smem_bytes, int *blocks);
+int stl_launch_128_fh(const KProgram &P, const LaunchArgs &A);
+int stl_occupancy_128_fh(int smem_bytes, int *blocks);
+int stl_launch_128_fs(const KProgram &P, const LaunchArgs &A);
+int stl_occupancy_128_fs(int smem_bytes, int *blocks);
+int stl_launch_128_bh(const KProgram &P, const LaunchArgs &A);
+int stl_occupancy_128_bh(int smem_bytes, int *blocks);
+int stl_launch_128_bs(const KProgram &P, const LaunchArgs &A);
+int stl_occupancy_128_bs(int smem_bytes, int *blocks);
+int stl_launch_256_fh(const KProgram &P, const LaunchArgs &A);
+int stl_occupancy_256_fh(int smem_bytes, int *blocks);
+int stl_launch_256_fs(const KProgram &P, const LaunchArgs &A);
+int stl_occupancy_256_fs(int smem_bytes, int *blocks);
+int stl_launch_256_bh(const KProgram &P, const LaunchArgs &A);
+int stl_occupancy_256_bh(int smem_bytes, int *blocks);
+int stl_launch_256_bs(const KProgram &P, const LaunchArgs &A);
+int stl_occupancy_256_bs(int smem_bytes, int *blocks);
 
 namespace {
 __device__ int g_device_status;   // sticky per-device status word (0 = OK)
@@ -19,20 +29,32 @@ int stl_status_ptr(int **ptr) {
 }
 
 int stl_launch_main(const KProgram &P, const LaunchArgs &A) {
-  switch (A.threads) {
-    case 128: return stl_launch_nt128(P, A);
-    case 256: return stl_launch_nt256(P, A);
-    case 512: return stl_launch_nt512(P, A);
-    default: return (int)cudaErrorInvalidValue;
+  const int v = (A.threads == 256 ? 4 : 0) + (P.bwd ? 2 : 0) + (P.mode == 1 ? 1 : 0);
+  if (A.threads != 128 && A.threads != 256) return (int)cudaErrorInvalidValue;
+  switch (v) {
+    case 0: return stl_launch_128_fh(P, A);
+    case 1: return stl_launch_128_fs(P, A);
+    case 2: return stl_launch_128_bh(P, A);
+    case 3: return stl_launch_128_bs(P, A);
+    case 4: return stl_launch_256_fh(P, A);
+    case 5: return stl_launch_256_fs(P, A);
+    case 6: return stl_launch_256_bh(P, A);
+    default: return stl_launch_256_bs(P, A);
   }
 }
 
-int stl_blocks_per_sm(int threads, int smem_bytes, int *blocks) {
-  switch (threads) {
-    case 128: return stl_occupancy_nt128(smem_bytes, blocks);
-    case 256: return stl_occupancy_nt256(smem_bytes, blocks);
-    case 512: return stl_occupancy_nt512(smem_bytes, blocks);
-    default: return (int)cudaErrorInvalidValue;
+int stl_blocks_per_sm(int threads, int bwd, int smooth, int smem_bytes, int *blocks) {
+  const int v = (threads == 256 ? 4 : 0) + (bwd ? 2 : 0) + (smooth ? 1 : 0);
+  if (threads != 128 && threads != 256) return (int)cudaErrorInvalidValue;
+  switch (v) {
+    case 0: return stl_occupancy_128_fh(smem_bytes, blocks);
+    case 1: return stl_occupancy_128_fs(smem_bytes, blocks);
+    case 2: return stl_occupancy_128_bh(smem_bytes, blocks);
+    case 3: return stl_occupancy_128_bs(smem_bytes, blocks);
+    case 4: return stl_occupancy_256_fh(smem_bytes, blocks);
+    case 5: return stl_occupancy_256_fs(smem_bytes, blocks);
+    case 6: return stl_occupancy_256_bh(smem_bytes, blocks);
+    default: return stl_occupancy_256_bs(smem_bytes, blocks);
   }
 }
 
