@@ -138,7 +138,7 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
 
   // A window pass covers threads x R outputs; by default the tile equals one pass and is the
   // largest that keeps every ring in shared memory.
-  const int win_r = 15;   // thread-run length of the long windows (odd: conflict-free strides)
+  const int win_r = 7;    // thread-run length of the windows (odd: conflict-free strides)
   P.win_r = win_r;
   int threads = h->launch.threads ? h->launch.threads : 256;
   int tile = h->launch.tile ? h->launch.tile : threads * win_r;
@@ -161,7 +161,9 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
       const int cap = round_up((long long)tl + hi[i] - lo[i], 4);
       int nrings = 1;
       if (bwd) {
-        nrings += 1;
+        // hard backward: only predicates keep an adjoint (selection walk), temporal nodes
+        // keep their selected samples; smooth backward: every node keeps an adjoint
+        if (p.mode == STL_SMOOTH || is_pred(nd.op)) nrings += 1;
         if (p.mode == STL_HARD && is_temporal(nd.op)) nrings += 1;
       }
       words[i] = nrings * padded(cap);
@@ -190,7 +192,7 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
     if (!ok) return fail(STL_ERR_UNSUPPORTED, "formula scratch does not fit in shared memory");
     if (gwords == 0 || tile <= 256 || h->launch.tile) break;
     tile = std::max(256, round_up(tile / 2, 32));
-    if (!h->launch.threads) threads = tile >= 256 * win_r ? 256 : 128;
+    if (!h->launch.threads) threads = 256;
   }
   P.tile = tile;
 
@@ -220,7 +222,7 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
     k.adj_off = -1;
     k.aux_off = -1;
     if (bwd) {
-      k.adj_off = off; off += pw;
+      if (p.mode == STL_SMOOTH || is_pred(nd.op)) { k.adj_off = off; off += pw; }
       if (p.mode == STL_HARD && is_temporal(nd.op)) { k.aux_off = off; off += pw; }
     }
   }
@@ -399,8 +401,8 @@ void stl_destroy(stl_handle h) { delete h; }
 
 stl_status stl_set_launch(stl_handle h, const stl_launch *launch) {
   if (!h || !launch) return fail(STL_ERR_INVALID_ARG, "NULL argument");
-  if (launch->threads && launch->threads != 128 && launch->threads != 256)
-    return fail(STL_ERR_INVALID_ARG, "threads must be 0, 128 or 256");
+  if (launch->threads && launch->threads != 256 && launch->threads != 512)
+    return fail(STL_ERR_INVALID_ARG, "threads must be 0, 256 or 512");
   if (launch->tile < 0 || (launch->tile && launch->tile % 32) || launch->segment < 0)
     return fail(STL_ERR_INVALID_ARG, "tile must be a non-negative multiple of 32; segment >= 0");
   h->launch = *launch;

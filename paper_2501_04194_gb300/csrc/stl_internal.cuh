@@ -69,6 +69,8 @@ struct NodeRt {
   int lastaux;         // recorded source at sample T-1
   float padadj;        // adjoint accumulated for sample T-1
   float ga, gb;        // smooth-mask bound-gradient accumulators
+  int op, c0, c1;      // copies of the node's operator and children (selection walk)
+  int pred_k;          // index in the predicate list, or -1
 };
 
 // Host-side launch entry points (stl_kernels.cu).

@@ -19,8 +19,8 @@
 //   (max, scaled sum) pairs of logsumexp                  (smooth windows and their adjoint)
 // The hard Until rests on  rho_t = min( min_{k<=a} phi_{t+k},
 //                                       (f_{t+a} o ... o f_{t+b})(-inf) ),
-// which follows from min distributing over max in the definition of Sec. IV-C.  R is odd,
-// so the strided runs of a warp fall in distinct shared-memory banks.
+// which follows from min distributing over max in the definition of Sec. IV-C.  R = 7 is
+// odd, so the strided runs of a warp fall in distinct shared-memory banks.
 //
 // Backward launches recompute the forward trace of every node step by step (values run
 // ahead of the root by `hi`), and propagate adjoints in reverse order over the samples whose
@@ -214,11 +214,13 @@ __device__ __forceinline__ void window_reduce(int q0, int q1, int ia, int ib, co
   }
 }
 
+constexpr int RUN = 7;   // thread-run length (odd)
+
 template <class M, class Elem, class Out>
 __device__ __forceinline__ void window_any(int K, int q0, int q1, int ia, int ib, const Elem &elem,
                                            const Out &out, void *scratch) {
-  if (K >= 64) window_reduce<M, 15>(q0, q1, ia, ib, elem, out, scratch);
-  else window_reduce<M, 7>(q0, q1, ia, ib, elem, out, scratch);
+  (void)K;
+  window_reduce<M, RUN>(q0, q1, ia, ib, elem, out, scratch);
 }
 
 // ------------------------------------------------------------------ interpreter state
@@ -486,7 +488,7 @@ __device__ void eval_hard_until(const Cta &C, int n, int F, int E, int ia, int i
       const float A = o.v[q - o.start];
       if (!(A <= r.c)) o.put(q, r.c, r.cs);
     };
-    window_reduce<ClampI, 15>(F, E, ia, ib, elem, out, C.scratch);
+    window_reduce<ClampI, RUN>(F, E, ia, ib, elem, out, C.scratch);
   } else {
     {
       auto elem = [&](int j) { return cp.get(j); };
@@ -505,7 +507,7 @@ __device__ void eval_hard_until(const Cta &C, int n, int F, int E, int ia, int i
       const float A = o.v[q - o.start];
       if (!(A <= r.c)) o.put(q, r.c);
     };
-    window_reduce<ClampV, 15>(F, E, ia, ib, elem, out, C.scratch);
+    window_reduce<ClampV, RUN>(F, E, ia, ib, elem, out, C.scratch);
   }
 }
 
@@ -859,7 +861,12 @@ __device__ void setup_geometry(Cta &C, const float *bounds, float *ws_cta, char 
       r.padadj = 0.f;
       r.ga = r.gb = 0.f;
       r.base = 0;
+      r.op = nd.op;
+      r.c0 = nd.c0;
+      r.c1 = nd.c1;
+      r.pred_k = -1;
     }
+    for (int k = 0; k < P.npred; ++k) C.rt[P.pred[k]].pred_k = k;
   }
   __syncthreads();
 }
@@ -903,7 +910,7 @@ __device__ void shift_buffers(const Cta &C, int tile) {
       const int len = min(tile, span - c0);
       move_down(r.val + c0, tile, len);
       if (BWD) {
-        move_down(r.adj + c0, tile, len);
+        if (r.adj) move_down(r.adj + c0, tile, len);
         if (r.aux) move_down(reinterpret_cast<float *>(r.aux) + c0, tile, len);
       }
     }
@@ -913,9 +920,66 @@ __device__ void shift_buffers(const Cta &C, int tile) {
     // the next step's new samples start with a zero adjoint
     for (int n = 0; n < P.n; ++n) {
       const NodeRt &r = C.rt[n];
-      zero_words(r.adj, r.hi - r.lo, r.cap);
+      if (r.adj) zero_words(r.adj, r.hi - r.lo, r.cap);
     }
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ hard-mode selection walk
+// In hard semantics the gradient of a root sample flows to exactly one predicate sample (or
+// nowhere): follow the recorded selections down the tree and deposit the root gradient
+// there.  One pass over the root samples of the step, with no barrier between levels;
+// internal nodes keep no adjoint at all.
+__device__ void hard_walk(const Cta &C, const float *gout_row, int t0, int t1) {
+  const NodeRt *rt = C.rt;
+  const int T = C.T;
+  const int lane = threadIdx.x & 31;
+  for (int qb = t0; qb < t1; qb += blockDim.x) {
+    const int q = qb + threadIdx.x;
+    int pk = -1, j = -1;
+    float g = 0.f;
+    if (q < t1) {
+      g = __ldg(gout_row + q);
+      int n = C.root;
+      j = q;
+      for (;;) {
+        const NodeRt &r = rt[n];
+        const int op = r.op;
+        if (op == OP_PGT || op == OP_PLT) { pk = r.pred_k; break; }
+        if (op == OP_TRUE) break;
+        if (op == OP_NOT) { g = -g; n = r.c0; continue; }
+        if (op == OP_AND || op == OP_OR) {
+          const NodeRt &a = rt[r.c0], &b = rt[r.c1];
+          const float x = j >= T - 1 ? a.lastval : a.val[j - (C.t0 + a.lo)];
+          const float y = j >= T - 1 ? b.lastval : b.val[j - (C.t0 + b.lo)];
+          const bool left = op == OP_AND ? x <= y : x >= y;
+          n = left ? r.c0 : r.c1;
+          continue;
+        }
+        const int key = j >= T - 1 ? r.lastaux : r.aux[j - (C.t0 + r.lo)];
+        if (key < 0) break;
+        if (op == OP_UNTIL) { n = (key & 1) ? r.c1 : r.c0; j = key >> 1; }
+        else { n = r.c0; j = key; }
+      }
+    }
+    // runs of consecutive lanes ending on the same predicate sample add once
+    const int pj = __shfl_up_sync(FULL, j, 1), pp = __shfl_up_sync(FULL, pk, 1);
+    const bool head = lane == 0 || pj != j || pp != pk;
+    const unsigned heads = __ballot_sync(FULL, head);
+    const int rid = __popc(heads & (0xffffffffu >> (31 - lane)));
+    float s = g;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const float sv = __shfl_down_sync(FULL, s, off);
+      const int rv = __shfl_down_sync(FULL, rid, off);
+      if (lane + off < 32 && rv == rid) s += sv;
+    }
+    if (head && pk >= 0 && s != 0.f) {
+      const NodeRt &r = rt[C.P->pred[pk]];
+      if (j >= T - 1) atomicAdd(const_cast<float *>(&r.padadj), s);
+      else atomicAdd(&r.adj[j - (C.t0 + r.lo)], s);
+    }
   }
 }
 
@@ -944,7 +1008,8 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
     C.out_row = BWD ? nullptr : A.out + (size_t)C.b * T;
     setup_geometry(C, A.bounds, ws_cta, smem, A.status);
     if (BWD) {
-      for (int n = 0; n < P.n; ++n) zero_words(C.rt[n].adj, 0, C.rt[n].cap);
+      for (int n = 0; n < P.n; ++n)
+        if (C.rt[n].adj) zero_words(C.rt[n].adj, 0, C.rt[n].cap);
       __syncthreads();
     }
     const int R0 = BWD ? (s0 - P.hmax > 0 ? s0 - P.hmax : 0) : s0;
@@ -961,7 +1026,11 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
         if (F < E) eval_node<BWD, SMOOTH>(C, n, F, E);
         __syncthreads();
       }
-      if constexpr (BWD) {
+      if constexpr (BWD && !SMOOTH) {
+        hard_walk(C, A.gout + (size_t)C.b * T, t0, t1);
+        __syncthreads();
+      }
+      if constexpr (BWD && SMOOTH) {
         // root adjoint for [t0, t1), then nodes in reverse order
         {
           NodeRt &r = C.rt[C.root];
@@ -988,6 +1057,8 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
           }
           __syncthreads();
         }
+      }
+      if constexpr (BWD) {
         // signal gradient for the samples whose predicate adjoints are complete
         {
           int j0 = t0 + P.lp, j1 = t1 + P.lp;
@@ -1016,8 +1087,9 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
     }
     if constexpr (BWD) {
       if (s1 == T) {
-        // finish sample T-1 of every node, parents first (all reads go to the T-1 cells)
-        for (int n = P.n - 1; n >= 0; --n) {
+        // finish sample T-1 of every node, parents first (all reads go to the T-1 cells);
+        // the hard walk already delivered sample T-1 of every root sample
+        for (int n = P.n - 1; SMOOTH && n >= 0; --n) {
           if (SMOOTH && P.nd[n].op == OP_UNTIL)
             adjoint_smooth_until(C, n, T - 1, T, ut, ut_stride);
           else

@@ -3,14 +3,14 @@
 
 #include "stl_internal.cuh"
 
-int stl_launch_128_fh(const KProgram &P, const LaunchArgs &A);
-int stl_occupancy_128_fh(int smem_bytes, int *blocks);
-int stl_launch_128_fs(const KProgram &P, const LaunchArgs &A);
-int stl_occupancy_128_fs(int smem_bytes, int *blocks);
-int stl_launch_128_bh(const KProgram &P, const LaunchArgs &A);
-int stl_occupancy_128_bh(int smem_bytes, int *blocks);
-int stl_launch_128_bs(const KProgram &P, const LaunchArgs &A);
-int stl_occupancy_128_bs(int smem_bytes, int *blocks);
+int stl_launch_512_fh(const KProgram &P, const LaunchArgs &A);
+int stl_occupancy_512_fh(int smem_bytes, int *blocks);
+int stl_launch_512_fs(const KProgram &P, const LaunchArgs &A);
+int stl_occupancy_512_fs(int smem_bytes, int *blocks);
+int stl_launch_512_bh(const KProgram &P, const LaunchArgs &A);
+int stl_occupancy_512_bh(int smem_bytes, int *blocks);
+int stl_launch_512_bs(const KProgram &P, const LaunchArgs &A);
+int stl_occupancy_512_bs(int smem_bytes, int *blocks);
 int stl_launch_256_fh(const KProgram &P, const LaunchArgs &A);
 int stl_occupancy_256_fh(int smem_bytes, int *blocks);
 int stl_launch_256_fs(const KProgram &P, const LaunchArgs &A);
@@ -30,12 +30,12 @@ int stl_status_ptr(int **ptr) {
 
 int stl_launch_main(const KProgram &P, const LaunchArgs &A) {
   const int v = (A.threads == 256 ? 4 : 0) + (P.bwd ? 2 : 0) + (P.mode == 1 ? 1 : 0);
-  if (A.threads != 128 && A.threads != 256) return (int)cudaErrorInvalidValue;
+  if (A.threads != 512 && A.threads != 256) return (int)cudaErrorInvalidValue;
   switch (v) {
-    case 0: return stl_launch_128_fh(P, A);
-    case 1: return stl_launch_128_fs(P, A);
-    case 2: return stl_launch_128_bh(P, A);
-    case 3: return stl_launch_128_bs(P, A);
+    case 0: return stl_launch_512_fh(P, A);
+    case 1: return stl_launch_512_fs(P, A);
+    case 2: return stl_launch_512_bh(P, A);
+    case 3: return stl_launch_512_bs(P, A);
     case 4: return stl_launch_256_fh(P, A);
     case 5: return stl_launch_256_fs(P, A);
     case 6: return stl_launch_256_bh(P, A);
@@ -45,12 +45,12 @@ int stl_launch_main(const KProgram &P, const LaunchArgs &A) {
 
 int stl_blocks_per_sm(int threads, int bwd, int smooth, int smem_bytes, int *blocks) {
   const int v = (threads == 256 ? 4 : 0) + (bwd ? 2 : 0) + (smooth ? 1 : 0);
-  if (threads != 128 && threads != 256) return (int)cudaErrorInvalidValue;
+  if (threads != 512 && threads != 256) return (int)cudaErrorInvalidValue;
   switch (v) {
-    case 0: return stl_occupancy_128_fh(smem_bytes, blocks);
-    case 1: return stl_occupancy_128_fs(smem_bytes, blocks);
-    case 2: return stl_occupancy_128_bh(smem_bytes, blocks);
-    case 3: return stl_occupancy_128_bs(smem_bytes, blocks);
+    case 0: return stl_occupancy_512_fh(smem_bytes, blocks);
+    case 1: return stl_occupancy_512_fs(smem_bytes, blocks);
+    case 2: return stl_occupancy_512_bh(smem_bytes, blocks);
+    case 3: return stl_occupancy_512_bs(smem_bytes, blocks);
     case 4: return stl_occupancy_256_fh(smem_bytes, blocks);
     case 5: return stl_occupancy_256_fs(smem_bytes, blocks);
     case 6: return stl_occupancy_256_bh(smem_bytes, blocks);

@@ -103,7 +103,7 @@ def test_config1_small_batch(stl, mode, tau, T):
     check(stl, W.config1_formula(), sig, mode=mode, tau=tau)
 
 
-@pytest.mark.parametrize("launch", [dict(tile=256), dict(tile=256, segment=700), dict(tile=512, threads=128),
+@pytest.mark.parametrize("launch", [dict(tile=256), dict(tile=256, segment=700), dict(tile=512, threads=256),
                                     dict(tile=1024, threads=256, segment=1500)])
 @pytest.mark.parametrize("mode,tau", [("hard", 1.0), ("smooth", 10.0)])
 def test_config1_streaming_and_segments(stl, launch, mode, tau):
