@@ -370,15 +370,51 @@ __device__ __forceinline__ ChildAdj child_adj(const Cta &C, int c) {
 }
 
 // ------------------------------------------------------------------ forward ops
+// Predicates: a thread first issues the loads of all its samples of the step (BATCH samples
+// at a time, independent loads in flight), then evaluates and stores them.
+constexpr int BATCH = 8;
+
+template <int DD>
+__device__ __forceinline__ void pred_batch(const float *__restrict__ xs, const float *w, bool gt, float pc,
+                                           const NodeOut &out, int F, int E) {
+  const int NT = blockDim.x;
+  for (int base = F + threadIdx.x; base < E; base += NT * BATCH) {
+    float x[BATCH][DD];
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const int q = base + k * NT;
+#pragma unroll
+      for (int d = 0; d < DD; ++d) x[k][d] = q < E ? __ldg(xs + (size_t)q * DD + d) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const int q = base + k * NT;
+      if (q < E) {
+        float s = __fmul_rn(w[0], x[k][0]);
+#pragma unroll
+        for (int d = 1; d < DD; ++d) s = __fadd_rn(s, __fmul_rn(w[d], x[k][d]));
+        out.put(q, gt ? __fsub_rn(s, pc) : __fsub_rn(pc, s));
+      }
+    }
+  }
+}
+
 __device__ void eval_pred(const Cta &C, int n, int F, int E) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
   const int D = P.D;
   const float *w = P.w + nd.w_off;
-  const float *xs = C.sig + (size_t)C.b * (size_t)C.T * D;
+  const float *__restrict__ xs = C.sig + (size_t)C.b * (size_t)C.T * D;
   const NodeOut out = node_out(C, n);
   const bool gt = nd.op == OP_PGT;
   const float pc = nd.pc;
+  switch (D) {
+    case 1: pred_batch<1>(xs, w, gt, pc, out, F, E); return;
+    case 2: pred_batch<2>(xs, w, gt, pc, out, F, E); return;
+    case 3: pred_batch<3>(xs, w, gt, pc, out, F, E); return;
+    case 4: pred_batch<4>(xs, w, gt, pc, out, F, E); return;
+    default: break;
+  }
   for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
     const float *x = xs + (size_t)q * D;
     float s = __fmul_rn(w[0], __ldg(x));
@@ -931,54 +967,66 @@ __device__ void shift_buffers(const Cta &C, int tile) {
 // nowhere): follow the recorded selections down the tree and deposit the root gradient
 // there.  One pass over the root samples of the step, with no barrier between levels;
 // internal nodes keep no adjoint at all.
-__device__ void hard_walk(const Cta &C, const float *gout_row, int t0, int t1) {
+__device__ void hard_walk(const Cta &C, const float *__restrict__ gout_row, int t0, int t1) {
   const NodeRt *rt = C.rt;
   const int T = C.T;
   const int lane = threadIdx.x & 31;
-  for (int qb = t0; qb < t1; qb += blockDim.x) {
-    const int q = qb + threadIdx.x;
-    int pk = -1, j = -1;
-    float g = 0.f;
-    if (q < t1) {
-      g = __ldg(gout_row + q);
-      int n = C.root;
-      j = q;
-      for (;;) {
-        const NodeRt &r = rt[n];
-        const int op = r.op;
-        if (op == OP_PGT || op == OP_PLT) { pk = r.pred_k; break; }
-        if (op == OP_TRUE) break;
-        if (op == OP_NOT) { g = -g; n = r.c0; continue; }
-        if (op == OP_AND || op == OP_OR) {
-          const NodeRt &a = rt[r.c0], &b = rt[r.c1];
-          const float x = j >= T - 1 ? a.lastval : a.val[j - (C.t0 + a.lo)];
-          const float y = j >= T - 1 ? b.lastval : b.val[j - (C.t0 + b.lo)];
-          const bool left = op == OP_AND ? x <= y : x >= y;
-          n = left ? r.c0 : r.c1;
-          continue;
-        }
-        const int key = j >= T - 1 ? r.lastaux : r.aux[j - (C.t0 + r.lo)];
-        if (key < 0) break;
-        if (op == OP_UNTIL) { n = (key & 1) ? r.c1 : r.c0; j = key >> 1; }
-        else { n = r.c0; j = key; }
-      }
-    }
-    // runs of consecutive lanes ending on the same predicate sample add once
-    const int pj = __shfl_up_sync(FULL, j, 1), pp = __shfl_up_sync(FULL, pk, 1);
-    const bool head = lane == 0 || pj != j || pp != pk;
-    const unsigned heads = __ballot_sync(FULL, head);
-    const int rid = __popc(heads & (0xffffffffu >> (31 - lane)));
-    float s = g;
+  const int NT = blockDim.x;
+  for (int qb0 = t0; qb0 < t1; qb0 += NT * BATCH) {
+    float gb[BATCH];
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const float sv = __shfl_down_sync(FULL, s, off);
-      const int rv = __shfl_down_sync(FULL, rid, off);
-      if (lane + off < 32 && rv == rid) s += sv;
+    for (int k = 0; k < BATCH; ++k) {
+      const int q = qb0 + k * NT + threadIdx.x;
+      gb[k] = q < t1 ? __ldg(gout_row + q) : 0.f;
     }
-    if (head && pk >= 0 && s != 0.f) {
-      const NodeRt &r = rt[C.P->pred[pk]];
-      if (j >= T - 1) atomicAdd(const_cast<float *>(&r.padadj), s);
-      else atomicAdd(&r.adj[j - (C.t0 + r.lo)], s);
+#pragma unroll 1
+    for (int k = 0; k < BATCH; ++k) {
+      const int qb = qb0 + k * NT;
+      if (qb >= t1) break;
+      const int q = qb + threadIdx.x;
+      int pk = -1, j = -1;
+      float g = 0.f;
+      if (q < t1) {
+        g = gb[k];
+        int n = C.root;
+        j = q;
+        for (;;) {
+          const NodeRt &r = rt[n];
+          const int op = r.op;
+          if (op == OP_PGT || op == OP_PLT) { pk = r.pred_k; break; }
+          if (op == OP_TRUE) break;
+          if (op == OP_NOT) { g = -g; n = r.c0; continue; }
+          if (op == OP_AND || op == OP_OR) {
+            const NodeRt &a = rt[r.c0], &b = rt[r.c1];
+            const float x = j >= T - 1 ? a.lastval : a.val[j - (C.t0 + a.lo)];
+            const float y = j >= T - 1 ? b.lastval : b.val[j - (C.t0 + b.lo)];
+            const bool left = op == OP_AND ? x <= y : x >= y;
+            n = left ? r.c0 : r.c1;
+            continue;
+          }
+          const int key = j >= T - 1 ? r.lastaux : r.aux[j - (C.t0 + r.lo)];
+          if (key < 0) break;
+          if (op == OP_UNTIL) { n = (key & 1) ? r.c1 : r.c0; j = key >> 1; }
+          else { n = r.c0; j = key; }
+        }
+      }
+      // runs of consecutive lanes ending on the same predicate sample add once
+      const int pj = __shfl_up_sync(FULL, j, 1), pp = __shfl_up_sync(FULL, pk, 1);
+      const bool head = lane == 0 || pj != j || pp != pk;
+      const unsigned heads = __ballot_sync(FULL, head);
+      const int rid = __popc(heads & (0xffffffffu >> (31 - lane)));
+      float s = g;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const float sv = __shfl_down_sync(FULL, s, off);
+        const int rv = __shfl_down_sync(FULL, rid, off);
+        if (lane + off < 32 && rv == rid) s += sv;
+      }
+      if (head && pk >= 0 && s != 0.f) {
+        const NodeRt &r = rt[C.P->pred[pk]];
+        if (j >= T - 1) atomicAdd(const_cast<float *>(&r.padadj), s);
+        else atomicAdd(&r.adj[j - (C.t0 + r.lo)], s);
+      }
     }
   }
 }
