@@ -158,6 +158,29 @@ STL_API stl_status stl_robustness_backward(stl_handle h, const float *sig, int64
                                    const float *grad_out, float *grad_sig, float *grad_bounds,
                                    void *workspace, size_t workspace_bytes, void *stream);
 
+/* Bytes of the static device scratch behind stl_robustness_backward_noalloc (32 MiB). */
+#define STL_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+
+/* Allocation-free backward (the paper has no counterpart; this serves callers that cannot
+ * allocate device memory at all while they run -- a host application that forbids device
+ * allocation after start-up, a real-time loop with frozen memory, or a plugin whose framework
+ * owns every device byte).  Same arguments and results as stl_robustness_backward, without
+ * the workspace: the scratch comes from a file-scope static __device__ array of
+ * STL_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until exit.
+ *   - The first call on a device looks up that array's device address (cudaGetSymbolAddress,
+ *     with the device current); make that first call before any stream capture.
+ *   - If the scratch cannot hold what all resident CTAs would need, fewer CTAs are launched
+ *     (they walk all work items); if a single CTA needs more, the call returns
+ *     STL_ERR_WORKSPACE with a message stating both sizes.
+ *   - Every call shares the one array and leaves its last contents there; the kernels write
+ *     each scratch word before reading it.  Calls whose kernels overlap on the GPU (different
+ *     streams, no ordering) race on the array and give undefined results: serialise them.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
+STL_API stl_status stl_robustness_backward_noalloc(stl_handle h, const float *sig, int64_t B, int64_t T,
+                                                   const float *bounds, const stl_params *p,
+                                                   const float *grad_out, float *grad_sig,
+                                                   float *grad_bounds, void *stream);
+
 /* Sticky device-side status of the current device (STL_OK or STL_ERR_DEVICE_CHECK);
  * synchronises `stream`, then reads and clears the word. */
 STL_API stl_status stl_get_device_status(void *stream, int32_t *status);

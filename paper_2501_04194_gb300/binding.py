@@ -199,6 +199,19 @@ def robustness_backward_raw(f: Formula, sig_ptr, B, T, bounds_ptr, p: StlParams,
                                          gsig_ptr, gb_ptr, ws_ptr, ws_bytes, stream))
 
 
+def robustness_backward_noalloc_raw(f: Formula, sig_ptr, B, T, bounds_ptr, p: StlParams, gout_ptr, gsig_ptr,
+                                    gb_ptr, stream):
+    """stl_robustness_backward_noalloc: the backward without a caller-provided workspace (its
+    scratch is the library's static device array; see include/stl.h)."""
+    lib = load()
+    fn = lib.stl_robustness_backward_noalloc
+    if fn.argtypes is None:
+        vp, i64 = ctypes.c_void_p, ctypes.c_int64
+        fn.argtypes = [vp, vp, i64, i64, vp, ctypes.POINTER(StlParams), vp, vp, vp, vp]
+        fn.restype = ctypes.c_int32
+    check(fn(f.handle, sig_ptr, B, T, bounds_ptr, ctypes.byref(p), gout_ptr, gsig_ptr, gb_ptr, stream))
+
+
 def device_status(stream=None) -> int:
     st = ctypes.c_int32()
     check(load().stl_get_device_status(stream, ctypes.byref(st)))

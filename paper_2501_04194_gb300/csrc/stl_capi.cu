@@ -508,3 +508,31 @@ stl_status stl_get_device_status(void *stream, int32_t *status) {
 }
 
 }  // extern "C"
+
+// Internal: plan a backward launch whose workspace must fit in `capacity_bytes`; the grid is
+// reduced (items are then walked by fewer resident CTAs) until it fits.  Used by the
+// allocation-free entry point in stl_noalloc.cu.
+stl_status stl_internal_plan_backward_capped(stl_handle h, const float *sig, int64_t B, int64_t T,
+                                             const float *bounds, const stl_params *p, size_t capacity_bytes,
+                                             KProgram *prog, int *grid, int *threads, size_t *ws_bytes) {
+  stl_status s = check_call(h, sig, B, T, bounds, p);
+  if (s) return s;
+  Plan pl;
+  s = make_plan(h, B, T, *p, true, pl);
+  if (s) return s;
+  const size_t per_cta_words = (size_t)pl.P.gwords + (size_t)pl.P.ut_len * pl.threads;
+  if (per_cta_words * 4 > capacity_bytes)
+    return fail(STL_ERR_WORKSPACE, "one CTA needs %zu bytes of scratch, the static scratch holds %zu",
+                per_cta_words * 4, capacity_bytes);
+  int g = pl.grid;
+  const size_t fit = capacity_bytes / (per_cta_words * 4 > 0 ? per_cta_words * 4 : 1);
+  if (per_cta_words > 0 && (size_t)g > fit) g = (int)fit;
+  pl.P.ut_off = (long long)pl.P.gwords * g;
+  *prog = pl.P;
+  *grid = g;
+  *threads = pl.threads;
+  *ws_bytes = per_cta_words * 4 * (size_t)g;
+  return STL_OK;
+}
+
+stl_status stl_internal_fail(stl_status st, const char *msg) { return fail(st, "%s", msg); }

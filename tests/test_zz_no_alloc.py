@@ -1,0 +1,67 @@
+"""The allocation-free backward (stl_robustness_backward_noalloc) against the regular one.
+
+It exists for callers that may not allocate device memory while running; it takes no
+workspace and keeps its scratch in the library's static device array.  Called through the C
+ABI twice in a row (the array keeps the previous call's contents), on cases whose backward
+needs scratch (smooth Until), one large enough that fewer CTAs are launched, a hard case that
+needs none, and one whose single-CTA scratch exceeds the array (a clear error, no launch).
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def stl():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2501_04194_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def rel_err(a, b):
+    a = a.double().cpu().numpy().reshape(a.shape[0], -1)
+    b = b.double().cpu().numpy().reshape(b.shape[0], -1)
+    scale = np.maximum(np.abs(b).max(axis=1, keepdims=True), 1e-30)
+    return float((np.abs(a - b) / scale).max())
+
+
+def noalloc_backward(stl, f, x, g, p):
+    from paper_2501_04194_gb300.binding import robustness_backward_noalloc_raw
+    B, T, D = x.shape
+    gs = torch.full((B, T, D), float("nan"), device=x.device)
+    stream = torch.cuda.current_stream().cuda_stream
+    robustness_backward_noalloc_raw(f, x.data_ptr(), B, T, None, p, g.data_ptr(), gs.data_ptr(), None, stream)
+    return gs
+
+
+@pytest.mark.parametrize("mode,B,T", [("smooth", 8, 2000), ("smooth", 2048, 3000), ("hard", 64, 5000)])
+def test_noalloc_matches_workspace_backward(stl, mode, B, T):
+    f = stl.Formula(W.config1_formula(), D=3)
+    p = stl.params(mode, tau=10.0)
+    x = torch.from_numpy(W.random_walk(B, T, 3, seed=7)).cuda()
+    for call in range(2):
+        g = torch.from_numpy(np.random.default_rng(call).normal(size=(B, T)).astype(np.float32)).cuda()
+        ref, _ = stl.robustness_backward(f, x, g, p=p)
+        got = noalloc_backward(stl, f, x, g, p)
+        torch.cuda.synchronize()
+        assert torch.isfinite(got).all()
+        assert rel_err(got, ref) <= GRAD_TOL
+
+
+def test_noalloc_rejects_scratch_beyond_its_array(stl):
+    from paper_2501_04194_gb300.binding import StlError
+    f = stl.Formula(W.Until(0, 40000, W.gt([1.0], 0.0), W.lt([1.0], 0.5)), D=1)
+    p = stl.params("smooth", tau=5.0)
+    x = torch.zeros((2, 41000, 1), device="cuda")
+    g = torch.zeros((2, 41000), device="cuda")
+    with pytest.raises(StlError) as ei:
+        noalloc_backward(stl, f, x, g, p)
+    assert ei.value.status == -4 and "static scratch" in str(ei.value)
