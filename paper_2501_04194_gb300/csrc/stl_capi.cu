@@ -140,7 +140,9 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
   // largest that keeps every ring in shared memory.
   const int win_r = 7;    // thread-run length of the windows (odd: conflict-free strides)
   P.win_r = win_r;
-  int threads = h->launch.threads ? h->launch.threads : 256;
+  // measured defaults: forward launches prefer several 256-thread CTAs per SM, backward
+  // launches (larger per-sample state) one or two 512-thread CTAs
+  int threads = h->launch.threads ? h->launch.threads : (bwd ? 512 : 256);
   int tile = h->launch.tile ? h->launch.tile : threads * win_r;
   tile = std::min(tile, round_up(T, 32));
   tile = std::max(32, round_up(tile, 32));
@@ -192,7 +194,7 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
     if (!ok) return fail(STL_ERR_UNSUPPORTED, "formula scratch does not fit in shared memory");
     if (gwords == 0 || tile <= 256 || h->launch.tile) break;
     tile = std::max(256, round_up(tile / 2, 32));
-    if (!h->launch.threads) threads = 256;
+    if (!h->launch.threads && tile < 512 * win_r) threads = 256;
   }
   P.tile = tile;
 

@@ -1031,6 +1031,49 @@ __device__ void hard_walk(const Cta &C, const float *__restrict__ gout_row, int 
   }
 }
 
+// ------------------------------------------------------------------ signal gradient
+// grad_sig[j, d] = sum_k pw[k][d] * pbar_k[j] for the complete samples [j0, j1); every
+// predicate buffer starts at sample pst.  One thread per sample, D unrolled when small.
+template <int DD>
+__device__ __forceinline__ void signal_gradient_d(const KProgram &P, float *const *padj, float *gs, int pst, int j0,
+                                                  int j1) {
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    float acc[DD];
+#pragma unroll
+    for (int d = 0; d < DD; ++d) acc[d] = 0.f;
+    for (int k = 0; k < P.npred; ++k) {
+      const float a = padj[k][j - pst];
+#pragma unroll
+      for (int d = 0; d < DD; ++d) acc[d] = fmaf(P.pw[k * STL_MAX_D + d], a, acc[d]);
+    }
+    float *o = gs + (size_t)j * DD;
+#pragma unroll
+    for (int d = 0; d < DD; ++d) o[d] = acc[d];
+  }
+}
+
+__device__ void signal_gradient(const Cta &C, float *gs, int pst, int j0, int j1) {
+  const KProgram &P = *C.P;
+  float **padj = reinterpret_cast<float **>(C.scratch);   // free between node evaluations
+  if (threadIdx.x < P.npred) padj[threadIdx.x] = C.rt[P.pred[threadIdx.x]].adj;
+  __syncthreads();
+  switch (P.D) {
+    case 1: signal_gradient_d<1>(P, padj, gs, pst, j0, j1); break;
+    case 2: signal_gradient_d<2>(P, padj, gs, pst, j0, j1); break;
+    case 3: signal_gradient_d<3>(P, padj, gs, pst, j0, j1); break;
+    case 4: signal_gradient_d<4>(P, padj, gs, pst, j0, j1); break;
+    default: {
+      const int D = P.D;
+      for (int idx = threadIdx.x; idx < (j1 - j0) * D; idx += blockDim.x) {
+        const int j = j0 + idx / D, d = idx - (idx / D) * D;
+        float acc = 0.f;
+        for (int k = 0; k < P.npred; ++k) acc = fmaf(P.pw[k * STL_MAX_D + d], padj[k][j - pst], acc);
+        gs[(size_t)j * D + d] = acc;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ main kernel
 template <int NT, bool BWD, bool SMOOTH>
 __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram P, LaunchArgs A) {
@@ -1120,14 +1163,7 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
             for (int idx = threadIdx.x; idx < (z1 - s0) * D; idx += NT)
               A.gsig[((size_t)C.b * T + s0) * D + idx] = 0.f;
           }
-          const int pst = t0 + P.lp;   // every predicate buffer starts at t0 + lp
-          for (int idx = threadIdx.x; idx < (j1 - j0) * D; idx += NT) {
-            const int j = j0 + idx / D, d = idx - (idx / D) * D;
-            float acc = 0.f;
-            for (int k = 0; k < P.npred; ++k)
-              acc = fmaf(P.pw[k * STL_MAX_D + d], C.rt[P.pred[k]].adj[j - pst], acc);
-            A.gsig[((size_t)C.b * T + j) * D + d] = acc;
-          }
+          signal_gradient(C, A.gsig + (size_t)C.b * T * D, t0 + P.lp, j0, j1);
         }
         __syncthreads();
       }
