@@ -26,7 +26,7 @@
  * [B, n_slots, 2] holding (a, b) in time steps.  All array arguments are DEVICE pointers.
  *
  * Ownership and execution.  The caller owns every pointer; the library never allocates or
- * frees device memory on the call path (only stl_compile_set, which uploads the program
+ * frees device memory on the call path (only stl_set_prepare, which uploads the program
  * table of a formula set, allocates).  Calls are asynchronous on the given cudaStream_t
  * (passed as void*; NULL = the legacy default stream) and fully overwrite their outputs.
  * Argument errors are detected on the host before anything is launched and returned as a
@@ -180,6 +180,46 @@ STL_API stl_status stl_robustness_backward_noalloc(stl_handle h, const float *si
                                                    const float *bounds, const stl_params *p,
                                                    const float *grad_out, float *grad_sig,
                                                    float *grad_bounds, void *stream);
+
+/* ---- Ragged batches: many traces of different lengths and formulas in one launch ----
+ * Traces are packed one after another: trace i has offsets[i+1] - offsets[i] samples starting
+ * at row offsets[i] of sig [sum T, D]; outputs are packed the same way.  formula_id[i] selects
+ * the formula of trace i in the set; order (optional, may be NULL) lists the traces in the
+ * order CTAs take them from a shared work counter (longest first balances the tail).
+ * Interval semantics per trace as in stl_robustness (Sec. IV-E: intervals are data). */
+
+/* Group compiled formulas (same D) for ragged launches.  The set refers to the handles, which
+ * must outlive it. */
+STL_API stl_status stl_set_create(const stl_handle *formulas, int32_t n_formulas, stl_set_handle *out);
+STL_API void stl_set_destroy(stl_set_handle s);
+
+/* Prepare the set for up to n_traces traces of at most T_max samples with semantics p, for
+ * the forward (backward = 0) or backward (1) launch: plans every formula and uploads the
+ * per-formula program table to the device (the only allocation of the ragged path, freed by
+ * stl_set_destroy).  Returns the workspace size the matching ragged calls need.  Host-side,
+ * synchronous; call it before any stream capture. */
+STL_API stl_status stl_set_prepare(stl_set_handle s, int64_t n_traces, int64_t T_max, const stl_params *p,
+                                   int32_t backward, size_t *workspace_bytes);
+
+/* Robustness of a ragged batch in ONE launch (capturable in a CUDA graph: no allocation, no
+ * synchronisation).  p must equal the prepared params.  Device arrays:
+ *   sig [sum T, D], offsets int64 [n_traces+1], formula_id int32 [n_traces],
+ *   order int32 [n_traces] or NULL, bounds [n_traces, n_slots, 2] or NULL, out [sum T].
+ * Traces with a formula_id outside the set, an order entry out of range or more than T_max
+ * samples are skipped and set the device status word (stl_get_device_status). */
+STL_API stl_status stl_robustness_ragged(stl_set_handle s, const float *sig, const int64_t *offsets,
+                                         const int32_t *formula_id, const int32_t *order, int64_t n_traces,
+                                         const float *bounds, int32_t n_slots, const stl_params *p, float *out,
+                                         void *workspace, size_t workspace_bytes, void *stream);
+
+/* Gradient of sum(grad_out * rho) for a ragged batch (grad_out [sum T], grad_sig [sum T, D],
+ * grad_bounds [n_traces, n_slots, 2] or NULL), one launch, same rules as above. */
+STL_API stl_status stl_robustness_ragged_backward(stl_set_handle s, const float *sig, const int64_t *offsets,
+                                                  const int32_t *formula_id, const int32_t *order,
+                                                  int64_t n_traces, const float *bounds, int32_t n_slots,
+                                                  const stl_params *p, const float *grad_out, float *grad_sig,
+                                                  float *grad_bounds, void *workspace, size_t workspace_bytes,
+                                                  void *stream);
 
 /* Sticky device-side status of the current device (STL_OK or STL_ERR_DEVICE_CHECK);
  * synchronises `stream`, then reads and clears the word. */

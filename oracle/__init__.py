@@ -204,5 +204,30 @@ def robustness_ragged_multi(formulas, formula_id, sig, offsets, bounds=None, **k
     return out
 
 
-__all__ = ["build", "robustness", "robustness_grad", "robustness_ragged_multi", "num_threads",
+def robustness_grad_ragged_multi(formulas, formula_id, sig, offsets, grad_out, bounds=None, **kw):
+    """Ragged gradient where trace i follows ``formulas[formula_id[i]]``: packed float64 signal
+    gradient [sum T, D] and bounds gradient [n, n_slots, 2] (or None)."""
+    offsets = np.asarray(offsets, dtype=np.int64)
+    formula_id = np.asarray(formula_id)
+    gout = np.asarray(grad_out, dtype=np.float64)
+    gsig = np.zeros((int(offsets[-1]), sig.shape[1]), dtype=np.float64)
+    gb = None if bounds is None else np.zeros((len(formula_id), bounds.shape[1], 2), dtype=np.float64)
+    for k, f in enumerate(formulas):
+        idx = np.nonzero(formula_id == k)[0]
+        if len(idx) == 0:
+            continue
+        sub_off = np.zeros(len(idx) + 1, dtype=np.int64)
+        sub_off[1:] = np.cumsum(offsets[idx + 1] - offsets[idx])
+        sub_sig = np.concatenate([sig[offsets[i]:offsets[i + 1]] for i in idx])
+        sub_g = np.concatenate([gout[offsets[i]:offsets[i + 1]] for i in idx])
+        sub_b = None if bounds is None else bounds[idx]
+        g, b = robustness_grad(f, sub_sig, sub_g, bounds=sub_b, offsets=sub_off, **kw)
+        for j, i in enumerate(idx):
+            gsig[offsets[i]:offsets[i + 1]] = g[sub_off[j]:sub_off[j + 1]]
+            if gb is not None and b is not None:
+                gb[i] = b[j]
+    return gsig, gb
+
+
+__all__ = ["robustness_grad_ragged_multi", "build", "robustness", "robustness_grad", "robustness_ragged_multi", "num_threads",
            "HARD", "SMOOTH", "math"]

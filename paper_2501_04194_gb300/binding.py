@@ -212,6 +212,68 @@ def robustness_backward_noalloc_raw(f: Formula, sig_ptr, B, T, bounds_ptr, p: St
     check(fn(f.handle, sig_ptr, B, T, bounds_ptr, ctypes.byref(p), gout_ptr, gsig_ptr, gb_ptr, stream))
 
 
+class FormulaSet:
+    """Formulas of the same D evaluated together by the ragged launch (stl_set_* in stl.h)."""
+
+    def __init__(self, formulas):
+        lib = load()
+        self._setup(lib)
+        self.formulas = list(formulas)   # keep the handles alive
+        arr = (ctypes.c_void_p * len(self.formulas))(*[f.handle.value for f in self.formulas])
+        h = ctypes.c_void_p()
+        check(lib.stl_set_create(arr, len(self.formulas), ctypes.byref(h)))
+        self._h = h
+        self.D = self.formulas[0].D
+        self.n_slots = max(f.n_slots for f in self.formulas)
+
+    @staticmethod
+    def _setup(lib):
+        if getattr(lib, "_set_ready", False):
+            return
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        lib.stl_set_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
+        lib.stl_set_create.restype = i32
+        lib.stl_set_destroy.argtypes = [vp]
+        lib.stl_set_destroy.restype = None
+        lib.stl_set_prepare.argtypes = [vp, i64, i64, ctypes.POINTER(StlParams), i32, ctypes.POINTER(sz)]
+        lib.stl_set_prepare.restype = i32
+        lib.stl_robustness_ragged.argtypes = [vp, vp, vp, vp, vp, i64, vp, i32, ctypes.POINTER(StlParams), vp, vp,
+                                              sz, vp]
+        lib.stl_robustness_ragged.restype = i32
+        lib.stl_robustness_ragged_backward.argtypes = [vp, vp, vp, vp, vp, i64, vp, i32, ctypes.POINTER(StlParams),
+                                                       vp, vp, vp, vp, sz, vp]
+        lib.stl_robustness_ragged_backward.restype = i32
+        lib._set_ready = True
+
+    @property
+    def handle(self):
+        return self._h
+
+    def prepare(self, n_traces, T_max, p: StlParams, backward=False) -> int:
+        n = ctypes.c_size_t()
+        check(load().stl_set_prepare(self._h, n_traces, T_max, ctypes.byref(p), int(backward), ctypes.byref(n)))
+        return int(n.value)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.stl_set_destroy(h)
+            self._h = None
+
+
+def robustness_ragged_raw(s: FormulaSet, sig_ptr, off_ptr, fid_ptr, order_ptr, n, bounds_ptr, p, out_ptr, ws_ptr,
+                          ws_bytes, stream):
+    check(load().stl_robustness_ragged(s.handle, sig_ptr, off_ptr, fid_ptr, order_ptr, n, bounds_ptr, s.n_slots,
+                                       ctypes.byref(p), out_ptr, ws_ptr, ws_bytes, stream))
+
+
+def robustness_ragged_backward_raw(s: FormulaSet, sig_ptr, off_ptr, fid_ptr, order_ptr, n, bounds_ptr, p, gout_ptr,
+                                   gsig_ptr, gb_ptr, ws_ptr, ws_bytes, stream):
+    check(load().stl_robustness_ragged_backward(s.handle, sig_ptr, off_ptr, fid_ptr, order_ptr, n, bounds_ptr,
+                                                s.n_slots, ctypes.byref(p), gout_ptr, gsig_ptr, gb_ptr, ws_ptr,
+                                                ws_bytes, stream))
+
+
 def device_status(stream=None) -> int:
     st = ctypes.c_int32()
     check(load().stl_get_device_status(stream, ctypes.byref(st)))

@@ -60,6 +60,24 @@ struct stl_program {
   stl_launch launch{};
 };
 
+// A group of formulas evaluated together in one ragged launch.  The device table holds one
+// program per formula for the prepared (T_max, semantics, direction).
+struct SetState {
+  bool ready = false;
+  long long T_max = 0;
+  stl_params p{};
+  KProgram *dtable = nullptr;   // device copy (allocated at prepare time)
+  int threads = 256, grid = 1, smem_words = 0, gwords = 0, ut_len = 0;
+  long long ut_off = 0;
+  size_t ws_bytes = 0;
+};
+
+struct stl_program_set {
+  std::vector<stl_program *> formulas;
+  int D = 0, n_slots = 0;
+  SetState st[2];   // [forward, backward]
+};
+
 namespace {
 
 struct Plan {
@@ -84,7 +102,8 @@ int window_lo(const stl_node &nd) {
 }
 
 // Compute node geometry, ring layout and launch shape for one call.
-stl_status make_plan(const stl_program *h, long long B, long long T, const stl_params &p, bool bwd, Plan &pl) {
+stl_status make_plan(const stl_program *h, long long B, long long T, const stl_params &p, bool bwd, Plan &pl,
+                     int force_threads = 0) {
   KProgram &P = pl.P;
   std::memset(&P, 0, sizeof P);
   const int n = (int)h->nodes.size();
@@ -135,6 +154,7 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
   if (e) return cuda_fail(e, "cudaDeviceGetAttribute(multiprocessors)");
   e = stl_max_smem_optin(&max_smem);
   if (e) return cuda_fail(e, "cudaDeviceGetAttribute(max shared memory)");
+  max_smem -= 1024;   // the kernel's own static shared variables
 
   // A window pass covers threads x R outputs; by default the tile equals one pass and is the
   // largest that keeps every ring in shared memory.
@@ -142,7 +162,7 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
   P.win_r = win_r;
   // measured defaults: forward launches prefer several 256-thread CTAs per SM, backward
   // launches (larger per-sample state) one or two 512-thread CTAs
-  int threads = h->launch.threads ? h->launch.threads : (bwd ? 512 : 256);
+  int threads = force_threads ? force_threads : h->launch.threads ? h->launch.threads : (bwd ? 512 : 256);
   int tile = h->launch.tile ? h->launch.tile : threads * win_r;
   tile = std::min(tile, round_up(T, 32));
   tile = std::max(32, round_up(tile, 32));
@@ -194,7 +214,7 @@ stl_status make_plan(const stl_program *h, long long B, long long T, const stl_p
     if (!ok) return fail(STL_ERR_UNSUPPORTED, "formula scratch does not fit in shared memory");
     if (gwords == 0 || tile <= 256 || h->launch.tile) break;
     tile = std::max(256, round_up(tile / 2, 32));
-    if (!h->launch.threads && tile < 512 * win_r) threads = 256;
+    if (!force_threads && !h->launch.threads && tile < 512 * win_r) threads = 256;
   }
   P.tile = tile;
 
@@ -538,3 +558,181 @@ stl_status stl_internal_plan_backward_capped(stl_handle h, const float *sig, int
 }
 
 stl_status stl_internal_fail(stl_status st, const char *msg) { return fail(st, "%s", msg); }
+
+// ------------------------------------------------------------------ formula sets (ragged)
+extern "C" {
+
+stl_status stl_set_create(const stl_handle *formulas, int32_t n_formulas, stl_set_handle *out) {
+  if (!out) return fail(STL_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!formulas || n_formulas < 1 || n_formulas > 1024)
+    return fail(STL_ERR_INVALID_ARG, "n_formulas must be in [1, 1024]");
+  stl_program_set *s = new (std::nothrow) stl_program_set;
+  if (!s) return fail(STL_ERR_INVALID_ARG, "out of host memory");
+  for (int i = 0; i < n_formulas; ++i) {
+    if (!formulas[i]) { delete s; return fail(STL_ERR_INVALID_ARG, "formula %d is NULL", i); }
+    if (i && formulas[i]->D != formulas[0]->D) {
+      delete s;
+      return fail(STL_ERR_INVALID_ARG, "formula %d has D=%d, formula 0 has D=%d", i, formulas[i]->D,
+                  formulas[0]->D);
+    }
+    s->formulas.push_back(formulas[i]);
+    s->n_slots = std::max(s->n_slots, formulas[i]->n_slots);
+  }
+  s->D = formulas[0]->D;
+  *out = s;
+  return STL_OK;
+}
+
+void stl_set_destroy(stl_set_handle s) {
+  if (!s) return;
+  for (auto &st : s->st)
+    if (st.dtable) cudaFree(st.dtable);
+  delete s;
+}
+
+stl_status stl_set_prepare(stl_set_handle s, int64_t n_traces, int64_t T_max, const stl_params *p,
+                           int32_t backward, size_t *workspace_bytes) {
+  if (!s || !p || !workspace_bytes) return fail(STL_ERR_INVALID_ARG, "NULL argument");
+  if (n_traces < 1 || T_max < 1 || T_max > (1LL << 30)) return fail(STL_ERR_INVALID_ARG, "need n_traces >= 1 and T_max in [1, 2^30]");
+  SetState &st = s->st[backward ? 1 : 0];
+  const int nf = (int)s->formulas.size();
+  std::vector<KProgram> progs(nf);
+  const int threads = backward ? 512 : 256;
+  int smem = 0, gwords = 0, ut_len = 0;
+  for (int k = 0; k < nf; ++k) {
+    stl_status e = check_params(s->formulas[k], p);
+    if (e) return e;
+    Plan pl;
+    e = make_plan(s->formulas[k], n_traces, T_max, *p, backward != 0, pl, threads);
+    if (e) return e;
+    pl.P.n_slots = s->n_slots;          // one bounds array for the whole set
+    pl.P.seg = (int)T_max;
+    pl.P.segs_per_trace = 1;
+    progs[k] = pl.P;
+    smem = std::max(smem, pl.P.smem_words);
+    gwords = std::max(gwords, pl.P.gwords);
+    ut_len = std::max(ut_len, pl.P.ut_len);
+  }
+  int sms = 0, bps = 0;
+  int e = stl_num_sms(&sms);
+  if (e) return cuda_fail(e, "cudaDeviceGetAttribute(multiprocessors)");
+  e = stl_blocks_per_sm(threads, backward ? 1 : 0, p->mode == STL_SMOOTH ? 1 : 0, smem * 4, &bps);
+  if (e) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (bps < 1) return fail(STL_ERR_UNSUPPORTED, "kernel does not fit on an SM (%d B shared)", smem * 4);
+  const long long grid = std::max(1LL, std::min((long long)sms * bps, (long long)n_traces));
+  for (auto &P : progs) {
+    P.smem_words = smem;   // every program sees the launch's shared arena
+  }
+  if (!st.dtable) {
+    cudaError_t ce = cudaMalloc((void **)&st.dtable, sizeof(KProgram) * 1024);
+    if (ce != cudaSuccess) { st.dtable = nullptr; return cuda_fail((int)ce, "cudaMalloc(program table)"); }
+  }
+  cudaError_t ce = cudaMemcpy(st.dtable, progs.data(), sizeof(KProgram) * nf, cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) return cuda_fail((int)ce, "cudaMemcpy(program table)");
+  st.threads = threads;
+  st.grid = (int)grid;
+  st.smem_words = smem;
+  st.gwords = gwords;
+  st.ut_len = ut_len;
+  // workspace: [work counter: 256 B][global node buffers grid x gwords][smooth-until arrays]
+  st.ut_off = (long long)gwords * grid;
+  st.ws_bytes = 256 + ((size_t)gwords * grid + (size_t)ut_len * grid * threads) * 4;
+  st.T_max = T_max;
+  st.p = *p;
+  st.ready = true;
+  *workspace_bytes = st.ws_bytes;
+  return STL_OK;
+}
+
+static stl_status ragged_common(stl_set_handle s, const float *sig, const int64_t *offsets, const int32_t *fid,
+                                int64_t n_traces, const float *bounds, int32_t n_slots, const stl_params *p,
+                                bool bwd, void *workspace, size_t workspace_bytes, SetState **out) {
+  if (!s || !p) return fail(STL_ERR_INVALID_ARG, "NULL argument");
+  SetState &st = s->st[bwd ? 1 : 0];
+  if (!st.ready) return fail(STL_ERR_INVALID_ARG, "call stl_set_prepare for this direction first");
+  if (std::memcmp(&st.p, p, sizeof *p) != 0) return fail(STL_ERR_INVALID_ARG, "params differ from stl_set_prepare");
+  if (n_traces < 0) return fail(STL_ERR_INVALID_ARG, "n_traces must be >= 0");
+  if (n_traces > 0 && (!sig || !offsets || !fid)) return fail(STL_ERR_INVALID_ARG, "signal / offsets / formula_id is NULL");
+  if (n_slots != s->n_slots) return fail(STL_ERR_INVALID_ARG, "bounds must have %d slots", s->n_slots);
+  if (s->n_slots > 0 && n_traces > 0 && !bounds) return fail(STL_ERR_INVALID_ARG, "bounds is NULL");
+  if (!workspace || workspace_bytes < st.ws_bytes)
+    return fail(STL_ERR_WORKSPACE, "workspace of %zu bytes needed", st.ws_bytes);
+  *out = &st;
+  return STL_OK;
+}
+
+static stl_status ragged_launch(stl_set_handle s, SetState &st, const float *sig, const int64_t *offsets,
+                                const int32_t *fid, const int32_t *order, int64_t n_traces, const float *bounds,
+                                const float *gout, float *out, float *gsig, float *gbounds, void *workspace,
+                                void *stream) {
+  if (n_traces == 0) return STL_OK;
+  cudaError_t ce = cudaMemsetAsync(workspace, 0, 256, (cudaStream_t)stream);
+  if (ce != cudaSuccess) return cuda_fail((int)ce, "cudaMemsetAsync(work counter)");
+  LaunchArgs A{};
+  int e0 = stl_status_ptr(&A.status);
+  if (e0) return cuda_fail(e0, "cudaGetSymbolAddress(status)");
+  A.sig = sig;
+  A.bounds = s->n_slots ? bounds : nullptr;
+  A.gout = gout;
+  A.out = out;
+  A.gsig = gsig;
+  A.gbounds = s->n_slots ? gbounds : nullptr;
+  A.ws = (float *)((char *)workspace + 256);
+  A.table = st.dtable;
+  A.offsets = (const long long *)offsets;
+  A.fid = fid;
+  A.order = order;
+  A.counter = (unsigned long long *)workspace;
+  A.n_traces = n_traces;
+  A.n_formulas = (int)s->formulas.size();
+  A.T_max = st.T_max;
+  A.gwords = st.gwords;
+  A.ut_len = st.ut_len;
+  A.ut_off = st.ut_off;
+  A.grid = (int)std::min<long long>(st.grid, n_traces);
+  A.threads = st.threads;
+  A.stream = stream;
+  KProgram dummy;
+  std::memset(&dummy, 0, sizeof dummy);
+  dummy.smem_words = st.smem_words;
+  dummy.bwd = gsig ? 1 : 0;
+  dummy.mode = st.p.mode;
+  int e = stl_launch_main(dummy, A);
+  if (e) return cuda_fail(e, "ragged kernel launch");
+  return STL_OK;
+}
+
+stl_status stl_robustness_ragged(stl_set_handle s, const float *sig, const int64_t *offsets, const int32_t *formula_id,
+                                 const int32_t *order, int64_t n_traces, const float *bounds, int32_t n_slots,
+                                 const stl_params *p, float *out, void *workspace, size_t workspace_bytes,
+                                 void *stream) {
+  SetState *st = nullptr;
+  stl_status r = ragged_common(s, sig, offsets, formula_id, n_traces, bounds, n_slots, p, false, workspace,
+                               workspace_bytes, &st);
+  if (r) return r;
+  if (n_traces > 0 && !out) return fail(STL_ERR_INVALID_ARG, "out is NULL");
+  return ragged_launch(s, *st, sig, offsets, formula_id, order, n_traces, bounds, nullptr, out, nullptr, nullptr,
+                       workspace, stream);
+}
+
+stl_status stl_robustness_ragged_backward(stl_set_handle s, const float *sig, const int64_t *offsets,
+                                          const int32_t *formula_id, const int32_t *order, int64_t n_traces,
+                                          const float *bounds, int32_t n_slots, const stl_params *p,
+                                          const float *grad_out, float *grad_sig, float *grad_bounds,
+                                          void *workspace, size_t workspace_bytes, void *stream) {
+  SetState *st = nullptr;
+  stl_status r = ragged_common(s, sig, offsets, formula_id, n_traces, bounds, n_slots, p, true, workspace,
+                               workspace_bytes, &st);
+  if (r) return r;
+  if (n_traces > 0 && (!grad_out || !grad_sig)) return fail(STL_ERR_INVALID_ARG, "grad_out / grad_sig is NULL");
+  if (grad_bounds && s->n_slots > 0 && n_traces > 0) {
+    cudaError_t ce = cudaMemsetAsync(grad_bounds, 0, (size_t)n_traces * s->n_slots * 2 * sizeof(float),
+                                     (cudaStream_t)stream);
+    if (ce != cudaSuccess) return cuda_fail((int)ce, "cudaMemsetAsync(grad_bounds)");
+  }
+  return ragged_launch(s, *st, sig, offsets, formula_id, order, n_traces, bounds, grad_out, nullptr, grad_sig,
+                       grad_bounds, workspace, stream);
+}
+
+}  // extern "C"

@@ -83,6 +83,18 @@ struct LaunchArgs {
   float *gbounds;
   float *ws;
   int *status;         // device status word (sticky error flag)
+  // ragged launches (table != nullptr): per-trace programs and packed traces
+  const KProgram *table;        // device table of programs, one per formula
+  const long long *offsets;     // [n_traces + 1] first sample row of each trace
+  const int *fid;               // [n_traces] formula of each trace
+  const int *order;             // [n_traces] processing order, or nullptr
+  unsigned long long *counter;  // work counter (zeroed before the launch)
+  long long n_traces;
+  int n_formulas;
+  long long T_max;              // longest trace the table was prepared for
+  int gwords;                   // global buffer words per CTA (max over formulas)
+  int ut_len;
+  long long ut_off;
   int grid;
   int threads;
   void *stream;

@@ -229,7 +229,8 @@ struct Cta {
   NodeRt *rt;
   void *scratch;
   const float *sig;
-  long long b;
+  long long b;         // trace index (bounds row)
+  long long row0;      // first sample row of the trace in the (packed) signal
   int T;
   int t0, t1;          // current root step [t0, t1)
   int root;
@@ -404,7 +405,7 @@ __device__ void eval_pred(const Cta &C, int n, int F, int E) {
   const KNode &nd = P.nd[n];
   const int D = P.D;
   const float *w = P.w + nd.w_off;
-  const float *__restrict__ xs = C.sig + (size_t)C.b * (size_t)C.T * D;
+  const float *__restrict__ xs = C.sig + C.row0 * D;
   const NodeOut out = node_out(C, n);
   const bool gt = nd.op == OP_PGT;
   const float pc = nd.pc;
@@ -1075,28 +1076,69 @@ __device__ void signal_gradient(const Cta &C, float *gs, int pst, int j0, int j1
 }
 
 // ------------------------------------------------------------------ main kernel
+// Dense launches walk (trace, segment) items with a static stride and use the program passed
+// by value.  Ragged launches (A.table != nullptr) take whole traces from an atomic work
+// counter, in the caller's order, and read each trace's program from the device table.
 template <int NT, bool BWD, bool SMOOTH>
-__global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram P, LaunchArgs A) {
+__global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram Pdense, LaunchArgs A) {
   extern __shared__ float4 smem4[];
   char *smem = reinterpret_cast<char *>(smem4);
+  __shared__ long long s_item;
+  const bool ragged = A.table != nullptr;
   Cta C;
-  C.P = &P;
-  C.rt = reinterpret_cast<NodeRt *>(smem + (size_t)P.rt_off * 4);
-  C.scratch = smem + (size_t)P.scratch_off * 4;
   C.sig = A.sig;
-  C.T = (int)P.T;
-  C.root = P.n - 1;
-  float *ws_cta = A.ws ? A.ws + (size_t)blockIdx.x * (size_t)P.gwords : nullptr;
-  float *ut = (A.ws && P.ut_len > 0) ? A.ws + P.ut_off + blockIdx.x * (long long)NT + threadIdx.x : nullptr;
+  const int gwords = ragged ? A.gwords : Pdense.gwords;
+  const int ut_len = ragged ? A.ut_len : Pdense.ut_len;
+  const long long ut_off = ragged ? A.ut_off : Pdense.ut_off;
+  float *ws_cta = A.ws ? A.ws + (size_t)blockIdx.x * (size_t)gwords : nullptr;
+  float *ut = (A.ws && ut_len > 0) ? A.ws + ut_off + blockIdx.x * (long long)NT + threadIdx.x : nullptr;
   const long long ut_stride = (long long)gridDim.x * NT;
-  const int T = C.T;
+  const long long n_items = ragged ? A.n_traces : Pdense.n_items;
 
-  for (long long item = blockIdx.x; item < P.n_items; item += gridDim.x) {
-    C.b = item / P.segs_per_trace;
-    const int sidx = (int)(item % P.segs_per_trace);
-    const int s0 = sidx * P.seg;
-    const int s1 = (s0 + P.seg < T) ? s0 + P.seg : T;
-    C.out_row = BWD ? nullptr : A.out + (size_t)C.b * T;
+  for (long long it = 0;; ++it) {
+    long long item;
+    if (ragged) {
+      if (threadIdx.x == 0) s_item = atomicAdd(A.counter, 1ULL);
+      __syncthreads();
+      item = s_item;
+      __syncthreads();
+    } else {
+      item = blockIdx.x + it * (long long)gridDim.x;
+    }
+    if (item >= n_items) break;
+    int s0, s1;
+    if (ragged) {
+      // per-trace data is checked here: a bad entry sets the status word and skips the trace
+      const long long b = A.order ? (long long)A.order[item] : item;
+      if (b < 0 || b >= A.n_traces) { if (threadIdx.x == 0 && A.status) atomicExch(A.status, 1); continue; }
+      const int k = A.fid[b];
+      const long long r0 = A.offsets[b], len = A.offsets[b + 1] - r0;
+      if (k < 0 || k >= A.n_formulas || r0 < 0 || len > A.T_max) {
+        if (threadIdx.x == 0 && A.status) atomicExch(A.status, 1);
+        continue;
+      }
+      if (len <= 0) continue;
+      C.P = A.table + k;
+      C.b = b;
+      C.row0 = r0;
+      C.T = (int)len;
+      s0 = 0;
+      s1 = C.T;
+    } else {
+      C.P = &Pdense;
+      C.b = item / Pdense.segs_per_trace;
+      C.T = (int)Pdense.T;
+      C.row0 = C.b * (long long)C.T;
+      const int sidx = (int)(item % Pdense.segs_per_trace);
+      s0 = sidx * Pdense.seg;
+      s1 = (s0 + Pdense.seg < C.T) ? s0 + Pdense.seg : C.T;
+    }
+    const KProgram &P = *C.P;
+    const int T = C.T;
+    C.rt = reinterpret_cast<NodeRt *>(smem + (size_t)P.rt_off * 4);
+    C.scratch = smem + (size_t)P.scratch_off * 4;
+    C.root = P.n - 1;
+    C.out_row = BWD ? nullptr : A.out + C.row0;
     setup_geometry(C, A.bounds, ws_cta, smem, A.status);
     if (BWD) {
       for (int n = 0; n < P.n; ++n)
@@ -1118,7 +1160,7 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
         __syncthreads();
       }
       if constexpr (BWD && !SMOOTH) {
-        hard_walk(C, A.gout + (size_t)C.b * T, t0, t1);
+        hard_walk(C, A.gout + C.row0, t0, t1);
         __syncthreads();
       }
       if constexpr (BWD && SMOOTH) {
@@ -1127,7 +1169,7 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
           NodeRt &r = C.rt[C.root];
           float *ra = r.adj;
           const int st = t0 + r.lo;
-          const float *g = A.gout + (size_t)C.b * T;
+          const float *g = A.gout + C.row0;
           for (int q = t0 + threadIdx.x; q < t1; q += NT) {
             const float v = __ldg(g + q);
             if (q == T - 1) r.padadj += v;
@@ -1141,7 +1183,7 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
           int A1 = t1 + r.lo;
           A1 = A1 < T - 1 ? A1 : T - 1;
           if (A0 < A1) {
-            if (SMOOTH && P.nd[n].op == OP_UNTIL)
+            if (P.nd[n].op == OP_UNTIL)
               adjoint_smooth_until(C, n, A0, A1, ut, ut_stride);
             else
               adjoint_node<SMOOTH>(C, n, A0, A1, s0 + r.lo, s1 + r.lo);
@@ -1151,20 +1193,18 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
       }
       if constexpr (BWD) {
         // signal gradient for the samples whose predicate adjoints are complete
-        {
-          int j0 = t0 + P.lp, j1 = t1 + P.lp;
-          j0 = j0 > s0 ? j0 : s0;
-          j1 = j1 < s1 ? j1 : s1;
-          j1 = j1 < T - 1 ? j1 : T - 1;
-          const int D = P.D;
-          if (t0 == R0) {
-            // samples before the first predicate offset are read by no predicate: zero gradient
-            const int z1 = j0 < T - 1 ? j0 : T - 1;
-            for (int idx = threadIdx.x; idx < (z1 - s0) * D; idx += NT)
-              A.gsig[((size_t)C.b * T + s0) * D + idx] = 0.f;
-          }
-          signal_gradient(C, A.gsig + (size_t)C.b * T * D, t0 + P.lp, j0, j1);
+        int j0 = t0 + P.lp, j1 = t1 + P.lp;
+        j0 = j0 > s0 ? j0 : s0;
+        j1 = j1 < s1 ? j1 : s1;
+        j1 = j1 < T - 1 ? j1 : T - 1;
+        const int D = P.D;
+        if (t0 == R0) {
+          // samples before the first predicate offset are read by no predicate: zero gradient
+          const int z1 = j0 < T - 1 ? j0 : T - 1;
+          for (int idx = threadIdx.x; idx < (z1 - s0) * D; idx += NT)
+            A.gsig[(C.row0 + s0) * D + idx] = 0.f;
         }
+        signal_gradient(C, A.gsig + C.row0 * D, t0 + P.lp, j0, j1);
         __syncthreads();
       }
       if (t1 < s1) shift_buffers<BWD>(C, P.tile);
@@ -1174,7 +1214,7 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
         // finish sample T-1 of every node, parents first (all reads go to the T-1 cells);
         // the hard walk already delivered sample T-1 of every root sample
         for (int n = P.n - 1; SMOOTH && n >= 0; --n) {
-          if (SMOOTH && P.nd[n].op == OP_UNTIL)
+          if (P.nd[n].op == OP_UNTIL)
             adjoint_smooth_until(C, n, T - 1, T, ut, ut_stride);
           else
             adjoint_node<SMOOTH>(C, n, T - 1, T, T - 1, T);
@@ -1184,7 +1224,7 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
         for (int d = threadIdx.x; d < D; d += NT) {
           float acc = 0.f;
           for (int k = 0; k < P.npred; ++k) acc = fmaf(P.pw[k * STL_MAX_D + d], C.rt[P.pred[k]].padadj, acc);
-          A.gsig[((size_t)C.b * T + (T - 1)) * D + d] = acc;
+          A.gsig[(C.row0 + (T - 1)) * D + d] = acc;
         }
       }
       __syncthreads();

@@ -7,7 +7,8 @@ from __future__ import annotations
 
 import torch
 
-from .binding import Formula, StlParams, params as make_params, robustness_backward_raw, robustness_raw
+from .binding import (Formula, FormulaSet, StlParams, params as make_params, robustness_backward_raw,
+                      robustness_ragged_backward_raw, robustness_ragged_raw, robustness_raw)
 
 
 def _check_sig(f: Formula, sig: torch.Tensor):
@@ -84,3 +85,67 @@ class STLRobustness(torch.autograd.Function):
         sig, bounds = ctx.saved_tensors
         gsig, gb = robustness_backward(ctx.f, sig, grad_out, bounds if ctx.has_bounds else None, ctx.p)
         return None, gsig, (gb if ctx.has_bounds else None), None
+
+
+class RaggedBatch:
+    """Device-resident ragged batch for a FormulaSet: packed signal [sum T, D], offsets, formula
+    ids, optional processing order and bounds.  forward() / backward() each issue ONE launch and
+    allocate nothing, so both can be captured in a CUDA graph (see capture())."""
+
+    def __init__(self, fset: FormulaSet, sig, offsets, formula_id, bounds=None, p: StlParams | None = None,
+                 order=None, device="cuda"):
+        self.fset, self.p = fset, p or make_params()
+        self.sig = sig.to(device=device, dtype=torch.float32).contiguous()
+        self.offsets = offsets.to(device=device, dtype=torch.int64).contiguous()
+        self.fid = formula_id.to(device=device, dtype=torch.int32).contiguous()
+        self.order = None if order is None else order.to(device=device, dtype=torch.int32).contiguous()
+        self.n = int(self.fid.numel())
+        lens = (offsets[1:] - offsets[:-1])
+        self.T_max = int(lens.max().item()) if self.n else 1
+        self.bounds = None
+        if fset.n_slots:
+            if bounds is None:
+                raise ValueError("the formulas use per-trace bounds")
+            self.bounds = bounds.to(device=device, dtype=torch.float32).contiguous()
+        total = int(offsets[-1].item())
+        self.out = torch.empty(total, dtype=torch.float32, device=device)
+        self.gsig = torch.empty((total, fset.D), dtype=torch.float32, device=device)
+        self.gbounds = torch.empty((self.n, fset.n_slots, 2), device=device) if fset.n_slots else None
+        nf = fset.prepare(max(1, self.n), self.T_max, self.p, False)
+        nb = fset.prepare(max(1, self.n), self.T_max, self.p, True)
+        self.ws_f = torch.empty(nf // 4 + 1, dtype=torch.float32, device=device)
+        self.ws_b = torch.empty(nb // 4 + 1, dtype=torch.float32, device=device)
+        self.nf, self.nb = nf, nb
+
+    def _ptr(self, t):
+        return None if t is None else t.data_ptr()
+
+    def forward(self):
+        st = torch.cuda.current_stream(self.sig.device).cuda_stream
+        robustness_ragged_raw(self.fset, self.sig.data_ptr(), self.offsets.data_ptr(), self.fid.data_ptr(),
+                              self._ptr(self.order), self.n, self._ptr(self.bounds), self.p, self.out.data_ptr(),
+                              self.ws_f.data_ptr(), self.nf, st)
+        return self.out
+
+    def backward(self, grad_out):
+        st = torch.cuda.current_stream(self.sig.device).cuda_stream
+        robustness_ragged_backward_raw(self.fset, self.sig.data_ptr(), self.offsets.data_ptr(), self.fid.data_ptr(),
+                                       self._ptr(self.order), self.n, self._ptr(self.bounds), self.p,
+                                       grad_out.data_ptr(), self.gsig.data_ptr(), self._ptr(self.gbounds),
+                                       self.ws_b.data_ptr(), self.nb, st)
+        return self.gsig, self.gbounds
+
+    def capture(self, grad_out):
+        """Capture forward + backward into a CUDA graph (after one eager warm-up call)."""
+        self.forward()
+        self.backward(grad_out)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self.forward()
+                self.backward(grad_out)
+        torch.cuda.current_stream().wait_stream(s)
+        return g

@@ -1,0 +1,107 @@
+"""Ragged batches in one persistent launch: uneven trace lengths, 16 seed-generated formulas
+of depth <= 4 with per-trace bounds (the config-3 shape at a size the oracle finishes in
+seconds), checked trace by trace against the FP64 oracle; the processing order does not change
+the result; a CUDA-graph replay reproduces the eager result; bad per-trace data is rejected on
+the device without a fault."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+VAL_TOL, GRAD_TOL = 1e-5, 1e-4
+
+
+@pytest.fixture(scope="module")
+def stl():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2501_04194_gb300 as m
+    return m
+
+
+def per_trace_err(got, ref, offsets):
+    worst = 0.0
+    for i in range(len(offsets) - 1):
+        g = np.asarray(got[offsets[i]:offsets[i + 1]], dtype=np.float64)
+        r = np.asarray(ref[offsets[i]:offsets[i + 1]], dtype=np.float64)
+        fin = np.isfinite(r)
+        assert np.array_equal(fin, np.isfinite(g))
+        scale = max(np.abs(r[fin]).max() if fin.any() else 0.0, 1e-30)
+        worst = max(worst, float((np.abs(g[fin] - r[fin]) / scale).max()) if fin.any() else 0.0)
+    return worst
+
+
+def make_batch(stl, wl, mode, order=None):
+    fs = [stl.Formula(f, D=4, n_slots=wl["n_slots"]) for f in wl["formulas"]]
+    fset = stl.FormulaSet(fs)
+    p = stl.params(mode, tau=3.0)
+    rb = stl.RaggedBatch(fset, torch.from_numpy(wl["signal"]), torch.from_numpy(wl["offsets"]),
+                         torch.from_numpy(wl["formula_id"]), bounds=torch.from_numpy(wl["bounds"]), p=p,
+                         order=None if order is None else torch.from_numpy(order))
+    return rb, fs, fset
+
+
+@pytest.mark.parametrize("mode", ["hard", "smooth"])
+def test_ragged_matches_oracle(stl, mode):
+    wl = W.config3_workload(n_traces=40, t_lo=50, t_hi=2000, seed=3)
+    rb, _, _ = make_batch(stl, wl, mode)
+    rng = np.random.default_rng(0)
+    gout = rng.normal(size=int(wl["offsets"][-1])).astype(np.float32)
+    rho = rb.forward().cpu().numpy()
+    gs, gb = rb.backward(torch.from_numpy(gout).cuda())
+    gs = gs.cpu().numpy()
+    torch.cuda.synchronize()
+    from paper_2501_04194_gb300.binding import device_status
+    assert device_status() == 0
+    om = oracle.HARD if mode == "hard" else oracle.SMOOTH
+    kw = dict(mode=om, tau=3.0)
+    ref = oracle.robustness_ragged_multi(wl["formulas"], wl["formula_id"], wl["signal"], wl["offsets"],
+                                         bounds=wl["bounds"], **kw)
+    if mode == "hard":
+        np.testing.assert_array_equal(rho, ref.astype(np.float32))
+    else:
+        assert per_trace_err(rho, ref, wl["offsets"]) <= VAL_TOL
+    gref, _ = oracle.robustness_grad_ragged_multi(wl["formulas"], wl["formula_id"], wl["signal"], wl["offsets"],
+                                                  gout.astype(np.float64), bounds=wl["bounds"], **kw)
+    assert per_trace_err(gs.reshape(-1, 4), gref, wl["offsets"]) <= GRAD_TOL
+
+
+def test_ragged_order_and_graph_replay(stl):
+    wl = W.config3_workload(n_traces=64, t_lo=50, t_hi=3000, seed=5)
+    lengths = np.diff(wl["offsets"])
+    order = np.argsort(-lengths, kind="stable").astype(np.int32)
+    rb0, _, _ = make_batch(stl, wl, "hard")
+    rb1, _, _ = make_batch(stl, wl, "hard", order=order)
+    g = torch.randn(int(wl["offsets"][-1]), device="cuda")
+    a = rb0.forward().clone()
+    ga, _ = rb0.backward(g)
+    ga = ga.clone()
+    b = rb1.forward().clone()
+    gb, _ = rb1.backward(g)
+    assert torch.equal(a, b)
+    assert torch.allclose(ga, gb, rtol=1e-5, atol=1e-6)
+    graph = rb1.capture(g)
+    rb1.out.zero_()
+    rb1.gsig.zero_()
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(rb1.out, a)
+        assert torch.allclose(rb1.gsig, ga, rtol=1e-5, atol=1e-6)
+
+
+def test_ragged_bad_formula_id_is_rejected_on_device(stl):
+    from paper_2501_04194_gb300.binding import device_status
+    wl = W.config3_workload(n_traces=8, t_lo=50, t_hi=400, seed=7)
+    wl["formula_id"] = wl["formula_id"].copy()
+    wl["formula_id"][3] = 99
+    rb, _, _ = make_batch(stl, wl, "hard")
+    device_status()
+    rb.forward()
+    torch.cuda.synchronize()
+    assert device_status() == -6
+    assert device_status() == 0
