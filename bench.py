@@ -162,6 +162,75 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_ms(torch, fn, steps=3, warmup=2):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def side_measurements(stl, W, torch, dev, args):
+    """Secondary numbers reported beside the headline (not the metric):
+    - config 1 in smooth mode (tau = 10) at T = 10000, fwd+bwd trace-steps/s;
+    - config 3: 10,000 ragged traces (T ~ U[50, 20000], D = 4, 16 formulas, hard), fwd+bwd in
+      one persistent launch each, against one launch per formula over its own traces."""
+    out = {}
+    B1, T1 = 1024, 10000
+    f = stl.Formula(W.config1_formula(), D=3)
+    p = stl.params("smooth", tau=10.0)
+    x = torch.from_numpy(W.random_walk(B1, T1, 3, seed=0)).to(dev)
+    g = torch.randn((B1, T1), device=dev)
+    ms_f = time_ms(torch, lambda: stl.robustness(f, x, p=p))
+    ms_b = time_ms(torch, lambda: stl.robustness_backward(f, x, g, p=p))
+    out["smooth_config1_T10000"] = {"value": B1 * T1 / ((ms_f + ms_b) * 1e-3), "unit": UNIT, "fwd_ms": ms_f,
+                                    "bwd_ms": ms_b, "note": "smooth Until is O(b) per sample (compute-bound)"}
+    wl = W.config3_workload()
+    fs = [stl.Formula(t, D=4, n_slots=wl["n_slots"]) for t in wl["formulas"]]
+    offs = torch.from_numpy(wl["offsets"])
+    order = torch.from_numpy(np.argsort(-np.diff(wl["offsets"]), kind="stable").astype(np.int32))
+    ph = stl.params("hard")
+    rb = stl.RaggedBatch(stl.FormulaSet(fs), torch.from_numpy(wl["signal"]), offs,
+                         torch.from_numpy(wl["formula_id"]), bounds=torch.from_numpy(wl["bounds"]), p=ph, order=order)
+    gg = torch.randn(int(wl["offsets"][-1]), device=dev)
+    steps_total = int(wl["offsets"][-1])
+    ms_one = time_ms(torch, lambda: (rb.forward(), rb.backward(gg)))
+    graph = rb.capture(gg)
+    ms_graph = time_ms(torch, graph.replay)
+    # one launch per formula, each over its own traces (same kernels, 16 + 16 launches)
+    per = []
+    for k in range(len(fs)):
+        idx = np.nonzero(wl["formula_id"] == k)[0]
+        if len(idx) == 0:
+            continue
+        lens = np.diff(wl["offsets"])[idx]
+        sub_off = np.zeros(len(idx) + 1, dtype=np.int64)
+        sub_off[1:] = np.cumsum(lens)
+        sub_sig = np.concatenate([wl["signal"][wl["offsets"][i]:wl["offsets"][i + 1]] for i in idx])
+        per.append(stl.RaggedBatch(stl.FormulaSet([fs[k]]), torch.from_numpy(sub_sig), torch.from_numpy(sub_off),
+                                   torch.zeros(len(idx), dtype=torch.int32), bounds=torch.from_numpy(wl["bounds"][idx]),
+                                   p=ph, order=torch.from_numpy(np.argsort(-lens, kind="stable").astype(np.int32))))
+    gper = [torch.randn(int(r.offsets[-1].item()), device=dev) for r in per]
+
+    def per_formula():
+        for r, gk in zip(per, gper):
+            r.forward()
+            r.backward(gk)
+
+    ms_per = time_ms(torch, per_formula)
+    out["ragged_config3"] = {"traces": int(len(wl["formula_id"])), "trace_steps": steps_total, "formulas": len(fs),
+                             "one_launch": {"value": steps_total / (ms_one * 1e-3), "ms": ms_one},
+                             "one_launch_graph": {"value": steps_total / (ms_graph * 1e-3), "ms": ms_graph},
+                             "per_formula_launches": {"value": steps_total / (ms_per * 1e-3), "ms": ms_per},
+                             "unit": UNIT, "mode": "hard", "fwd+bwd": True}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -175,6 +244,8 @@ def main():
     ap.add_argument("--ref-traces", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the smooth and ragged side measurements")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -215,6 +286,16 @@ def main():
     rho = torch.empty((B, T), device=dev)
     gsig = torch.empty((B, T, D), device=dev)
     from paper_2501_04194_gb300.binding import robustness_backward_raw, robustness_raw
+    tuned = None
+    if not args.no_tune:
+        # launch-shape autotuning (outside the timed region)
+        lf, _ = stl.autotune(f, x, p=p, backward=False)
+        lb, _ = stl.autotune(f, x, p=p, backward=True)
+        tuned = {"forward": lf, "backward": lb}
+        ws_f = f.workspace_size(B, T, p, False)
+        ws_b = f.workspace_size(B, T, p, True)
+        wsf = torch.empty(max(1, ws_f // 4 + 1), device=dev)
+        wsb = torch.empty(max(1, ws_b // 4 + 1), device=dev)
 
     def step(ev=None):
         if ev:
@@ -318,6 +399,7 @@ def main():
         v, dt, cores = oracle_sample(B, T, tree, n, seed=0)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{n} of {B} traces x T={T}, fwd+bwd, FP64 oracle ({dt:.1f} s)"}
+    extra = None if (args.no_extra or world > 1) else side_measurements(stl, W, torch, dev, args)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -325,7 +407,7 @@ def main():
                        "tau": args.tau if args.mode == "smooth" else None,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
-            "clocks": ck}
+            "clocks": ck, "launch": tuned, "side": extra}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

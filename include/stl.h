@@ -128,6 +128,20 @@ STL_API void stl_destroy(stl_handle h);
 /* Override (or, with all-zero fields, reset) the launch shape used for this handle. */
 STL_API stl_status stl_set_launch(stl_handle h, const stl_launch *launch);
 
+/* Autotuner: time candidate launch shapes (CTA size x tile) for this handle, call shape and
+ * direction on the caller's buffers (backward = 0: out is [B, T]; 1: grad_out [B, T] and
+ * out = grad_sig [B, T, D]), keep the fastest in the handle for that direction and return it
+ * (best_ms: mean time of the winner, -1 when taken from the cache).  Candidates whose
+ * workspace exceeds workspace_bytes are skipped.  If the environment variable
+ * STL_TUNE_CACHE names a file, results are looked up there first (key: formula hash, D,
+ * slots, semantics, direction, log2 buckets of B and T) and appended after tuning.
+ * Synchronous (events + synchronisation): call it before any stream capture.  The outputs
+ * hold the result of the last timed launch. */
+STL_API stl_status stl_autotune(stl_handle h, const float *sig, int64_t B, int64_t T, const float *bounds,
+                                const stl_params *p, int32_t backward, const float *grad_out, float *out,
+                                float *grad_bounds, void *workspace, size_t workspace_bytes, void *stream,
+                                stl_launch *best, float *best_ms);
+
 /* Launch shape the library would use for this call shape (after heuristics/overrides). */
 STL_API stl_status stl_get_launch(stl_handle h, int64_t B, int64_t T, const stl_params *p,
                           int32_t backward, stl_launch *out);

@@ -176,6 +176,22 @@ class Formula:
         check(load().stl_get_launch(self._h, B, T, ctypes.byref(p), int(backward), ctypes.byref(out)))
         return dict(tile=out.tile, threads=out.threads, segment=out.segment, grid=out.reserved)
 
+    def autotune(self, sig_ptr, B, T, bounds_ptr, p: StlParams, backward, grad_out_ptr, out_ptr, gb_ptr, ws_ptr,
+                 ws_bytes, stream):
+        """stl_autotune: time candidate launch shapes, keep the best for this direction.
+        Returns (launch dict, mean ms of the winner or -1 if it came from STL_TUNE_CACHE)."""
+        lib = load()
+        fn = lib.stl_autotune
+        if fn.argtypes is None:
+            vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+            fn.argtypes = [vp, vp, i64, i64, vp, ctypes.POINTER(StlParams), i32, vp, vp, vp, vp, sz, vp,
+                           ctypes.POINTER(StlLaunch), ctypes.POINTER(ctypes.c_float)]
+            fn.restype = i32
+        best, ms = StlLaunch(), ctypes.c_float()
+        check(fn(self._h, sig_ptr, B, T, bounds_ptr, ctypes.byref(p), int(backward), grad_out_ptr, out_ptr, gb_ptr,
+                 ws_ptr, ws_bytes, stream, ctypes.byref(best), ctypes.byref(ms)))
+        return dict(tile=best.tile, threads=best.threads, segment=best.segment), float(ms.value)
+
     def workspace_size(self, B, T, p: StlParams, backward=False) -> int:
         n = ctypes.c_size_t()
         check(load().stl_workspace_size(self._h, B, T, ctypes.byref(p), int(backward), ctypes.byref(n)))

@@ -6,8 +6,11 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <new>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -57,7 +60,8 @@ struct stl_program {
   std::vector<float> w;
   int D = 0, n_slots = 0;
   bool has_sm = false, has_until = false;
-  stl_launch launch{};
+  stl_launch launch_dir[2]{};   // [forward, backward]: explicit or tuned launch shapes
+  stl_launch launch{};          // the shape used by the planner for the current direction
 };
 
 // A group of formulas evaluated together in one ragged launch.  The device table holds one
@@ -102,8 +106,11 @@ int window_lo(const stl_node &nd) {
 }
 
 // Compute node geometry, ring layout and launch shape for one call.
-stl_status make_plan(const stl_program *h, long long B, long long T, const stl_params &p, bool bwd, Plan &pl,
+stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_params &p, bool bwd, Plan &pl,
                      int force_threads = 0) {
+  stl_program hv = *hp;               // shallow copy carrying this direction's launch shape
+  hv.launch = hp->launch_dir[bwd ? 1 : 0];
+  const stl_program *h = &hv;
   KProgram &P = pl.P;
   std::memset(&P, 0, sizeof P);
   const int n = (int)h->nodes.size();
@@ -427,7 +434,7 @@ stl_status stl_set_launch(stl_handle h, const stl_launch *launch) {
     return fail(STL_ERR_INVALID_ARG, "threads must be 0, 256 or 512");
   if (launch->tile < 0 || (launch->tile && launch->tile % 32) || launch->segment < 0)
     return fail(STL_ERR_INVALID_ARG, "tile must be a non-negative multiple of 32; segment >= 0");
-  h->launch = *launch;
+  h->launch_dir[0] = h->launch_dir[1] = *launch;
   return STL_OK;
 }
 
@@ -733,6 +740,123 @@ stl_status stl_robustness_ragged_backward(stl_set_handle s, const float *sig, co
   }
   return ragged_launch(s, *st, sig, offsets, formula_id, order, n_traces, bounds, grad_out, nullptr, grad_sig,
                        grad_bounds, workspace, stream);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ autotuner
+namespace {
+
+uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ULL) {
+  const unsigned char *b = (const unsigned char *)data;
+  for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ULL; }
+  return h;
+}
+
+int log2_bucket(long long v) {
+  int k = 0;
+  while (v > 1) { v >>= 1; ++k; }
+  return k;
+}
+
+std::string tune_key(const stl_program *h, long long B, long long T, const stl_params &p, bool bwd) {
+  uint64_t x = fnv1a(h->nodes.data(), h->nodes.size() * sizeof(stl_node));
+  x = fnv1a(h->w.data(), h->w.size() * sizeof(float), x);
+  char buf[128];
+  snprintf(buf, sizeof buf, "%016llx-D%d-S%d-m%d-%s-B%d-T%d", (unsigned long long)x, h->D, h->n_slots, p.mode,
+           bwd ? "bwd" : "fwd", log2_bucket(B), log2_bucket(T));
+  return buf;
+}
+
+bool cache_lookup(const char *path, const std::string &key, stl_launch *out) {
+  std::ifstream f(path);
+  if (!f) return false;
+  std::string line;
+  bool found = false;
+  while (std::getline(f, line)) {
+    std::istringstream is(line);
+    std::string k;
+    stl_launch l{};
+    double ms;
+    if (is >> k >> l.tile >> l.threads >> l.segment >> ms && k == key) { *out = l; found = true; }
+  }
+  return found;
+}
+
+void cache_store(const char *path, const std::string &key, const stl_launch &l, double ms) {
+  std::ofstream f(path, std::ios::app);
+  if (f) f << key << " " << l.tile << " " << l.threads << " " << l.segment << " " << ms << "\n";
+}
+
+}  // namespace
+
+extern "C" {
+
+stl_status stl_autotune(stl_handle h, const float *sig, int64_t B, int64_t T, const float *bounds, const stl_params *p,
+                        int32_t backward, const float *grad_out, float *out, float *grad_bounds, void *workspace,
+                        size_t workspace_bytes, void *stream, stl_launch *best, float *best_ms) {
+  stl_status s = check_call(h, sig, B, T, bounds, p);
+  if (s) return s;
+  if (!best) return fail(STL_ERR_INVALID_ARG, "best is NULL");
+  if (B == 0) return fail(STL_ERR_INVALID_ARG, "nothing to tune for B = 0");
+  const bool bwd = backward != 0;
+  if (!out || (bwd && !grad_out)) return fail(STL_ERR_INVALID_ARG, "output buffers are NULL");
+  const char *cache = std::getenv("STL_TUNE_CACHE");
+  const std::string key = tune_key(h, B, T, *p, bwd);
+  stl_launch hit{};
+  if (cache && *cache && cache_lookup(cache, key, &hit)) {
+    h->launch_dir[bwd ? 1 : 0] = hit;
+    *best = hit;
+    if (best_ms) *best_ms = -1.f;
+    return STL_OK;
+  }
+  const stl_launch saved = h->launch_dir[bwd ? 1 : 0];
+  std::vector<stl_launch> cands;
+  for (int nt : {256, 512})
+    for (int mult : {4, 7, 14}) {
+      stl_launch l{};
+      l.threads = nt;
+      l.tile = std::max(256, (nt * mult / 32) * 32);
+      cands.push_back(l);
+    }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(STL_ERR_CUDA, "cudaEventCreate failed");
+  float best_t = 1e30f;
+  stl_launch best_l = saved;
+  bool any = false;
+  for (const stl_launch &c : cands) {
+    h->launch_dir[bwd ? 1 : 0] = c;
+    size_t need = 0;
+    if (stl_workspace_size(h, B, T, p, backward, &need) != STL_OK || need > workspace_bytes) continue;
+    auto run = [&]() {
+      return bwd ? stl_robustness_backward(h, sig, B, T, bounds, p, grad_out, out, grad_bounds, workspace,
+                                           workspace_bytes, stream)
+                 : stl_robustness(h, sig, B, T, bounds, p, out, workspace, workspace_bytes, stream);
+    };
+    if (run() != STL_OK) continue;
+    cudaEventRecord(e0, (cudaStream_t)stream);
+    bool ok = true;
+    for (int r = 0; r < 3 && ok; ++r) ok = run() == STL_OK;
+    cudaEventRecord(e1, (cudaStream_t)stream);
+    if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 3.f;
+    any = true;
+    if (ms < best_t) { best_t = ms; best_l = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!any) {
+    h->launch_dir[bwd ? 1 : 0] = saved;
+    return fail(STL_ERR_WORKSPACE, "no candidate launch shape fits the given workspace");
+  }
+  h->launch_dir[bwd ? 1 : 0] = best_l;
+  *best = best_l;
+  if (best_ms) *best_ms = best_t;
+  if (cache && *cache) cache_store(cache, key, best_l, best_t);
+  return STL_OK;
 }
 
 }  // extern "C"

@@ -69,6 +69,30 @@ def robustness_backward(f: Formula, sig: torch.Tensor, grad_out: torch.Tensor, b
     return gsig, gb
 
 
+def autotune(f: Formula, sig: torch.Tensor, bounds=None, p: StlParams | None = None, backward=False,
+             max_workspace_bytes: int = 1 << 30):
+    """Tune the launch shape of ``f`` for this call shape (see stl_autotune); returns
+    (launch, ms)."""
+    p = p or make_params()
+    sig = _check_sig(f, sig)
+    B, T, D = sig.shape
+    b = _bounds(f, bounds, sig)
+    stream = torch.cuda.current_stream(sig.device).cuda_stream
+    ws = torch.empty(max_workspace_bytes // 4, dtype=torch.float32, device=sig.device)
+    if backward:
+        g = torch.zeros((B, T), dtype=torch.float32, device=sig.device)
+        out = torch.empty((B, T, D), dtype=torch.float32, device=sig.device)
+        gb = torch.empty((B, f.n_slots, 2), dtype=torch.float32, device=sig.device) if f.n_slots else None
+        res = f.autotune(sig.data_ptr(), B, T, None if b is None else b.data_ptr(), p, True, g.data_ptr(),
+                         out.data_ptr(), None if gb is None else gb.data_ptr(), ws.data_ptr(), ws.numel() * 4, stream)
+    else:
+        out = torch.empty((B, T), dtype=torch.float32, device=sig.device)
+        res = f.autotune(sig.data_ptr(), B, T, None if b is None else b.data_ptr(), p, False, None, out.data_ptr(),
+                         None, ws.data_ptr(), ws.numel() * 4, stream)
+    del ws
+    return res
+
+
 class STLRobustness(torch.autograd.Function):
     """rho = STLRobustness.apply(formula, sig, bounds, params); differentiable w.r.t. sig and
     bounds.  The backward recomputes the forward on chip (no stored intermediates)."""

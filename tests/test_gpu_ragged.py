@@ -105,3 +105,27 @@ def test_ragged_bad_formula_id_is_rejected_on_device(stl):
     torch.cuda.synchronize()
     assert device_status() == -6
     assert device_status() == 0
+
+
+def test_autotune_keeps_parity_and_uses_the_cache(stl, tmp_path, monkeypatch):
+    """The autotuner picks a launch shape that still matches the oracle, and a second tuning
+    with STL_TUNE_CACHE set is served from the cache file."""
+    monkeypatch.setenv("STL_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    tree = W.config1_formula()
+    sig = W.config1_inputs(B=12, T=4000, seed=11)
+    x = torch.from_numpy(sig).cuda()
+    for bwd in (False, True):
+        f = stl.Formula(tree, D=3)
+        p = stl.params("hard")
+        launch, ms = stl.autotune(f, x, p=p, backward=bwd)
+        assert launch["threads"] in (256, 512) and launch["tile"] >= 256 and ms > 0
+        rho = stl.robustness(f, x, p=p).cpu().numpy()
+        np.testing.assert_array_equal(rho, oracle.robustness(tree, sig).astype(np.float32))
+        g = np.random.default_rng(1).normal(size=(12, 4000)).astype(np.float32)
+        gs, _ = stl.robustness_backward(f, x, torch.from_numpy(g).cuda(), p=p)
+        gref, _ = oracle.robustness_grad(tree, sig, g.astype(np.float64))
+        err = np.abs(gs.cpu().numpy() - gref).max() / np.abs(gref).max()
+        assert err <= GRAD_TOL
+        f2 = stl.Formula(tree, D=3)
+        launch2, ms2 = stl.autotune(f2, x, p=p, backward=bwd)
+        assert launch2 == launch and ms2 == -1.0
