@@ -197,8 +197,12 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
       }
       words[i] = nrings * padded(cap);
     }
+    int tab_words = 0;
+    for (int i = 0; i < n; ++i)
+      if (is_sm(h->nodes[i].op) && p.mode == STL_SMOOTH)
+        tab_words += round_up(3LL * (window_hi(h->nodes[i], T, p) + 2), 4);
     space_out.assign(n, 0);
-    smem_words = scratch_words + rt_words;
+    smem_words = scratch_words + rt_words + tab_words;
     for (int i = 0; i < n; ++i) smem_words += words[i];
     gwords = 0;
     // spill the largest rings to the global workspace until the arena fits
@@ -254,6 +258,16 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
       if (p.mode == STL_SMOOTH || is_pred(nd.op)) { k.adj_off = off; off += pw; }
       if (p.mode == STL_HARD && is_temporal(nd.op)) { k.aux_off = off; off += pw; }
     }
+    k.tab_off = -1;
+    k.tab_len = 0;
+  }
+  // smooth-mask weight tables live in shared memory after the buffers
+  for (int i = 0; i < n; ++i) {
+    if (!(is_sm(h->nodes[i].op) && p.mode == STL_SMOOTH)) continue;
+    KNode &k = P.nd[i];
+    k.tab_len = window_hi(h->nodes[i], T, p) + 2;
+    k.tab_off = off_s;
+    off_s += round_up(3LL * k.tab_len, 4);
   }
   for (int i = 0; i < n; ++i) {
     if (P.nd[i].c0 >= 0) P.nd[P.nd[i].c0].parent = i;
@@ -306,7 +320,7 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
     for (int i = 0; i < n; ++i)
       if (h->nodes[i].op == STL_OP_UNTIL) ut = std::max(ut, window_hi(h->nodes[i], T, p) + 1);
     P.ut_len = ut;
-    ws_words += (size_t)ut * pl.grid * threads;
+    ws_words += (size_t)2 * ut * pl.grid * threads;   // P_k and z_k per tap and thread
   }
   pl.ws_bytes = ws_words * 4;
   return STL_OK;
@@ -549,7 +563,7 @@ stl_status stl_internal_plan_backward_capped(stl_handle h, const float *sig, int
   Plan pl;
   s = make_plan(h, B, T, *p, true, pl);
   if (s) return s;
-  const size_t per_cta_words = (size_t)pl.P.gwords + (size_t)pl.P.ut_len * pl.threads;
+  const size_t per_cta_words = (size_t)pl.P.gwords + (size_t)2 * pl.P.ut_len * pl.threads;
   if (per_cta_words * 4 > capacity_bytes)
     return fail(STL_ERR_WORKSPACE, "one CTA needs %zu bytes of scratch, the static scratch holds %zu",
                 per_cta_words * 4, capacity_bytes);
@@ -644,7 +658,7 @@ stl_status stl_set_prepare(stl_set_handle s, int64_t n_traces, int64_t T_max, co
   st.ut_len = ut_len;
   // workspace: [work counter: 256 B][global node buffers grid x gwords][smooth-until arrays]
   st.ut_off = (long long)gwords * grid;
-  st.ws_bytes = 256 + ((size_t)gwords * grid + (size_t)ut_len * grid * threads) * 4;
+  st.ws_bytes = 256 + ((size_t)gwords * grid + (size_t)2 * ut_len * grid * threads) * 4;
   st.T_max = T_max;
   st.p = *p;
   st.ready = true;

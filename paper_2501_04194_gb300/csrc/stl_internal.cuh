@@ -24,6 +24,8 @@ struct KNode {
   int adj_off;         // -1 if the node keeps no adjoint buffer
   int aux_off;         // -1 if the node keeps no selected-source buffer
   int space;           // 0: shared memory, 1: global workspace
+  int tab_off;         // smooth-mask weight tables (3 x tab_len words in shared memory), -1 if none
+  int tab_len;
 };
 
 struct KProgram {
@@ -69,6 +71,8 @@ struct NodeRt {
   int lastaux;         // recorded source at sample T-1
   float padadj;        // adjoint accumulated for sample T-1
   float ga, gb;        // smooth-mask bound-gradient accumulators
+  float *tab;          // smooth-mask tables: m_i, dm_i/da, dm_i/db for i in [ia, ib]
+  int band_a, band_b;  // bound gradients use offsets [ia, band_a] and [band_b, ib]
   int op, c0, c1;      // copies of the node's operator and children (selection walk)
   int pred_k;          // index in the predicate list, or -1
 };

@@ -105,8 +105,8 @@ struct LseM {
     if (b.m == -INFINITY) return a;
     if (a.m == -INFINITY) return b;
     T o;
-    if (b.m > a.m) { o.m = b.m; o.s = fmaf(a.s, expf(a.m - b.m), b.s); }
-    else { o.m = a.m; o.s = fmaf(b.s, expf(b.m - a.m), a.s); }
+    if (b.m > a.m) { o.m = b.m; o.s = fmaf(a.s, __expf(a.m - b.m), b.s); }
+    else { o.m = a.m; o.s = fmaf(b.s, __expf(b.m - a.m), a.s); }
     return o;
   }
 };
@@ -489,7 +489,7 @@ __device__ void eval_smooth_window(const Cta &C, int n, int F, int E, int ia, in
   const float sgn = nd.op == OP_EV ? 1.f : -1.f;
   const float st = sgn * P.tau, sit = sgn * P.inv_tau;
   auto elem = [&](int j) { LS r; r.m = st * cv.get(j); r.s = 1.f; return r; };
-  auto out = [&](int q, LS r) { o.put(q, (r.m + logf(r.s)) * sit); };
+  auto out = [&](int q, LS r) { o.put(q, (r.m + __logf(r.s)) * sit); };
   window_any<LseM>(ib - ia + 1, F, E, ia, ib, elem, out, C.scratch);
 }
 
@@ -548,7 +548,28 @@ __device__ void eval_hard_until(const Cta &C, int n, int F, int E, int ia, int i
   }
 }
 
-// smooth Until (nested logsumexp, Sec. IV-C with Sec. III-C), one output per thread
+// Smooth Until (nested logsumexp of Sec. IV-C with the smooth min/max of Sec. III-C; the
+// nesting flattens, Sec. IV-D):  U = (1/tau) log sum_{i in [a,b]} 1/(S_i + Q_i) with
+// S_i = sum_{k<=i} e^{-tau phi_k}, Q_i = e^{-tau psi_i}.  Computed in the log domain with running
+// maxima so that nothing overflows; one output per thread, O(b) taps.
+struct LseAcc {   // running log(sum e^{z}) as (max, scaled sum)
+  float m = -INFINITY, s = 0.f;
+  __device__ __forceinline__ void add(float z) {
+    if (z == -INFINITY) return;
+    if (z > m) { s = fmaf(s, __expf(m - z), 1.f); m = z; }
+    else s += __expf(z - m);
+  }
+  __device__ __forceinline__ float log() const { return m == -INFINITY ? -INFINITY : m + __logf(s); }
+};
+
+// L = log(S + Q) with S = e^{acc}, Q = e^{zq}: -tau * smin(P, psi)
+__device__ __forceinline__ float log_s_plus_q(const LseAcc &acc, float zq) {
+  if (acc.m == -INFINITY) return zq;
+  if (zq == -INFINITY) return acc.log();
+  if (zq > acc.m) return zq + __logf(fmaf(acc.s, __expf(acc.m - zq), 1.f));
+  return acc.m + __logf(acc.s + __expf(zq - acc.m));
+}
+
 __device__ void eval_smooth_until(const Cta &C, int n, int F, int E, int ia, int ib) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
@@ -557,28 +578,13 @@ __device__ void eval_smooth_until(const Cta &C, int n, int F, int E, int ia, int
   const NodeOut o = node_out(C, n);
   const float tau = P.tau, itau = P.inv_tau;
   for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
-    float M1 = -INFINITY, S1 = 0.f;   // sum_k e^{-tau phi}: (max exponent, scaled sum)
-    float M2 = -INFINITY, S2 = 0.f;   // sum_i e^{tau z_i}
+    LseAcc S, Z;   // S: sum_k e^{-tau phi_k};  Z: sum_i e^{tau z_i}
     for (int i = 0; i <= ib; ++i) {
-      const float zp = -tau * cp.get(q + i);
-      if (zp != -INFINITY) {
-        if (zp > M1) { S1 = fmaf(S1, expf(M1 - zp), 1.f); M1 = zp; }
-        else S1 += expf(zp - M1);
-      }
-      if (i >= ia) {
-        const float Pv = M1 == -INFINITY ? INFINITY : -(M1 + logf(S1)) * itau;
-        const float qv = cq.get(q + i);
-        float z;
-        if (isinf(Pv) || isinf(qv)) z = Pv < qv ? Pv : qv;
-        else z = fminf(Pv, qv) - log1pf(expf(-tau * fabsf(Pv - qv))) * itau;
-        const float e = tau * z;
-        if (e != -INFINITY) {
-          if (e > M2) { S2 = fmaf(S2, expf(M2 - e), 1.f); M2 = e; }
-          else S2 += expf(e - M2);
-        }
-      }
+      S.add(-tau * cp.get(q + i));
+      if (i >= ia) Z.add(-log_s_plus_q(S, -tau * cq.get(q + i)));
     }
-    o.put(q, M2 == -INFINITY ? -INFINITY : (M2 + logf(S2)) * itau);
+    const float lz = Z.log();
+    o.put(q, lz == -INFINITY ? -INFINITY : lz * itau);
   }
 }
 
@@ -589,27 +595,27 @@ __device__ __forceinline__ float smask(float i, float a, float b, float c, float
   return m > 0.f ? m : 0.f;
 }
 
-// smooth-mask window in smooth mode: (sgn/tau) log sum_i m_i e^{sgn tau x_{q+i}}
+// smooth-mask window in smooth mode: (sgn/tau) log sum_i m_i e^{sgn tau x_{q+i}}, with the
+// weights m_i of this trace read from the node's table
 __device__ void eval_smooth_mask(const Cta &C, int n, int F, int E) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
   const NodeRt &me = C.rt[n];
   const ChildView cv = child_view(C, nd, nd.c0);
   const NodeOut o = node_out(C, n);
-  const int ia = me.ia, ib = me.ib;
-  const float fa = me.fa, fb = me.fb, mc = P.mask_c, meps = P.mask_eps;
+  const int ia = me.ia, len = me.ib - me.ia + 1;
+  const float *w = me.tab;
   const float sgn = nd.op == OP_EVSM ? 1.f : -1.f;
   const float st = sgn * P.tau;
   for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
     float M = -INFINITY, S = 0.f;
-    for (int i = ia; i <= ib; ++i) {
-      const float m = smask((float)i, fa, fb, mc, meps);
-      if (m <= 0.f) continue;
-      const float z = st * cv.get(q + i);
-      if (z > M) { S = fmaf(S, expf(M - z), m); M = z; }
-      else S = fmaf(m, expf(z - M), S);
+    for (int i = 0; i < len; ++i) {
+      const float m = w[i];
+      const float z = st * cv.get(q + ia + i);
+      if (z > M) { S = fmaf(S, __expf(M - z), m); M = z; }
+      else S = fmaf(m, __expf(z - M), S);
     }
-    o.put(q, M == -INFINITY ? sgn * -INFINITY : sgn * (M + logf(S)) * P.inv_tau);
+    o.put(q, M == -INFINITY ? sgn * -INFINITY : sgn * (M + __logf(S)) * P.inv_tau);
   }
 }
 
@@ -729,35 +735,40 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
   } else {
     const ChildView cv = child_view(C, nd, nd.c0);
     if (op == OP_EVSM || op == OP_ALWSM) {
-      // smooth-mask window: direct scatter over the support, plus bound gradients
+      // smooth-mask window.  Signal part as a gather (no atomics):
+      //   x̄_j += sum_{i in support, q = j - i in [A0, A1)} g_q m_i e^{sgn tau (x_j - y_q)}
+      // (every term <= |g_q|), bound part per parent sample over the two edge bands:
+      //   ā += g_q (sgn/tau) sum_i dm_i/da e^{sgn tau (x_{q+i} - y_q)}, likewise b̄.
       NodeRt &rt = C.rt[n];
       const float sgn = op == OP_EVSM ? 1.f : -1.f;
-      const float c = P.mask_c, eps = P.mask_eps, fa = rt.fa, fb = rt.fb;
-      const int ia = rt.ia, ib = rt.ib;
-      float ga = 0.f, gbv = 0.f;
-      for (int qb = A0; qb < A1; qb += NT) {
-        const int q = qb + threadIdx.x;
-        if (q < A1) {
+      const float st = sgn * tau;
+      const int ia = rt.ia, ib = rt.ib, len = ib - ia + 1;
+      const float *w = rt.tab, *wa = rt.tab + len, *wb = rt.tab + 2 * len;
+      for (int j = A0 + ia + threadIdx.x; j < A1 + ib; j += NT) {
+        int src;
+        const float x = cv.get(j, src);
+        if (src < 0) continue;
+        const int ilo = max(ia, j - (A1 - 1)), ihi = min(ib, j - A0);
+        float acc = 0.f;
+        const float sx = st * x;
+        for (int i = ilo; i <= ihi; ++i) {
+          const int q = j - i;
           const float g = me.g(q);
-          const float y = me.val(q);
-          const bool own = q >= own0 && q < own1;
-          if (g != 0.f) {
-            for (int i = ia; i <= ib; ++i) {
-              const float fi = (float)i;
-              const float sa = sigmoidf_(c * (fi - fa)), sb = sigmoidf_(c * (fi - fb));
-              const float m = sa - sb - eps;
-              if (m <= 0.f) continue;
-              int src;
-              const float x = cv.get(q + i, src);
-              const float e = expf(sgn * tau * (x - y));
-              a0.add_atomic(src, g * m * e);
-              if (own) {
-                ga += g * sgn * P.inv_tau * (-c * sa * (1.f - sa)) * e;
-                gbv += g * sgn * P.inv_tau * (c * sb * (1.f - sb)) * e;
-              }
-            }
-          }
+          acc = fmaf(g * w[i - ia], __expf(sx - st * me.val(q)), acc);
         }
+        a0.add_owned(src, acc);
+      }
+      float ga = 0.f, gbv = 0.f;
+      for (int q = A0 + threadIdx.x; q < A1; q += NT) {
+        if (q < own0 || q >= own1) continue;
+        const float g = me.g(q);
+        if (g == 0.f) continue;
+        const float sy = st * me.val(q);
+        float sa = 0.f, sb = 0.f;
+        for (int i = ia; i <= rt.band_a; ++i) sa = fmaf(wa[i - ia], __expf(st * cv.get(q + i) - sy), sa);
+        for (int i = rt.band_b; i <= ib; ++i) sb = fmaf(wb[i - ia], __expf(st * cv.get(q + i) - sy), sb);
+        ga = fmaf(g * sgn * P.inv_tau, sa, ga);
+        gbv = fmaf(g * sgn * P.inv_tau, sb, gbv);
       }
       accumulate_shared(&rt.ga, ga);
       accumulate_shared(&rt.gb, gbv);
@@ -780,13 +791,18 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
       int src;
       const float x = cv.get(j, src);
       if (src < 0) return;
-      a0.add_owned(src, r.s * expf(st * x + r.m));
+      a0.add_owned(src, r.s * __expf(st * x + r.m));
     };
     window_any<LseM>(ib - ia + 1, A0 + ia, A1 + ib, -ib, -ia, elem, out, C.scratch);
   }
 }
 
-// smooth Until adjoint (kept separate: it needs a per-thread array of length b+1)
+// Smooth Until adjoint.  With L_i = log(S_i + Q_i) = -tau z_i and tau U = log sum_i e^{-L_i}:
+//   dU/dpsi_{q+i} = e^{tau(z_i - U)} e^{tau(z_i - psi_i)}
+//   dU/dphi_{q+k} = e^{tau(P_k - phi_k)} D_k,  D_k = [k>=a] e^{tau(2 z_k - U - P_k)} + e^{tau(P_{k+1}-P_k)} D_{k+1}
+// where P_k = -(1/tau) log S_k.  A forward pass over the taps stores P_k and z_k in the
+// per-thread workspace arrays (2 (b+1) floats), a backward pass runs the D recursion; every
+// exponent above is <= 0, so nothing overflows.
 __device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, float *Pk, long long pstride) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
@@ -795,48 +811,35 @@ __device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, float 
   const ChildAdj ap = child_adj(C, nd.c0), aq = child_adj(C, nd.c1);
   const float tau = P.tau, itau = P.inv_tau;
   const int ia = C.rt[n].ia, ib = C.rt[n].ib;
+  float *Zk = Pk + (long long)P.ut_len * pstride;
   for (int q = A0 + threadIdx.x; q < A1; q += blockDim.x) {
     const float g = me.g(q);
     if (g == 0.f) continue;
-    const float U = me.val(q);
-    float M1 = -INFINITY, S1 = 0.f;
-    // forward pass: P_k for k = 0..ib; psi adjoint on the fly
+    const float tU = tau * me.val(q);
+    LseAcc S;
     for (int k = 0; k <= ib; ++k) {
-      const float zp = -tau * cp.get(q + k);
-      if (zp != -INFINITY) {
-        if (zp > M1) { S1 = fmaf(S1, expf(M1 - zp), 1.f); M1 = zp; }
-        else S1 += expf(zp - M1);
-      }
-      const float Pv = M1 == -INFINITY ? INFINITY : -(M1 + logf(S1)) * itau;
-      Pk[k * pstride] = Pv;
+      S.add(-tau * cp.get(q + k));
+      const float ls = S.log();
+      Pk[k * pstride] = ls == -INFINITY ? INFINITY : -ls * itau;
       if (k >= ia) {
         int sq;
-        const float qv = cq.get(q + k, sq);
-        float z;
-        if (isinf(Pv) || isinf(qv)) z = Pv < qv ? Pv : qv;
-        else z = fminf(Pv, qv) - log1pf(expf(-tau * fabsf(Pv - qv))) * itau;
-        const float alpha = expf(tau * (z - U));
-        const float gq = isinf(qv) ? 0.f : 1.f / (1.f + expf(-tau * (Pv - qv)));
-        aq.add_atomic(sq, g * alpha * gq);
+        const float zq = -tau * cq.get(q + k, sq);
+        const float L = log_s_plus_q(S, zq);
+        Zk[k * pstride] = -L * itau;
+        if (zq != -INFINITY && L != -INFINITY) aq.add_atomic(sq, g * __expf(-L - tU + zq - L));
       }
     }
-    // backward pass over k: D_k = [k>=a] alpha_k beta_k + e^{tau (P_{k+1}-P_k)} D_{k+1}
     float Dn = 0.f, Pnext = 0.f;
     for (int k = ib; k >= 0; --k) {
       const float Pv = Pk[k * pstride];
-      float Dk = (k < ib && !isinf(Pv)) ? expf(tau * (Pnext - Pv)) * Dn : 0.f;
-      if (k >= ia) {
-        const float qv = cq.get(q + k);
-        float z;
-        if (isinf(Pv) || isinf(qv)) z = Pv < qv ? Pv : qv;
-        else z = fminf(Pv, qv) - log1pf(expf(-tau * fabsf(Pv - qv))) * itau;
-        const float alpha = expf(tau * (z - U));
-        const float beta = isinf(Pv) ? 0.f : 1.f / (1.f + expf(-tau * (qv - Pv)));
-        Dk += alpha * beta;
+      float Dk = (k < ib && !isinf(Pv)) ? __expf(tau * (Pnext - Pv)) * Dn : 0.f;
+      if (k >= ia && !isinf(Pv)) {
+        const float tz = tau * Zk[k * pstride];
+        Dk += __expf(2.f * tz - tU - tau * Pv);
       }
       int sp;
       const float pv = cp.get(q + k, sp);
-      if (!isinf(pv) && !isinf(Pv)) ap.add_atomic(sp, g * expf(tau * (Pv - pv)) * Dk);
+      if (!isinf(pv) && !isinf(Pv)) ap.add_atomic(sp, g * __expf(tau * (Pv - pv)) * Dk);
       Dn = Dk;
       Pnext = Pv;
     }
@@ -902,8 +905,37 @@ __device__ void setup_geometry(Cta &C, const float *bounds, float *ws_cta, char 
       r.c0 = nd.c0;
       r.c1 = nd.c1;
       r.pred_k = -1;
+      r.tab = nd.tab_off >= 0 ? reinterpret_cast<float *>(smem) + nd.tab_off : nullptr;
+      if (r.tab) {
+        if (r.ib - r.ia + 1 > nd.tab_len) {   // cannot happen for bounds within the caps
+          if (status) atomicExch(status, 1);
+          r.ib = r.ia + nd.tab_len - 1;
+        }
+        // beyond 22/c from an edge, sigma(c d)(1 - sigma(c d)) < e^-22: the bound gradient
+        // terms there are below float resolution of the sums they join
+        const float band = 22.f / P.mask_c;
+        r.band_a = min(r.ib, (int)ceilf(a + band));
+        r.band_b = max(r.ia, (int)floorf(b - band));
+      }
     }
     for (int k = 0; k < P.npred; ++k) C.rt[P.pred[k]].pred_k = k;
+  }
+  __syncthreads();
+  // smooth-mask tables m_i, dm_i/da, dm_i/db over the support (Eq. smooth mask)
+  for (int n = 0; n < P.n; ++n) {
+    const NodeRt &r = C.rt[n];
+    if (!r.tab) continue;
+    const int len = r.ib - r.ia + 1;
+    const float c = P.mask_c, eps = P.mask_eps;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      const float fi = (float)(r.ia + i);
+      const float sa = 1.f / (1.f + expf(-c * (fi - r.fa)));
+      const float sb = 1.f / (1.f + expf(-c * (fi - r.fb)));
+      const float m = sa - sb - eps;
+      r.tab[i] = m > 0.f ? m : 0.f;
+      r.tab[len + i] = m > 0.f ? -c * sa * (1.f - sa) : 0.f;
+      r.tab[2 * len + i] = m > 0.f ? c * sb * (1.f - sb) : 0.f;
+    }
   }
   __syncthreads();
 }
