@@ -291,7 +291,7 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
 
   // launch shape
   int bps = 0;
-  e = stl_blocks_per_sm(threads, bwd ? 1 : 0, p.mode == STL_SMOOTH ? 1 : 0, P.smem_words * 4, &bps);
+  e = stl_blocks_per_sm(threads, bwd ? 1 : 0, p.mode == STL_SMOOTH ? 1 : 0, 0, P.smem_words * 4, &bps);
   if (e) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (bps < 1) return fail(STL_ERR_UNSUPPORTED, "kernel does not fit on an SM (%d B shared)", P.smem_words * 4);
   const long long slots = (long long)sms * bps;
@@ -638,7 +638,7 @@ stl_status stl_set_prepare(stl_set_handle s, int64_t n_traces, int64_t T_max, co
   int sms = 0, bps = 0;
   int e = stl_num_sms(&sms);
   if (e) return cuda_fail(e, "cudaDeviceGetAttribute(multiprocessors)");
-  e = stl_blocks_per_sm(threads, backward ? 1 : 0, p->mode == STL_SMOOTH ? 1 : 0, smem * 4, &bps);
+  e = stl_blocks_per_sm(threads, backward ? 1 : 0, p->mode == STL_SMOOTH ? 1 : 0, 1, smem * 4, &bps);
   if (e) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (bps < 1) return fail(STL_ERR_UNSUPPORTED, "kernel does not fit on an SM (%d B shared)", smem * 4);
   const long long grid = std::max(1LL, std::min((long long)sms * bps, (long long)n_traces));

@@ -105,7 +105,7 @@ struct LaunchArgs {
 };
 int stl_launch_main(const KProgram &P, const LaunchArgs &A);   // returns a cudaError_t
 int stl_max_smem_optin(int *bytes);
-int stl_blocks_per_sm(int threads, int bwd, int smooth, int smem_bytes, int *blocks);
+int stl_blocks_per_sm(int threads, int bwd, int smooth, int ragged, int smem_bytes, int *blocks);
 int stl_num_sms(int *sms);
 int stl_read_clear_status(void *stream, int *status);
 int stl_status_ptr(int **ptr);

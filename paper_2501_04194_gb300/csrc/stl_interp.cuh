@@ -210,7 +210,7 @@ __device__ __forceinline__ void window_reduce(int q0, int q1, int ia, int ib, co
         }
       }
     }
-    __syncthreads();
+    if (p0 + NT * R < q1) __syncthreads();   // the caller synchronises after the last pass
   }
 }
 
@@ -379,6 +379,9 @@ template <int DD>
 __device__ __forceinline__ void pred_batch(const float *__restrict__ xs, const float *w, bool gt, float pc,
                                            const NodeOut &out, int F, int E) {
   const int NT = blockDim.x;
+  float wr[DD];
+#pragma unroll
+  for (int d = 0; d < DD; ++d) wr[d] = w[d];
   for (int base = F + threadIdx.x; base < E; base += NT * BATCH) {
     float x[BATCH][DD];
 #pragma unroll
@@ -391,9 +394,9 @@ __device__ __forceinline__ void pred_batch(const float *__restrict__ xs, const f
     for (int k = 0; k < BATCH; ++k) {
       const int q = base + k * NT;
       if (q < E) {
-        float s = __fmul_rn(w[0], x[k][0]);
+        float s = __fmul_rn(wr[0], x[k][0]);
 #pragma unroll
-        for (int d = 1; d < DD; ++d) s = __fadd_rn(s, __fmul_rn(w[d], x[k][d]));
+        for (int d = 1; d < DD; ++d) s = __fadd_rn(s, __fmul_rn(wr[d], x[k][d]));
         out.put(q, gt ? __fsub_rn(s, pc) : __fsub_rn(pc, s));
       }
     }
@@ -1111,12 +1114,16 @@ __device__ void signal_gradient(const Cta &C, float *gs, int pst, int j0, int j1
 // Dense launches walk (trace, segment) items with a static stride and use the program passed
 // by value.  Ragged launches (A.table != nullptr) take whole traces from an atomic work
 // counter, in the caller's order, and read each trace's program from the device table.
-template <int NT, bool BWD, bool SMOOTH>
+// Dense and ragged launches are separate instantiations: in the dense one every program read
+// resolves to the by-value parameter (constant bank), in the ragged one to the device table.
+// No minimum-blocks hint: a register cap sized for three 256-thread CTAs per SM made the
+// forward re-load program fields inside its sample loops (measured 25-30% slower).
+template <int NT, bool BWD, bool SMOOTH, bool RAGGED>
 __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram Pdense, LaunchArgs A) {
   extern __shared__ float4 smem4[];
   char *smem = reinterpret_cast<char *>(smem4);
   __shared__ long long s_item;
-  const bool ragged = A.table != nullptr;
+  constexpr bool ragged = RAGGED;
   Cta C;
   C.sig = A.sig;
   const int gwords = ragged ? A.gwords : Pdense.gwords;
@@ -1126,10 +1133,17 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
   float *ut = (A.ws && ut_len > 0) ? A.ws + ut_off + blockIdx.x * (long long)NT + threadIdx.x : nullptr;
   const long long ut_stride = (long long)gridDim.x * NT;
   const long long n_items = ragged ? A.n_traces : Pdense.n_items;
+  if constexpr (!ragged) {
+    C.P = &Pdense;
+    C.T = (int)Pdense.T;
+    C.rt = reinterpret_cast<NodeRt *>(smem + (size_t)Pdense.rt_off * 4);
+    C.scratch = smem + (size_t)Pdense.scratch_off * 4;
+    C.root = Pdense.n - 1;
+  }
 
   for (long long it = 0;; ++it) {
     long long item;
-    if (ragged) {
+    if constexpr (ragged) {
       if (threadIdx.x == 0) s_item = atomicAdd(A.counter, 1ULL);
       __syncthreads();
       item = s_item;
@@ -1139,7 +1153,7 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
     }
     if (item >= n_items) break;
     int s0, s1;
-    if (ragged) {
+    if constexpr (ragged) {
       // per-trace data is checked here: a bad entry sets the status word and skips the trace
       const long long b = A.order ? (long long)A.order[item] : item;
       if (b < 0 || b >= A.n_traces) { if (threadIdx.x == 0 && A.status) atomicExch(A.status, 1); continue; }
@@ -1157,19 +1171,19 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
       s0 = 0;
       s1 = C.T;
     } else {
-      C.P = &Pdense;
       C.b = item / Pdense.segs_per_trace;
-      C.T = (int)Pdense.T;
       C.row0 = C.b * (long long)C.T;
       const int sidx = (int)(item % Pdense.segs_per_trace);
       s0 = sidx * Pdense.seg;
       s1 = (s0 + Pdense.seg < C.T) ? s0 + Pdense.seg : C.T;
     }
-    const KProgram &P = *C.P;
+    const KProgram &P = ragged ? *C.P : Pdense;
     const int T = C.T;
-    C.rt = reinterpret_cast<NodeRt *>(smem + (size_t)P.rt_off * 4);
-    C.scratch = smem + (size_t)P.scratch_off * 4;
-    C.root = P.n - 1;
+    if constexpr (ragged) {
+      C.rt = reinterpret_cast<NodeRt *>(smem + (size_t)P.rt_off * 4);
+      C.scratch = smem + (size_t)P.scratch_off * 4;
+      C.root = P.n - 1;
+    }
     C.out_row = BWD ? nullptr : A.out + C.row0;
     setup_geometry(C, A.bounds, ws_cta, smem, A.status);
     if (BWD) {
@@ -1278,19 +1292,19 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
 }  // namespace
 
 // instantiation helpers used by the per-variant translation units
-#define STL_DEFINE_VARIANT(NT, BWD, SM, NAME)                                                     \
+#define STL_DEFINE_VARIANT(NT, BWD, SM, RG, NAME)                                                 \
   int stl_launch_##NAME(const KProgram &P, const LaunchArgs &A) {                                \
     const size_t smem = (size_t)P.smem_words * 4;                                                 \
-    cudaError_t e = cudaFuncSetAttribute(stl_main<NT, BWD, SM>,                                   \
+    cudaError_t e = cudaFuncSetAttribute(stl_main<NT, BWD, SM, RG>,                               \
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return (int)e;                                                          \
-    stl_main<NT, BWD, SM><<<A.grid, NT, smem, (cudaStream_t)A.stream>>>(P, A);                    \
+    stl_main<NT, BWD, SM, RG><<<A.grid, NT, smem, (cudaStream_t)A.stream>>>(P, A);                \
     return (int)cudaGetLastError();                                                               \
   }                                                                                               \
   int stl_occupancy_##NAME(int smem_bytes, int *blocks) {                                         \
-    cudaError_t e = cudaFuncSetAttribute(stl_main<NT, BWD, SM>,                                   \
+    cudaError_t e = cudaFuncSetAttribute(stl_main<NT, BWD, SM, RG>,                               \
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes); \
     if (e != cudaSuccess) return (int)e;                                                          \
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, stl_main<NT, BWD, SM>, NT,  \
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, stl_main<NT, BWD, SM, RG>, NT, \
                                                               smem_bytes);                        \
   }

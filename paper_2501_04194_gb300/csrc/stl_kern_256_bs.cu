@@ -1,5 +1,5 @@
-// One instantiation of the interpreter: 256 threads, backward, smooth semantics
+// One instantiation of the interpreter: 256 threads, backward, smooth semantics, dense (program by value)
 // (one translation unit per variant so that the variants compile in parallel).
 #include "stl_interp.cuh"
 
-STL_DEFINE_VARIANT(256, true, true, 256_bs)
+STL_DEFINE_VARIANT(256, true, true, false, 256_bs)

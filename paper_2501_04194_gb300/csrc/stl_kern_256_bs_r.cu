@@ -1,0 +1,5 @@
+// One instantiation of the interpreter: 256 threads, backward, smooth semantics, ragged (device program table)
+// (one translation unit per variant so that the variants compile in parallel).
+#include "stl_interp.cuh"
+
+STL_DEFINE_VARIANT(256, true, true, true, 256_bs_r)

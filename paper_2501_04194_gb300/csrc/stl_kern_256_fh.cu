@@ -1,5 +1,5 @@
-// One instantiation of the interpreter: 256 threads, forward, hard semantics
+// One instantiation of the interpreter: 256 threads, forward, hard semantics, dense (program by value)
 // (one translation unit per variant so that the variants compile in parallel).
 #include "stl_interp.cuh"
 
-STL_DEFINE_VARIANT(256, false, false, 256_fh)
+STL_DEFINE_VARIANT(256, false, false, false, 256_fh)

@@ -1,5 +1,5 @@
-// One instantiation of the interpreter: 512 threads, backward, smooth semantics
+// One instantiation of the interpreter: 512 threads, backward, smooth semantics, dense (program by value)
 // (one translation unit per variant so that the variants compile in parallel).
 #include "stl_interp.cuh"
 
-STL_DEFINE_VARIANT(512, true, true, 512_bs)
+STL_DEFINE_VARIANT(512, true, true, false, 512_bs)

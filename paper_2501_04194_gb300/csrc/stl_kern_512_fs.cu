@@ -1,5 +1,5 @@
-// One instantiation of the interpreter: 512 threads, forward, smooth semantics
+// One instantiation of the interpreter: 512 threads, forward, smooth semantics, dense (program by value)
 // (one translation unit per variant so that the variants compile in parallel).
 #include "stl_interp.cuh"
 
-STL_DEFINE_VARIANT(512, false, true, 512_fs)
+STL_DEFINE_VARIANT(512, false, true, false, 512_fs)

@@ -3,22 +3,13 @@
 
 #include "stl_internal.cuh"
 
-int stl_launch_512_fh(const KProgram &P, const LaunchArgs &A);
-int stl_occupancy_512_fh(int smem_bytes, int *blocks);
-int stl_launch_512_fs(const KProgram &P, const LaunchArgs &A);
-int stl_occupancy_512_fs(int smem_bytes, int *blocks);
-int stl_launch_512_bh(const KProgram &P, const LaunchArgs &A);
-int stl_occupancy_512_bh(int smem_bytes, int *blocks);
-int stl_launch_512_bs(const KProgram &P, const LaunchArgs &A);
-int stl_occupancy_512_bs(int smem_bytes, int *blocks);
-int stl_launch_256_fh(const KProgram &P, const LaunchArgs &A);
-int stl_occupancy_256_fh(int smem_bytes, int *blocks);
-int stl_launch_256_fs(const KProgram &P, const LaunchArgs &A);
-int stl_occupancy_256_fs(int smem_bytes, int *blocks);
-int stl_launch_256_bh(const KProgram &P, const LaunchArgs &A);
-int stl_occupancy_256_bh(int smem_bytes, int *blocks);
-int stl_launch_256_bs(const KProgram &P, const LaunchArgs &A);
-int stl_occupancy_256_bs(int smem_bytes, int *blocks);
+#define STL_DECLARE_VARIANT(NAME)                                 \
+  int stl_launch_##NAME(const KProgram &P, const LaunchArgs &A); \
+  int stl_occupancy_##NAME(int smem_bytes, int *blocks);
+STL_DECLARE_VARIANT(512_fh) STL_DECLARE_VARIANT(512_fs) STL_DECLARE_VARIANT(512_bh) STL_DECLARE_VARIANT(512_bs)
+STL_DECLARE_VARIANT(256_fh) STL_DECLARE_VARIANT(256_fs) STL_DECLARE_VARIANT(256_bh) STL_DECLARE_VARIANT(256_bs)
+STL_DECLARE_VARIANT(512_fh_r) STL_DECLARE_VARIANT(512_fs_r) STL_DECLARE_VARIANT(512_bh_r) STL_DECLARE_VARIANT(512_bs_r)
+STL_DECLARE_VARIANT(256_fh_r) STL_DECLARE_VARIANT(256_fs_r) STL_DECLARE_VARIANT(256_bh_r) STL_DECLARE_VARIANT(256_bs_r)
 
 namespace {
 __device__ int g_device_status;   // sticky per-device status word (0 = OK)
@@ -28,34 +19,37 @@ int stl_status_ptr(int **ptr) {
   return (int)cudaGetSymbolAddress((void **)ptr, g_device_status);
 }
 
+namespace {
+using LaunchFn = int (*)(const KProgram &, const LaunchArgs &);
+using OccFn = int (*)(int, int *);
+// index: ragged * 8 + (threads == 256) * 4 + backward * 2 + smooth
+const LaunchFn k_launch[16] = {
+    stl_launch_512_fh,   stl_launch_512_fs,   stl_launch_512_bh,   stl_launch_512_bs,
+    stl_launch_256_fh,   stl_launch_256_fs,   stl_launch_256_bh,   stl_launch_256_bs,
+    stl_launch_512_fh_r, stl_launch_512_fs_r, stl_launch_512_bh_r, stl_launch_512_bs_r,
+    stl_launch_256_fh_r, stl_launch_256_fs_r, stl_launch_256_bh_r, stl_launch_256_bs_r};
+const OccFn k_occupancy[16] = {
+    stl_occupancy_512_fh,   stl_occupancy_512_fs,   stl_occupancy_512_bh,   stl_occupancy_512_bs,
+    stl_occupancy_256_fh,   stl_occupancy_256_fs,   stl_occupancy_256_bh,   stl_occupancy_256_bs,
+    stl_occupancy_512_fh_r, stl_occupancy_512_fs_r, stl_occupancy_512_bh_r, stl_occupancy_512_bs_r,
+    stl_occupancy_256_fh_r, stl_occupancy_256_fs_r, stl_occupancy_256_bh_r, stl_occupancy_256_bs_r};
+
+int variant(int threads, int bwd, int smooth, int ragged) {
+  if (threads != 512 && threads != 256) return -1;
+  return (ragged ? 8 : 0) + (threads == 256 ? 4 : 0) + (bwd ? 2 : 0) + (smooth ? 1 : 0);
+}
+}  // namespace
+
 int stl_launch_main(const KProgram &P, const LaunchArgs &A) {
-  const int v = (A.threads == 256 ? 4 : 0) + (P.bwd ? 2 : 0) + (P.mode == 1 ? 1 : 0);
-  if (A.threads != 512 && A.threads != 256) return (int)cudaErrorInvalidValue;
-  switch (v) {
-    case 0: return stl_launch_512_fh(P, A);
-    case 1: return stl_launch_512_fs(P, A);
-    case 2: return stl_launch_512_bh(P, A);
-    case 3: return stl_launch_512_bs(P, A);
-    case 4: return stl_launch_256_fh(P, A);
-    case 5: return stl_launch_256_fs(P, A);
-    case 6: return stl_launch_256_bh(P, A);
-    default: return stl_launch_256_bs(P, A);
-  }
+  const int v = variant(A.threads, P.bwd, P.mode == 1, A.table != nullptr);
+  if (v < 0) return (int)cudaErrorInvalidValue;
+  return k_launch[v](P, A);
 }
 
-int stl_blocks_per_sm(int threads, int bwd, int smooth, int smem_bytes, int *blocks) {
-  const int v = (threads == 256 ? 4 : 0) + (bwd ? 2 : 0) + (smooth ? 1 : 0);
-  if (threads != 512 && threads != 256) return (int)cudaErrorInvalidValue;
-  switch (v) {
-    case 0: return stl_occupancy_512_fh(smem_bytes, blocks);
-    case 1: return stl_occupancy_512_fs(smem_bytes, blocks);
-    case 2: return stl_occupancy_512_bh(smem_bytes, blocks);
-    case 3: return stl_occupancy_512_bs(smem_bytes, blocks);
-    case 4: return stl_occupancy_256_fh(smem_bytes, blocks);
-    case 5: return stl_occupancy_256_fs(smem_bytes, blocks);
-    case 6: return stl_occupancy_256_bh(smem_bytes, blocks);
-    default: return stl_occupancy_256_bs(smem_bytes, blocks);
-  }
+int stl_blocks_per_sm(int threads, int bwd, int smooth, int ragged, int smem_bytes, int *blocks) {
+  const int v = variant(threads, bwd, smooth, ragged);
+  if (v < 0) return (int)cudaErrorInvalidValue;
+  return k_occupancy[v](smem_bytes, blocks);
 }
 
 int stl_max_smem_optin(int *bytes) {
