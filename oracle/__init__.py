@@ -25,7 +25,7 @@ _lib = None
 
 # node encoding private to the oracle (mirrors the enum in stl_oracle.c)
 _OPS = {"pred>": 0, "pred<": 1, "true": 2, "not": 3, "and": 4, "or": 5, "eventually": 6,
-        "always": 7, "until": 8, "eventually_sm": 9, "always_sm": 10}
+        "always": 7, "until": 8, "eventually_sm": 9, "always_sm": 10, "norm>": 11, "norm<": 12}
 HARD, SMOOTH = 0, 1
 
 
@@ -96,6 +96,15 @@ class _Flat:
             nd.w_off = len(self.weights)
             self.weights.extend(float(np.float32(v)) for v in w)
             nd.c = float(np.float32(c))
+        elif op == "norm":
+            _, rel, scale, centre, r = f
+            if len(scale) != self.D or len(centre) != self.D:
+                raise ValueError("norm predicate scale/centre length != D")
+            nd.op = _OPS["norm>" if rel == ">" else "norm<"]
+            nd.w_off = len(self.weights)
+            self.weights.extend(float(np.float32(v)) for v in scale)
+            self.weights.extend(float(np.float32(v)) for v in centre)
+            nd.c = float(np.float32(r))
         elif op == "true":
             nd.op = _OPS["true"]
         elif op == "not":

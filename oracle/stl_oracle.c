@@ -35,7 +35,10 @@
  *       every operation is done in double and rounded to float (exact for +,-,x under
  *       double rounding since 53 >= 2*24+2); ``exact`` skips the rounding.
  *       Signals and bounds arrive as double (float32 inputs widen exactly), so that
- *       finite-difference checks can perturb them in double precision.
+ *       finite-difference checks can perturb them in double precision;
+ *   R8  a norm predicate (Sec. VI-A "inside" a region) is mu(x) = ||diag(s)(x - g)||_2 with
+ *       per-dimension scales s (0 drops a dimension) and centre g; "<" gives r - mu(x)
+ *       (inside the ball of radius r), ">" gives mu(x) - r (outside it).
  */
 #include <math.h>
 #include <pthread.h>
@@ -46,9 +49,10 @@
 
 enum {
   O_PRED_GT = 0, O_PRED_LT = 1, O_TRUE = 2, O_NOT = 3, O_AND = 4, O_OR = 5,
-  O_EV = 6, O_ALW = 7, O_UNTIL = 8, O_EV_SM = 9, O_ALW_SM = 10
+  O_EV = 6, O_ALW = 7, O_UNTIL = 8, O_EV_SM = 9, O_ALW_SM = 10, O_NORM_GT = 11, O_NORM_LT = 12
 };
 enum { O_PAD_LAST = 0, O_PAD_CONST = 1 };
+enum { O_MAX_D = 64 };   /* largest signal dimension the oracle accepts */
 enum { O_HARD = 0, O_SMOOTH = 1 };
 
 typedef struct {
@@ -184,18 +188,43 @@ static void work_free(work *wk, int n) {
   free(wk->val); free(wk->adj); free(wk->tmp); free(wk->tmp2); free(wk->tmp3); free(wk->itmp);
 }
 
-/* predicate mu(x_t) - c or c - mu(x_t), Eq. "quantitative" (R7) */
+/* mu(x) for a norm predicate: the Euclidean distance of the scaled offset from a centre,
+ * mu(x) = sqrt(sum_d u_d^2), u_d = s_d (x_d - g_d), with s = w[0..D) and g = w[D..2D).  This
+ * is the "inside region" predicate of the trajectory-planning example, Sec. VI-A (R8).
+ * Rounded mode: every operation in float32 order, sum left to right, then a correctly
+ * rounded square root (exact under double rounding, as for the other operations). */
+static double norm_mu(const octx *cx, const onode *nd, const double *row, double *u) {
+  const double *sc = cx->w + nd->w_off, *g = sc + cx->D;
+  double q = 0.0;
+  for (int d = 0; d < cx->D; d++) {
+    if (cx->exact) {
+      u[d] = sc[d] * (row[d] - g[d]);
+      q += u[d] * u[d];
+    } else {
+      u[d] = f32(sc[d] * f32(row[d] - g[d]));
+      q = d == 0 ? f32(u[d] * u[d]) : f32(q + f32(u[d] * u[d]));
+    }
+  }
+  return cx->exact ? sqrt(q) : f32(sqrt(q));
+}
+
+/* predicate mu(x_t) - c or c - mu(x_t), Eq. "quantitative" (R7); mu affine or a norm */
 static double pred_eval(const octx *cx, const onode *nd, const double *row) {
   const double *w = cx->w + nd->w_off;
   double s;
-  if (cx->exact) {
+  const int gt = nd->op == O_PRED_GT || nd->op == O_NORM_GT;
+  if (nd->op == O_NORM_GT || nd->op == O_NORM_LT) {
+    double u[O_MAX_D];
+    s = norm_mu(cx, nd, row, u);
+  } else if (cx->exact) {
     s = 0.0;
     for (int d = 0; d < cx->D; d++) s += w[d] * row[d];
-    return nd->op == O_PRED_GT ? s - nd->c : nd->c - s;
+  } else {
+    s = f32(w[0] * row[0]);
+    for (int d = 1; d < cx->D; d++) s = f32(s + f32(w[d] * row[d]));
   }
-  s = f32(w[0] * row[0]);
-  for (int d = 1; d < cx->D; d++) s = f32(s + f32(w[d] * row[d]));
-  return nd->op == O_PRED_GT ? f32(s - nd->c) : f32(nd->c - s);
+  if (cx->exact) return gt ? s - nd->c : nd->c - s;
+  return gt ? f32(s - nd->c) : f32(nd->c - s);
 }
 
 /* offsets i of a smooth-mask window for trace b: [0, last] (R6) */
@@ -212,6 +241,8 @@ static void forward_node(const octx *cx, work *wk, int k, int64_t b, const doubl
   switch (nd->op) {
     case O_PRED_GT:
     case O_PRED_LT:
+    case O_NORM_GT:
+    case O_NORM_LT:
       for (int64_t t = 0; t < T; t++) y[t] = pred_eval(cx, nd, xs + t * cx->D);
       break;
     case O_TRUE:
@@ -321,6 +352,8 @@ static void backward_node(const octx *cx, work *wk, int k, int64_t b, int64_t T,
   switch (nd->op) {
     case O_PRED_GT:
     case O_PRED_LT:
+    case O_NORM_GT:
+    case O_NORM_LT:
     case O_TRUE:
       break;
     case O_NOT: {
@@ -502,13 +535,24 @@ static int run_trace(octx *cx, int64_t b) {
     for (int k = cx->n_nodes - 1; k >= 0; k--) backward_node(cx, &wk, k, b, T, gb);
     double *gs = cx->gsig + r0 * cx->D;
     memset(gs, 0, (size_t)T * cx->D * sizeof(double));
-    /* d pred / d x_{t,d} = +w_d (GT) or -w_d (LT) */
+    /* d pred / d x_{t,d} = +w_d (GT) or -w_d (LT) for an affine mu;
+     * for a norm mu: +-s_d u_d / mu, and 0 at mu = 0 (a subgradient of the norm there) */
     for (int k = 0; k < cx->n_nodes; k++) {
       const onode *nd = &cx->nodes[k];
-      if (nd->op != O_PRED_GT && nd->op != O_PRED_LT) continue;
-      const double sg = nd->op == O_PRED_GT ? 1.0 : -1.0;
-      for (int64_t t = 0; t < T; t++)
-        for (int d = 0; d < cx->D; d++) gs[t * cx->D + d] += sg * cx->w[nd->w_off + d] * wk.adj[k][t];
+      const int norm = nd->op == O_NORM_GT || nd->op == O_NORM_LT;
+      if (nd->op != O_PRED_GT && nd->op != O_PRED_LT && !norm) continue;
+      const double sg = (nd->op == O_PRED_GT || nd->op == O_NORM_GT) ? 1.0 : -1.0;
+      for (int64_t t = 0; t < T; t++) {
+        if (norm) {
+          double u[O_MAX_D];
+          const double mu = norm_mu(cx, nd, xs + t * cx->D, u);
+          if (mu == 0.0) continue;
+          for (int d = 0; d < cx->D; d++)
+            gs[t * cx->D + d] += sg * cx->w[nd->w_off + d] * u[d] / mu * wk.adj[k][t];
+        } else {
+          for (int d = 0; d < cx->D; d++) gs[t * cx->D + d] += sg * cx->w[nd->w_off + d] * wk.adj[k][t];
+        }
+      }
     }
   }
   work_free(&wk, cx->n_nodes);
@@ -551,6 +595,7 @@ int oracle_forward(const onode *nodes, int n_nodes, int root, const double *w, i
                    const double *sig, const int64_t *offsets, int64_t B,
                    const double *bounds, int n_slots, int mode, double tau, double mask_c,
                    double mask_eps, int exact, double *out, int n_threads) {
+  if (D < 1 || D > O_MAX_D) return -2;
   octx cx;
   memset(&cx, 0, sizeof cx);
   cx.nodes = nodes; cx.n_nodes = n_nodes; cx.root = root; cx.w = w; cx.D = D;
@@ -567,6 +612,7 @@ int oracle_backward(const onode *nodes, int n_nodes, int root, const double *w, 
                     const double *bounds, int n_slots, int mode, double tau, double mask_c,
                     double mask_eps, int exact, const double *grad_out, double *grad_sig,
                     double *grad_bounds, int n_threads) {
+  if (D < 1 || D > O_MAX_D) return -2;
   octx cx;
   memset(&cx, 0, sizeof cx);
   cx.nodes = nodes; cx.n_nodes = n_nodes; cx.root = root; cx.w = w; cx.D = D;

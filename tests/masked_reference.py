@@ -88,6 +88,14 @@ def evaluate(f, x, hard=True, tau=1.0):
         c = float(np.float32(c))
         mu = x @ torch.tensor(w, dtype=x.dtype)
         return mu - c if rel == ">" else c - mu
+    if op == "norm":
+        # distance of the scaled offset from the centre (Sec. VI-A region predicates)
+        _, rel, sc, g, r = f
+        sc = torch.tensor([float(np.float32(v)) for v in sc], dtype=x.dtype)
+        g = torch.tensor([float(np.float32(v)) for v in g], dtype=x.dtype)
+        mu = torch.sqrt((((x - g) * sc) ** 2).sum(dim=1))
+        r = float(np.float32(r))
+        return mu - r if rel == ">" else r - mu
     if op == "true":
         return torch.full((x.shape[0],), BIG, dtype=x.dtype)
     if op == "not":
@@ -114,6 +122,13 @@ def boolean(f, x, t, T=None):
         c = float(np.float32(c))
         mu = float(sum(wd * float(xd) for wd, xd in zip(w, x[min(t, T - 1)])))
         return mu > c if rel == ">" else mu < c
+    if op == "norm":
+        _, rel, sc, g, r = f
+        row = x[min(t, T - 1)]
+        mu = math.sqrt(sum((float(np.float32(s_)) * (float(xd) - float(np.float32(gd)))) ** 2
+                           for s_, gd, xd in zip(sc, g, row)))
+        r = float(np.float32(r))
+        return mu > r if rel == ">" else mu < r
     if op == "true":
         return True
     if op == "not":

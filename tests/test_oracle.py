@@ -146,7 +146,9 @@ def test_boolean_semantics_sign():
     rng = np.random.default_rng(6)
     forms = [W.config0_formula(), W.Until(1, 3, W.gt([1, 0], 0.0), W.lt([0, 1], 0.2)),
              W.Or(W.Always(0, 2, W.gt([1, 0], 0.3)), W.Not(W.Eventually(1, 4, W.lt([1, 1], 0.0)))),
-             W.Until(0, 2, W.Eventually(0, 1, W.gt([0, 1], -0.2)), W.Always(1, 2, W.gt([1, 0], 0.1)), pad=0.5)]
+             W.Until(0, 2, W.Eventually(0, 1, W.gt([0, 1], -0.2)), W.Always(1, 2, W.gt([1, 0], 0.1)), pad=0.5),
+             W.And(W.Eventually(0, 4, W.norm_lt([1, 1], [0.3, -0.2], 0.9)),
+                   W.Always(0, 3, W.norm_gt([1, 0.5], [-0.4, 0.6], 0.4)))]
     for f in forms:
         for _ in range(20):
             T = int(rng.integers(1, 10))
@@ -243,6 +245,51 @@ def test_predicate_float32_rounding():
     np.testing.assert_array_equal(got, (c - acc).astype(np.float64))
 
 
+def test_norm_predicate_pythagorean_points():
+    """Region predicates of Sec. VI-A at points whose distances are exact integers
+    (3-4-5 and 5-12-13 triangles), so every float32 step is exact: inside = r - dist,
+    outside = dist - r.  A zero scale drops its dimension."""
+    g = (1.0, 2.0, 0.0)
+    pts = np.array([[[4.0, 6.0, 7.0], [1.0, 2.0, -3.0], [6.0, 14.0, 0.5], [-2.0, -2.0, 9.0]]], dtype=np.float32)
+    dist = np.array([5.0, 0.0, 13.0, 5.0])
+    inside = oracle.robustness(W.norm_lt([1, 1, 0], g, 2.5), pts)[0]
+    np.testing.assert_array_equal(inside, (np.float32(2.5) - dist.astype(np.float32)).astype(np.float64))
+    outside = oracle.robustness(W.norm_gt([1, 1, 0], g, 2.5), pts)[0]
+    np.testing.assert_array_equal(outside, -inside)
+    # scales: s = (2, 2, 0) doubles every distance
+    np.testing.assert_array_equal(oracle.robustness(W.norm_gt([2, 2, 0], g, 0.0), pts)[0], 2 * dist)
+
+
+def test_norm_predicate_gradient_closed_form():
+    """d(r - ||x - g||)/dx = -(x - g)/||x - g|| (the unit vector, here (3/5, 4/5)), and the
+    subgradient 0 at the centre; the scale enters squared: s_d^2 (x_d - g_d) / ||.||."""
+    pts = np.array([[[4.0, 6.0], [1.0, 2.0]]], dtype=np.float32)
+    g, _ = oracle.robustness_grad(W.norm_lt([1, 1], [1.0, 2.0], 0.3), pts, np.ones((1, 2)))
+    np.testing.assert_allclose(g[0], [[-0.6, -0.8], [0.0, 0.0]], rtol=0, atol=1e-15)
+    g, _ = oracle.robustness_grad(W.norm_gt([2, 1], [1.0, 2.0], 0.3), pts, np.ones((1, 2)))
+    n = math.sqrt(36 + 16)
+    np.testing.assert_allclose(g[0], [[4 * 3 / n, 4 / n], [0.0, 0.0]], rtol=1e-6)
+
+
+def test_reach_avoid_straight_line():
+    """Eventually inside a goal disc and always outside an obstacle disc along x_t = (t/10, 0):
+    the closest approach to the goal (1, 0) is at t = 10 (margin r_g), to the obstacle
+    (0.5, 0.5) at t = 5 (distance 0.5), so rho_0 = min(r_g, 0.5 - r_o)."""
+    T = 21
+    xs = np.zeros((1, T, 2), dtype=np.float32)
+    xs[0, :, 0] = np.arange(T, dtype=np.float32) / np.float32(10)
+    reach = W.Eventually(0, T - 1, W.norm_lt([1, 1], [1.0, 0.0], 0.3))
+    avoid = W.Always(0, T - 1, W.norm_gt([1, 1], [0.5, 0.5], 0.3))
+    np.testing.assert_allclose(oracle.robustness(reach, xs)[0, 0], 0.3, atol=1e-6)
+    np.testing.assert_allclose(oracle.robustness(avoid, xs)[0, 0], 0.2, atol=1e-6)
+    np.testing.assert_allclose(oracle.robustness(W.And(reach, avoid), xs)[0, 0], 0.2, atol=1e-6)
+    # the hard gradient of rho_0 lands on the obstacle's closest sample: (x_5 - o)/|x_5 - o| = (0, -1)
+    gout = np.zeros((1, T)); gout[0, 0] = 1.0
+    g, _ = oracle.robustness_grad(W.And(reach, avoid), xs, gout)
+    want = np.zeros((T, 2)); want[5] = [0.0, -1.0]
+    np.testing.assert_allclose(g[0], want, atol=1e-6)
+
+
 def test_ragged_equals_dense():
     rng = np.random.default_rng(12)
     s = rng.normal(size=(3, 50, 3)).astype(np.float32)
@@ -270,6 +317,8 @@ GRAD_FORMULAS = [
                 W.Eventually(0, 7, W.gt([0, 0, 1], 0.3))), 3),
     ("untilpad", W.Until(0, 3, W.Eventually(1, 2, W.gt([1, 0], 0.0)), W.lt([0, 1], 0.1), pad=0.4), 2),
     ("alw_or", W.Always(2, 6, W.Or(W.gt([1, -1], 0.0), W.Not(W.lt([0.5, 1], 0.2)))), 2),
+    ("reach_avoid", W.And(W.Eventually(0, 6, W.norm_lt([1, 1], [0.5, -0.2], 0.8)),
+                          W.Always(0, 9, W.norm_gt([1, 0.5], [-0.3, 0.4], 0.5))), 2),
 ]
 
 

@@ -10,6 +10,8 @@ Or / Eventually / Always and the smoothed-interval operators of Sec. V):
 
     ("pred", ">", w, c)        mu(x) - c  with mu(x) = sum_d w[d] * x[d]   (Eq. quantitative)
     ("pred", "<", w, c)        c - mu(x)
+    ("norm", ">", s, g, r)     ||diag(s)(x - g)||_2 - r   (outside a ball; Sec. VI-A regions)
+    ("norm", "<", s, g, r)     r - ||diag(s)(x - g)||_2   (inside it)
     ("true",)                  the constant formula T (rho_max = +inf)
     ("not", f)
     ("and", f, g)              ("or", f, g)
@@ -44,6 +46,14 @@ def gt(w, c):
 
 def lt(w, c):
     return ("pred", "<", tuple(float(v) for v in w), float(c))
+
+
+def norm_gt(scale, centre, r):
+    return ("norm", ">", tuple(float(v) for v in scale), tuple(float(v) for v in centre), float(r))
+
+
+def norm_lt(scale, centre, r):
+    return ("norm", "<", tuple(float(v) for v in scale), tuple(float(v) for v in centre), float(r))
 
 
 def true():
