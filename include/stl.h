@@ -73,7 +73,9 @@ typedef enum {
   STL_OP_ALWAYS = 7,
   STL_OP_UNTIL = 8,         /* child0 U_[a,b] child1 */
   STL_OP_EVENTUALLY_SM = 9, /* sigmoid-masked window, real a < b */
-  STL_OP_ALWAYS_SM = 10
+  STL_OP_ALWAYS_SM = 10,
+  STL_OP_NORM_GT = 11,      /* ||diag(s)(x - g)||_2 - r: outside a ball (Sec. VI-A regions) */
+  STL_OP_NORM_LT = 12       /* r - ||diag(s)(x - g)||_2: inside it */
 } stl_op;
 
 typedef enum { STL_PAD_LAST = 0, STL_PAD_CONST = 1 } stl_pad;
@@ -90,8 +92,9 @@ typedef struct {
                           integers for EVENTUALLY/ALWAYS/UNTIL */
   int32_t pad_mode;    /* stl_pad, for temporal nodes */
   float pad_value;     /* STL_PAD_CONST value */
-  int32_t pred_offset; /* predicates: weights are pred_weights[pred_offset .. pred_offset+D) */
-  float pred_c;        /* predicates: the constant c */
+  int32_t pred_offset; /* predicates: weights are pred_weights[pred_offset .. pred_offset+D);
+                          norm predicates: scales s then centre g, 2D entries from here */
+  float pred_c;        /* predicates: the constant c (the radius r of a norm predicate) */
 } stl_node;
 
 /* Per-call semantics. */

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libstl.so")
 
 STL_HARD, STL_SMOOTH = 0, 1
 OPS = {"pred>": 0, "pred<": 1, "true": 2, "not": 3, "and": 4, "or": 5, "eventually": 6, "always": 7,
-       "until": 8, "eventually_sm": 9, "always_sm": 10}
+       "until": 8, "eventually_sm": 9, "always_sm": 10, "norm>": 11, "norm<": 12}
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported", -3: "CUDA error", -4: "workspace too small",
           -5: "device wait timed out", -6: "device-side data check failed"}
 
@@ -91,7 +91,8 @@ def flatten(tree, D):
     """Nested-tuple formula -> (list of StlNode children-first with the root last, weights, n_slots).
 
     Tuple format (Sec. III-B grammar plus the derived and smoothed operators):
-      ("pred", ">" | "<", weights[D], c), ("true",), ("not", f), ("and", f, g), ("or", f, g),
+      ("pred", ">" | "<", weights[D], c), ("norm", ">" | "<", scales[D], centre[D], r),
+      ("true",), ("not", f), ("and", f, g), ("or", f, g),
       ("eventually" | "always" | "eventually_sm" | "always_sm", I, f), ("until", I, f, g)
     with I = (a, b, slot, pad): b may be inf; slot None or a bounds column; pad None (repeat the
     last sample) or a constant."""
@@ -111,6 +112,15 @@ def flatten(tree, D):
             nd.pred_offset = len(weights)
             weights.extend(float(v) for v in w)
             nd.pred_c = float(c)
+        elif op == "norm":
+            _, rel, scale, centre, r = f
+            if len(scale) != D or len(centre) != D:
+                raise ValueError(f"norm predicate needs {D} scales and {D} centre coordinates")
+            nd.op = OPS["norm>" if rel == ">" else "norm<"]
+            nd.pred_offset = len(weights)
+            weights.extend(float(v) for v in scale)
+            weights.extend(float(v) for v in centre)
+            nd.pred_c = float(r)
         elif op == "true":
             nd.op = OPS["true"]
         elif op == "not":

@@ -40,10 +40,12 @@ bool is_temporal(int op) {
          op == STL_OP_EVENTUALLY_SM || op == STL_OP_ALWAYS_SM;
 }
 bool is_sm(int op) { return op == STL_OP_EVENTUALLY_SM || op == STL_OP_ALWAYS_SM; }
-bool is_pred(int op) { return op == STL_OP_PRED_GT || op == STL_OP_PRED_LT; }
+bool is_norm(int op) { return op == STL_OP_NORM_GT || op == STL_OP_NORM_LT; }
+bool is_pred(int op) { return op == STL_OP_PRED_GT || op == STL_OP_PRED_LT || is_norm(op); }
 int arity(int op) {
   switch (op) {
-    case STL_OP_PRED_GT: case STL_OP_PRED_LT: case STL_OP_TRUE: return 0;
+    case STL_OP_PRED_GT: case STL_OP_PRED_LT: case STL_OP_NORM_GT: case STL_OP_NORM_LT:
+    case STL_OP_TRUE: return 0;
     case STL_OP_NOT: case STL_OP_EVENTUALLY: case STL_OP_ALWAYS:
     case STL_OP_EVENTUALLY_SM: case STL_OP_ALWAYS_SM: return 1;
     case STL_OP_AND: case STL_OP_OR: case STL_OP_UNTIL: return 2;
@@ -274,13 +276,16 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
     if (P.nd[i].c1 >= 0) P.nd[P.nd[i].c1].parent = i;
   }
   P.npred = 0;
+  P.norm_mask = 0;
   for (int i = 0; i < n; ++i) {
     const stl_node &nd = h->nodes[i];
     if (!is_pred(nd.op)) continue;
     const int k = P.npred++;
     P.pred[k] = i;
+    if (is_norm(nd.op)) P.norm_mask |= 1u << k;
     for (int d = 0; d < h->D; ++d)
-      P.pw[k * STL_MAX_D + d] = nd.op == STL_OP_PRED_GT ? h->w[nd.pred_offset + d] : -h->w[nd.pred_offset + d];
+      P.pw[k * STL_MAX_D + d] = is_norm(nd.op) ? 0.f
+                                : nd.op == STL_OP_PRED_GT ? h->w[nd.pred_offset + d] : -h->w[nd.pred_offset + d];
   }
   const int scratch_words = scratch_for(threads);
   P.scratch_off = round_up(off_s, 4);
@@ -398,7 +403,7 @@ stl_status stl_compile(const stl_node *nodes, int32_t n_nodes, const float *pred
       }
     }
     if (is_pred(nd.op)) {
-      if (nd.pred_offset < 0 || nd.pred_offset + D > n_w)
+      if (nd.pred_offset < 0 || nd.pred_offset + (is_norm(nd.op) ? 2 * D : D) > n_w)
         return fail(STL_ERR_INVALID_ARG, "node %d: predicate weights out of range", i);
       if (!std::isfinite(nd.pred_c)) return fail(STL_ERR_INVALID_ARG, "node %d: predicate constant not finite", i);
     }

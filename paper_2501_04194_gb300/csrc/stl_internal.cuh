@@ -52,8 +52,9 @@ struct KProgram {
   int ut_len;          // their length (max taps)
   int win_r;           // samples per thread-run of the largest windows (15)
   int npred;           // predicate nodes
+  unsigned norm_mask;  // bit k: predicate k is a norm predicate (its pw row is zero)
   int pred[STL_MAX_PRED];
-  float pw[STL_MAX_PRED * STL_MAX_D];   // +w (mu - c) or -w (c - mu) per predicate
+  float pw[STL_MAX_PRED * STL_MAX_D];   // +w (mu - c) or -w (c - mu) per affine predicate
   float w[STL_MAX_WEIGHTS];
   KNode nd[STL_MAX_NODES];
 };

@@ -39,8 +39,10 @@ namespace {
 
 enum {
   OP_PGT = 0, OP_PLT = 1, OP_TRUE = 2, OP_NOT = 3, OP_AND = 4, OP_OR = 5, OP_EV = 6,
-  OP_ALW = 7, OP_UNTIL = 8, OP_EVSM = 9, OP_ALWSM = 10
+  OP_ALW = 7, OP_UNTIL = 8, OP_EVSM = 9, OP_ALWSM = 10, OP_NGT = 11, OP_NLT = 12
 };
+
+__device__ __forceinline__ bool is_pred_op(int op) { return op == OP_PGT || op == OP_PLT || op == OP_NGT || op == OP_NLT; }
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int L2B = 8;   // runs per level-2 block in the window middle
@@ -403,6 +405,71 @@ __device__ __forceinline__ void pred_batch(const float *__restrict__ xs, const f
   }
 }
 
+// Norm predicates (region membership, Sec. VI-A): mu = ||diag(s)(x - g)||_2 with the same
+// float32 order as the affine form (difference, scale, squares summed left to right, then a
+// correctly rounded square root), value mu - r (outside) or r - mu (inside).
+template <int DD>
+__device__ __forceinline__ void norm_batch(const float *__restrict__ xs, const float *sg, bool gt, float r,
+                                           const NodeOut &out, int F, int E) {
+  const int NT = blockDim.x;
+  float sr[DD], gr[DD];
+#pragma unroll
+  for (int d = 0; d < DD; ++d) { sr[d] = sg[d]; gr[d] = sg[DD + d]; }
+  for (int base = F + threadIdx.x; base < E; base += NT * BATCH) {
+    float x[BATCH][DD];
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const int q = base + k * NT;
+#pragma unroll
+      for (int d = 0; d < DD; ++d) x[k][d] = q < E ? __ldg(xs + (size_t)q * DD + d) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const int q = base + k * NT;
+      if (q < E) {
+        float u = __fmul_rn(sr[0], __fsub_rn(x[k][0], gr[0]));
+        float s = __fmul_rn(u, u);
+#pragma unroll
+        for (int d = 1; d < DD; ++d) {
+          u = __fmul_rn(sr[d], __fsub_rn(x[k][d], gr[d]));
+          s = __fadd_rn(s, __fmul_rn(u, u));
+        }
+        const float mu = __fsqrt_rn(s);
+        out.put(q, gt ? __fsub_rn(mu, r) : __fsub_rn(r, mu));
+      }
+    }
+  }
+}
+
+__device__ void eval_norm(const Cta &C, int n, int F, int E) {
+  const KProgram &P = *C.P;
+  const KNode &nd = P.nd[n];
+  const int D = P.D;
+  const float *sg = P.w + nd.w_off;   // scales [0, D), centre [D, 2D)
+  const float *__restrict__ xs = C.sig + C.row0 * D;
+  const NodeOut out = node_out(C, n);
+  const bool gt = nd.op == OP_NGT;
+  const float r = nd.pc;
+  switch (D) {
+    case 1: norm_batch<1>(xs, sg, gt, r, out, F, E); return;
+    case 2: norm_batch<2>(xs, sg, gt, r, out, F, E); return;
+    case 3: norm_batch<3>(xs, sg, gt, r, out, F, E); return;
+    case 4: norm_batch<4>(xs, sg, gt, r, out, F, E); return;
+    default: break;
+  }
+  for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
+    const float *x = xs + (size_t)q * D;
+    float u = __fmul_rn(sg[0], __fsub_rn(__ldg(x), sg[D]));
+    float s = __fmul_rn(u, u);
+    for (int d = 1; d < D; ++d) {
+      u = __fmul_rn(sg[d], __fsub_rn(__ldg(x + d), sg[D + d]));
+      s = __fadd_rn(s, __fmul_rn(u, u));
+    }
+    const float mu = __fsqrt_rn(s);
+    out.put(q, gt ? __fsub_rn(mu, r) : __fsub_rn(r, mu));
+  }
+}
+
 __device__ void eval_pred(const Cta &C, int n, int F, int E) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
@@ -630,6 +697,8 @@ __device__ void eval_node(const Cta &C, int n, int F, int E) {
   switch (nd.op) {
     case OP_PGT:
     case OP_PLT: eval_pred(C, n, F, E); break;
+    case OP_NGT:
+    case OP_NLT: eval_norm(C, n, F, E); break;
     case OP_TRUE:
     case OP_NOT:
     case OP_AND:
@@ -690,7 +759,7 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
   const float tau = P.tau;
   const int NT = blockDim.x;
   const int op = nd.op;
-  if (op == OP_PGT || op == OP_PLT || op == OP_TRUE) return;
+  if (is_pred_op(op) || op == OP_TRUE) return;
   const OwnView me = own_view(C, n);
   const ChildAdj a0 = child_adj(C, nd.c0);
   if (op == OP_NOT) {
@@ -1029,7 +1098,7 @@ __device__ void hard_walk(const Cta &C, const float *__restrict__ gout_row, int 
         for (;;) {
           const NodeRt &r = rt[n];
           const int op = r.op;
-          if (op == OP_PGT || op == OP_PLT) { pk = r.pred_k; break; }
+          if (is_pred_op(op)) { pk = r.pred_k; break; }
           if (op == OP_TRUE) break;
           if (op == OP_NOT) { g = -g; n = r.c0; continue; }
           if (op == OP_AND || op == OP_OR) {
@@ -1068,11 +1137,49 @@ __device__ void hard_walk(const Cta &C, const float *__restrict__ gout_row, int 
 }
 
 // ------------------------------------------------------------------ signal gradient
-// grad_sig[j, d] = sum_k pw[k][d] * pbar_k[j] for the complete samples [j0, j1); every
+// grad_sig[j, d] = sum_k pw[k][d] * pbar_k[j] over the affine predicates, plus, for each
+// norm predicate k, pbar_k[j] * (+-) s_d u_d / mu with u = diag(s)(x_j - g), mu = ||u|| (zero
+// at mu = 0, a subgradient of the norm there), for the complete samples [j0, j1); every
 // predicate buffer starts at sample pst.  One thread per sample, D unrolled when small.
+__device__ __forceinline__ float norm_mu_d(const float *sg, const float *x, int D, int d, float *ud) {
+  float q = 0.f;
+  for (int e = 0; e < D; ++e) {
+    const float u = sg[e] * (x[e] - sg[D + e]);
+    if (e == d) *ud = u;
+    q = fmaf(u, u, q);
+  }
+  return q;
+}
+
 template <int DD>
-__device__ __forceinline__ void signal_gradient_d(const KProgram &P, float *const *padj, float *gs, int pst, int j0,
-                                                  int j1) {
+__device__ __forceinline__ void norm_grad(const KProgram &P, int k, const float *x, float a, float *acc) {
+  const KNode &nd = P.nd[P.pred[k]];
+  const float *sg = P.w + nd.w_off;
+  float u[DD], q = 0.f;
+#pragma unroll
+  for (int d = 0; d < DD; ++d) {
+    u[d] = sg[d] * (x[d] - sg[DD + d]);
+    q = fmaf(u[d], u[d], q);
+  }
+  if (q > 0.f) {
+    const float f = (nd.op == OP_NGT ? a : -a) * rsqrtf(q);
+#pragma unroll
+    for (int d = 0; d < DD; ++d) acc[d] = fmaf(f * sg[d], u[d], acc[d]);
+  }
+}
+
+// the norm term of dimension d for runtime D (wide signals and the final sample)
+__device__ __forceinline__ float norm_grad_dim(const KProgram &P, int k, const float *x, int D, int d, float a) {
+  const KNode &nd = P.nd[P.pred[k]];
+  const float *sg = P.w + nd.w_off;
+  float ud = 0.f;
+  const float q = norm_mu_d(sg, x, D, d, &ud);
+  return q > 0.f ? (nd.op == OP_NGT ? a : -a) * rsqrtf(q) * sg[d] * ud : 0.f;
+}
+
+template <int DD>
+__device__ __forceinline__ void signal_gradient_d(const KProgram &P, float *const *padj, const float *xs, float *gs,
+                                                  int pst, int j0, int j1) {
   for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
     float acc[DD];
 #pragma unroll
@@ -1081,6 +1188,16 @@ __device__ __forceinline__ void signal_gradient_d(const KProgram &P, float *cons
       const float a = padj[k][j - pst];
 #pragma unroll
       for (int d = 0; d < DD; ++d) acc[d] = fmaf(P.pw[k * STL_MAX_D + d], a, acc[d]);
+    }
+    if (P.norm_mask) {
+      float x[DD];
+#pragma unroll
+      for (int d = 0; d < DD; ++d) x[d] = __ldg(xs + (size_t)j * DD + d);
+      for (unsigned m = P.norm_mask; m; m &= m - 1) {
+        const int k = __ffs(m) - 1;
+        const float a = padj[k][j - pst];
+        if (a != 0.f) norm_grad<DD>(P, k, x, a, acc);
+      }
     }
     float *o = gs + (size_t)j * DD;
 #pragma unroll
@@ -1093,17 +1210,23 @@ __device__ void signal_gradient(const Cta &C, float *gs, int pst, int j0, int j1
   float **padj = reinterpret_cast<float **>(C.scratch);   // free between node evaluations
   if (threadIdx.x < P.npred) padj[threadIdx.x] = C.rt[P.pred[threadIdx.x]].adj;
   __syncthreads();
+  const float *xs = C.sig + C.row0 * P.D;
   switch (P.D) {
-    case 1: signal_gradient_d<1>(P, padj, gs, pst, j0, j1); break;
-    case 2: signal_gradient_d<2>(P, padj, gs, pst, j0, j1); break;
-    case 3: signal_gradient_d<3>(P, padj, gs, pst, j0, j1); break;
-    case 4: signal_gradient_d<4>(P, padj, gs, pst, j0, j1); break;
+    case 1: signal_gradient_d<1>(P, padj, xs, gs, pst, j0, j1); break;
+    case 2: signal_gradient_d<2>(P, padj, xs, gs, pst, j0, j1); break;
+    case 3: signal_gradient_d<3>(P, padj, xs, gs, pst, j0, j1); break;
+    case 4: signal_gradient_d<4>(P, padj, xs, gs, pst, j0, j1); break;
     default: {
       const int D = P.D;
       for (int idx = threadIdx.x; idx < (j1 - j0) * D; idx += blockDim.x) {
         const int j = j0 + idx / D, d = idx - (idx / D) * D;
         float acc = 0.f;
         for (int k = 0; k < P.npred; ++k) acc = fmaf(P.pw[k * STL_MAX_D + d], padj[k][j - pst], acc);
+        for (unsigned m = P.norm_mask; m; m &= m - 1) {
+          const int k = __ffs(m) - 1;
+          const float a = padj[k][j - pst];
+          if (a != 0.f) acc += norm_grad_dim(P, k, xs + (size_t)j * D, D, d, a);
+        }
         gs[(size_t)j * D + d] = acc;
       }
     }
@@ -1267,9 +1390,15 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
           __syncthreads();
         }
         const int D = P.D;
+        const float *xl = C.sig + (C.row0 + (T - 1)) * D;
         for (int d = threadIdx.x; d < D; d += NT) {
           float acc = 0.f;
           for (int k = 0; k < P.npred; ++k) acc = fmaf(P.pw[k * STL_MAX_D + d], C.rt[P.pred[k]].padadj, acc);
+          for (unsigned m = P.norm_mask; m; m &= m - 1) {
+            const int k = __ffs(m) - 1;
+            const float a = C.rt[P.pred[k]].padadj;
+            if (a != 0.f) acc += norm_grad_dim(P, k, xl, D, d, a);
+          }
           A.gsig[(C.row0 + (T - 1)) * D + d] = acc;
         }
       }

@@ -158,6 +158,33 @@ def test_random_formulas_per_trace_bounds(stl, seed, mode, tau):
     check(stl, tree, sig, bounds=bounds, mode=mode, tau=tau, launch=dict(tile=256, segment=400 if seed % 3 == 0 else 0))
 
 
+# ------------------------------------------------------------------ region (norm) predicates
+@pytest.mark.parametrize("D", [1, 2, 3, 5])
+@pytest.mark.parametrize("mode,tau", [("hard", 1.0), ("smooth", 3.0)])
+def test_norm_predicates(stl, D, mode, tau):
+    """Inside/outside-ball predicates in a reach/avoid tree, several tiles and a ragged tail,
+    one sample exactly at a centre (mu = 0: zero subgradient on both sides), a zero scale."""
+    rng = np.random.default_rng(40 + D)
+    sig = W.random_walk(5, 1337, D, seed=D)
+    g1 = [float(v) for v in sig[1, 600]]
+    g2 = [float(v) for v in rng.normal(size=D)]
+    s2 = [0.0 if (d == D - 1 and D > 1) else float(rng.uniform(0.5, 2.0)) for d in range(D)]
+    tree = W.And(W.Eventually(5, 60, W.norm_lt([1.0] * D, g1, 0.4)),
+                 W.Or(W.Always(0, 25, W.norm_gt(s2, g2, 0.7)), W.Until(0, 30, W.norm_gt([1.0] * D, g1, 0.2),
+                                                                       W.gt([1.0] + [0.0] * (D - 1), 0.3))))
+    check(stl, tree, sig, mode=mode, tau=tau, launch=dict(tile=256))
+
+
+@pytest.mark.parametrize("mode,tau", [("hard", 1.0), ("smooth", 20.0)])
+def test_reach_avoid_rollouts(stl, mode, tau):
+    """The control-synthesis specification (reach a goal disc within [50, 150], avoid three
+    obstacle discs throughout) on rollouts of the saturated single integrator, T = 200."""
+    for k, (g, o, r) in enumerate(W.config4_problems(3, seed=7)):
+        u = W.random_controls(64, seed=k, scale=2.0)
+        sig = W.rollout(u) + np.float32(0.3) * np.asarray(g, dtype=np.float32) * np.float32(k)
+        check(stl, W.reach_avoid_formula(g, o, r), sig.astype(np.float32), mode=mode, tau=tau, seed=k)
+
+
 # ------------------------------------------------------------------ degenerate cases
 EDGE = [
     ("T1", W.config1_formula(), 3, 1),

@@ -267,3 +267,45 @@ def table3_formulas(D=2, I=(0, 20)):
     for k in range(8, -1, -1):
         phi6 = And(phi6, Eventually(a, b, And(pv(k), ps(k))))
     return [phi1, phi2, phi3, phi4, phi5, phi6]
+
+
+# Reach/avoid planning problems (the control-synthesis workload): 2-D single integrator with
+# saturated controls, x_{t+1} = x_t + dt * tanh(u_t) from x_0 = 0, evaluated on x_1..x_T.
+CONFIG4_T = 200
+CONFIG4_OBSTACLES = 3
+
+
+def reach_avoid_formula(goal, obstacles, radii, reach=(50, 150), goal_r=0.3):
+    """Eventually_[reach] inside the goal disc (radius goal_r), and, for every obstacle k,
+    Always outside the disc of radius r_k around o_k."""
+    f = Eventually(reach[0], reach[1], norm_lt([1.0, 1.0], goal, goal_r))
+    for o, r in zip(obstacles, radii):
+        f = And(f, Always(0, INF, norm_gt([1.0, 1.0], o, r)))
+    return f
+
+
+def config4_problems(n, seed=0, n_obstacles=CONFIG4_OBSTACLES):
+    """n problems: goal g and obstacle centres o_k ~ U[-3, 3]^2, radii r_k ~ U[0.3, 0.8];
+    problems with the origin or the goal inside an obstacle are redrawn."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        g = rng.uniform(-3.0, 3.0, size=2).astype(np.float32)
+        o = rng.uniform(-3.0, 3.0, size=(n_obstacles, 2)).astype(np.float32)
+        r = rng.uniform(0.3, 0.8, size=n_obstacles).astype(np.float32)
+        if np.any(np.linalg.norm(o, axis=1) <= r) or np.any(np.linalg.norm(o - g, axis=1) <= r):
+            continue
+        out.append((g, o, r))
+    return out
+
+
+def rollout(u, dt=0.1):
+    """Trajectories [B, T, 2] (float32) of x_{t+1} = x_t + dt tanh(u_t), x_0 = 0, for controls
+    u [B, T, 2]; sample t of the result is x_{t+1}."""
+    u = np.asarray(u, dtype=np.float64)
+    return np.cumsum(dt * np.tanh(u), axis=1).astype(np.float32)
+
+
+def random_controls(B, T=CONFIG4_T, seed=0, scale=1.0):
+    rng = np.random.default_rng(seed)
+    return (scale * rng.normal(size=(B, T, 2))).astype(np.float32)
