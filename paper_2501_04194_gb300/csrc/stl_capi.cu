@@ -177,10 +177,11 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
   tile = std::max(32, round_up(tile, 32));
 
   auto padded = [](int cap) { return cap; };
-  // window scratch: run aggregates (threads + K/7) and their blocks of 8, 16 bytes each
+  // window scratch: run aggregates (threads + K/7) and their blocks of 8, 16 bytes each; the
+  // signal gradient reuses it for the predicate adjoint pointers
   auto scratch_for = [&](int nt) {
     const int runs = nt + maxK / 7 + 4;
-    return (runs + runs / 8 + 8) * 4;
+    return std::max((runs + runs / 8 + 8) * 4, 2 * STL_MAX_PRED);
   };
   auto layout = [&](int tl, std::vector<int> &space_out, int &smem_words, int &gwords) {
     // scratch for window run aggregates: (threads + maxK/R + 2) entries of up to 16 bytes

@@ -244,29 +244,31 @@ __device__ __forceinline__ int frontier(const Cta &C, int n) {
   return e < C.T ? e : C.T;
 }
 
-// A parent's read access to child values: a single compare decides the common case; pads,
-// sample T-1 and positions past the child's frontier take the cold path.
+// A parent's read access to child values.  Branch-free in the common case: the index is
+// clamped into the computed range [start, fmax] (reads outside it feed no output), and sample
+// T-1 and the pads past the end of the trace are selected from the per-node cells.
 struct ChildView {
   const float *p;
-  int start, span, T, fmax;
+  int start, T, fmax;
   float lastval, padv;
   bool padc;
   __device__ __forceinline__ float get(int j, int &src) const {
-    if ((unsigned)(j - start) < (unsigned)span) { src = j; return p[j - start]; }
-    return slow(j, src);
-  }
-  __device__ __noinline__ float slow(int j, int &src) const {
-    if (j >= T) {
-      src = padc ? -1 : T - 1;
-      return padc ? padv : lastval;
+    const int jj = max(min(j, fmax), start);
+    float v = p[jj - start];
+    src = jj;
+    if (j >= T - 1) {
+      const bool pad = j >= T && padc;
+      v = pad ? padv : lastval;
+      src = pad ? -1 : T - 1;
     }
-    if (j >= T - 1) { src = T - 1; return lastval; }
-    j = j > fmax ? fmax : j;
-    j = j < start ? start : j;
-    src = j;
-    return p[j - start];
+    return v;
   }
-  __device__ __forceinline__ float get(int j) const { int s; return get(j, s); }
+  __device__ __forceinline__ float get(int j) const {
+    const int jj = max(min(j, fmax), start);
+    float v = p[jj - start];
+    if (j >= T - 1) v = (j >= T && padc) ? padv : lastval;
+    return v;
+  }
 };
 
 __device__ __forceinline__ ChildView child_view(const Cta &C, const KNode &p, int c) {
@@ -275,8 +277,6 @@ __device__ __forceinline__ ChildView child_view(const Cta &C, const KNode &p, in
   cv.p = r.val;
   cv.start = C.t0 + r.lo;
   const int f = frontier(C, c);
-  const int lim = f < C.T - 1 ? f : C.T - 1;   // fast path: [start, lim)
-  cv.span = lim - cv.start;
   cv.T = C.T;
   cv.fmax = f - 1;
   cv.lastval = r.lastval;
@@ -494,38 +494,64 @@ __device__ void eval_pred(const Cta &C, int n, int F, int E) {
   }
 }
 
+// Elementwise nodes: each thread first loads BATCH samples of its children (independent loads
+// in flight), then combines and stores them.
 template <bool SMOOTH>
 __device__ void eval_elementwise(const Cta &C, int n, int F, int E) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
   const NodeOut out = node_out(C, n);
   const int op = nd.op;
+  const int NT = blockDim.x;
   if (op == OP_TRUE) {
-    for (int q = F + threadIdx.x; q < E; q += blockDim.x) out.put(q, INFINITY);
+    for (int q = F + threadIdx.x; q < E; q += NT) out.put(q, INFINITY);
     return;
   }
   const ChildView x = child_view(C, nd, nd.c0);
   if (op == OP_NOT) {
-    for (int q = F + threadIdx.x; q < E; q += blockDim.x) out.put(q, -x.get(q));
+    for (int base = F + threadIdx.x; base < E; base += NT * BATCH) {
+      float a[BATCH];
+#pragma unroll
+      for (int k = 0; k < BATCH; ++k) {
+        const int q = base + k * NT;
+        a[k] = q < E ? x.get(q) : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < BATCH; ++k) {
+        const int q = base + k * NT;
+        if (q < E) out.put(q, -a[k]);
+      }
+    }
     return;
   }
   const ChildView y = child_view(C, nd, nd.c1);
   const float tau = P.tau, itau = P.inv_tau;
   const float sg = op == OP_AND ? 1.f : -1.f;
-  for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
-    const float a = x.get(q), b = y.get(q);
-    float v;
-    if constexpr (!SMOOTH) {
-      v = op == OP_AND ? (a <= b ? a : b) : (a >= b ? a : b);
-    } else {
-      // two-term logsumexp min / max: min(x,y) - log1p(e^{-tau|x-y|}) / tau
-      const float xs = sg * a, ys = sg * b;
-      const float m = xs < ys ? xs : ys;
-      float corr = (xs == ys) ? 0.69314718f * itau : log1pf(expf(-tau * fabsf(xs - ys))) * itau;
-      if (isinf(xs) || isinf(ys)) corr = 0.f;
-      v = sg * (m - corr);
+  for (int base = F + threadIdx.x; base < E; base += NT * BATCH) {
+    float a[BATCH], b[BATCH];
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const int q = base + k * NT;
+      a[k] = q < E ? x.get(q) : 0.f;
+      b[k] = q < E ? y.get(q) : 0.f;
     }
-    out.put(q, v);
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const int q = base + k * NT;
+      if (q >= E) continue;
+      float v;
+      if constexpr (!SMOOTH) {
+        v = op == OP_AND ? (a[k] <= b[k] ? a[k] : b[k]) : (a[k] >= b[k] ? a[k] : b[k]);
+      } else {
+        // two-term logsumexp min / max: min(x,y) - log1p(e^{-tau|x-y|}) / tau
+        const float xs = sg * a[k], ys = sg * b[k];
+        const float m = xs < ys ? xs : ys;
+        float corr = (xs == ys) ? 0.69314718f * itau : log1pf(expf(-tau * fabsf(xs - ys))) * itau;
+        if (isinf(xs) || isinf(ys)) corr = 0.f;
+        v = sg * (m - corr);
+      }
+      out.put(q, v);
+    }
   }
 }
 
@@ -1119,13 +1145,15 @@ __device__ void hard_walk(const Cta &C, const float *__restrict__ gout_row, int 
       const int pj = __shfl_up_sync(FULL, j, 1), pp = __shfl_up_sync(FULL, pk, 1);
       const bool head = lane == 0 || pj != j || pp != pk;
       const unsigned heads = __ballot_sync(FULL, head);
-      const int rid = __popc(heads & (0xffffffffu >> (31 - lane)));
       float s = g;
+      if (heads != FULL) {   // some lanes share a target: segmented sum over the runs
+        const int rid = __popc(heads & (0xffffffffu >> (31 - lane)));
 #pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const float sv = __shfl_down_sync(FULL, s, off);
-        const int rv = __shfl_down_sync(FULL, rid, off);
-        if (lane + off < 32 && rv == rid) s += sv;
+        for (int off = 1; off < 32; off <<= 1) {
+          const float sv = __shfl_down_sync(FULL, s, off);
+          const int rv = __shfl_down_sync(FULL, rid, off);
+          if (lane + off < 32 && rv == rid) s += sv;
+        }
       }
       if (head && pk >= 0 && s != 0.f) {
         const NodeRt &r = rt[C.P->pred[pk]];
@@ -1140,7 +1168,8 @@ __device__ void hard_walk(const Cta &C, const float *__restrict__ gout_row, int 
 // grad_sig[j, d] = sum_k pw[k][d] * pbar_k[j] over the affine predicates, plus, for each
 // norm predicate k, pbar_k[j] * (+-) s_d u_d / mu with u = diag(s)(x_j - g), mu = ||u|| (zero
 // at mu = 0, a subgradient of the norm there), for the complete samples [j0, j1); every
-// predicate buffer starts at sample pst.  One thread per sample, D unrolled when small.
+// predicate buffer starts at sample pst.  A thread handles SB samples per iteration, D
+// unrolled when small (measured faster than one thread per element with coalesced stores).
 __device__ __forceinline__ float norm_mu_d(const float *sg, const float *x, int D, int d, float *ud) {
   float q = 0.f;
   for (int e = 0; e < D; ++e) {
@@ -1151,24 +1180,7 @@ __device__ __forceinline__ float norm_mu_d(const float *sg, const float *x, int 
   return q;
 }
 
-template <int DD>
-__device__ __forceinline__ void norm_grad(const KProgram &P, int k, const float *x, float a, float *acc) {
-  const KNode &nd = P.nd[P.pred[k]];
-  const float *sg = P.w + nd.w_off;
-  float u[DD], q = 0.f;
-#pragma unroll
-  for (int d = 0; d < DD; ++d) {
-    u[d] = sg[d] * (x[d] - sg[DD + d]);
-    q = fmaf(u[d], u[d], q);
-  }
-  if (q > 0.f) {
-    const float f = (nd.op == OP_NGT ? a : -a) * rsqrtf(q);
-#pragma unroll
-    for (int d = 0; d < DD; ++d) acc[d] = fmaf(f * sg[d], u[d], acc[d]);
-  }
-}
-
-// the norm term of dimension d for runtime D (wide signals and the final sample)
+// the norm term of dimension d of predicate k at one sample
 __device__ __forceinline__ float norm_grad_dim(const KProgram &P, int k, const float *x, int D, int d, float a) {
   const KNode &nd = P.nd[P.pred[k]];
   const float *sg = P.w + nd.w_off;
@@ -1180,28 +1192,49 @@ __device__ __forceinline__ float norm_grad_dim(const KProgram &P, int k, const f
 template <int DD>
 __device__ __forceinline__ void signal_gradient_d(const KProgram &P, float *const *padj, const float *xs, float *gs,
                                                   int pst, int j0, int j1) {
-  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-    float acc[DD];
+  constexpr int SB = 4;   // samples per thread per iteration (independent loads in flight)
+  const int NT = blockDim.x;
+  for (int base = j0 + threadIdx.x; base < j1; base += NT * SB) {
+    float acc[SB][DD];
 #pragma unroll
-    for (int d = 0; d < DD; ++d) acc[d] = 0.f;
+    for (int s = 0; s < SB; ++s)
+#pragma unroll
+      for (int d = 0; d < DD; ++d) acc[s][d] = 0.f;
     for (int k = 0; k < P.npred; ++k) {
-      const float a = padj[k][j - pst];
+      const float *pa = padj[k] - pst;
+      float w[DD], a[SB];
 #pragma unroll
-      for (int d = 0; d < DD; ++d) acc[d] = fmaf(P.pw[k * STL_MAX_D + d], a, acc[d]);
+      for (int d = 0; d < DD; ++d) w[d] = P.pw[k * STL_MAX_D + d];
+#pragma unroll
+      for (int s = 0; s < SB; ++s) {
+        const int j = base + s * NT;
+        a[s] = j < j1 ? pa[j] : 0.f;
+      }
+#pragma unroll
+      for (int s = 0; s < SB; ++s)
+#pragma unroll
+        for (int d = 0; d < DD; ++d) acc[s][d] = fmaf(w[d], a[s], acc[s][d]);
     }
-    if (P.norm_mask) {
-      float x[DD];
+    for (unsigned m = P.norm_mask; m; m &= m - 1) {
+      const int k = __ffs(m) - 1;
 #pragma unroll
-      for (int d = 0; d < DD; ++d) x[d] = __ldg(xs + (size_t)j * DD + d);
-      for (unsigned m = P.norm_mask; m; m &= m - 1) {
-        const int k = __ffs(m) - 1;
+      for (int s = 0; s < SB; ++s) {
+        const int j = base + s * NT;
+        if (j >= j1) continue;
         const float a = padj[k][j - pst];
-        if (a != 0.f) norm_grad<DD>(P, k, x, a, acc);
+        if (a == 0.f) continue;
+#pragma unroll
+        for (int d = 0; d < DD; ++d) acc[s][d] += norm_grad_dim(P, k, xs + (size_t)j * DD, DD, d, a);
       }
     }
-    float *o = gs + (size_t)j * DD;
 #pragma unroll
-    for (int d = 0; d < DD; ++d) o[d] = acc[d];
+    for (int s = 0; s < SB; ++s) {
+      const int j = base + s * NT;
+      if (j >= j1) continue;
+      float *o = gs + (size_t)j * DD;
+#pragma unroll
+      for (int d = 0; d < DD; ++d) o[d] = acc[s][d];
+    }
   }
 }
 
@@ -1210,14 +1243,14 @@ __device__ void signal_gradient(const Cta &C, float *gs, int pst, int j0, int j1
   float **padj = reinterpret_cast<float **>(C.scratch);   // free between node evaluations
   if (threadIdx.x < P.npred) padj[threadIdx.x] = C.rt[P.pred[threadIdx.x]].adj;
   __syncthreads();
-  const float *xs = C.sig + C.row0 * P.D;
-  switch (P.D) {
+  const int D = P.D;
+  const float *xs = C.sig + C.row0 * D;
+  switch (D) {
     case 1: signal_gradient_d<1>(P, padj, xs, gs, pst, j0, j1); break;
     case 2: signal_gradient_d<2>(P, padj, xs, gs, pst, j0, j1); break;
     case 3: signal_gradient_d<3>(P, padj, xs, gs, pst, j0, j1); break;
     case 4: signal_gradient_d<4>(P, padj, xs, gs, pst, j0, j1); break;
     default: {
-      const int D = P.D;
       for (int idx = threadIdx.x; idx < (j1 - j0) * D; idx += blockDim.x) {
         const int j = j0 + idx / D, d = idx - (idx / D) * D;
         float acc = 0.f;
