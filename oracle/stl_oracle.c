@@ -36,7 +36,7 @@
  *       double rounding since 53 >= 2*24+2); ``exact`` skips the rounding.
  *       Signals and bounds arrive as double (float32 inputs widen exactly), so that
  *       finite-difference checks can perturb them in double precision;
- *   R8  a norm predicate (Sec. VI-A "inside" a region) is mu(x) = ||diag(s)(x - g)||_2 with
+ *   R15 a norm predicate (Sec. VI-A "inside" a region) is mu(x) = ||diag(s)(x - g)||_2 with
  *       per-dimension scales s (0 drops a dimension) and centre g; "<" gives r - mu(x)
  *       (inside the ball of radius r), ">" gives mu(x) - r (outside it).
  */
@@ -190,7 +190,7 @@ static void work_free(work *wk, int n) {
 
 /* mu(x) for a norm predicate: the Euclidean distance of the scaled offset from a centre,
  * mu(x) = sqrt(sum_d u_d^2), u_d = s_d (x_d - g_d), with s = w[0..D) and g = w[D..2D).  This
- * is the "inside region" predicate of the trajectory-planning example, Sec. VI-A (R8).
+ * is the "inside region" predicate of the trajectory-planning example, Sec. VI-A (R15).
  * Rounded mode: every operation in float32 order, sum left to right, then a correctly
  * rounded square root (exact under double rounding, as for the other operations). */
 static double norm_mu(const octx *cx, const onode *nd, const double *row, double *u) {
