@@ -228,7 +228,30 @@ def side_measurements(stl, W, torch, dev, args):
                              "one_launch_graph": {"value": steps_total / (ms_graph * 1e-3), "ms": ms_graph},
                              "per_formula_launches": {"value": steps_total / (ms_per * 1e-3), "ms": ms_per},
                              "unit": UNIT, "mode": "hard", "fwd+bwd": True}
+    if not args.no_plan:
+        out["warm_vs_cold"] = plan_measurement(W, args)
     return out
+
+
+def plan_measurement(W, args):
+    """Learned warm start for STL trajectory optimisation (reach/avoid, 2-D saturated single
+    integrator, T = 200): solve the training problems from a cold start with Adam through the
+    smooth robustness (tau = 20), fit the BF16 MLP to the solutions, then solve 4096 held-out
+    problems from a cold start and from the MLP's output; a problem is solved once its hard
+    robustness at t = 0 is >= 0."""
+    import time as _t
+    from paper_2501_04194_gb300 import planning as PL
+    t0 = _t.time()
+    n_tr, n_te = args.plan_train, 4096
+    probs = W.config4_problems(n_tr + n_te, seed=0)
+    forms = [W.reach_avoid_formula(g, o, r) for g, o, r in probs]
+    mlp, frac, hist = PL.train_warm_start(probs[:n_tr], forms[:n_tr], max_iters=300, lr=0.05, epochs=30)
+    t1 = _t.time()
+    res = PL.warm_vs_cold(mlp, probs[n_tr:], forms[n_tr:], max_iters=300, lr=0.05)
+    res.update({"train_problems": n_tr, "train_solved": frac, "held_out": n_te, "mlp_final_mse": hist[-1],
+                "train_wall_s": t1 - t0, "eval_wall_s": _t.time() - t1, "batch": 4096, "tau": 20.0, "lr": 0.05,
+                "max_steps": 300, "unit": "ms per problem (Adam steps x batch time per step, + MLP inference)"})
+    return res
 
 
 def main():
@@ -245,7 +268,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the smooth and ragged side measurements")
+    ap.add_argument("--no-extra", action="store_true", help="skip the smooth, ragged and planning side measurements")
+    ap.add_argument("--no-plan", action="store_true", help="skip the warm-start planning side measurement")
+    ap.add_argument("--plan-train", type=int, default=100000, help="training problems of the warm-start MLP")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

@@ -205,8 +205,9 @@ STL_API stl_status stl_robustness_backward_noalloc(stl_handle h, const float *si
  * order CTAs take them from a shared work counter (longest first balances the tail).
  * Interval semantics per trace as in stl_robustness (Sec. IV-E: intervals are data). */
 
-/* Group compiled formulas (same D) for ragged launches.  The set refers to the handles, which
- * must outlive it. */
+/* Group compiled formulas (same D; 1 <= n_formulas <= 65536) for ragged launches.  The set
+ * refers to the handles, which must outlive it.  stl_set_prepare copies every formula's program
+ * into one device table (about 10 KB per formula), allocated on the first prepare. */
 STL_API stl_status stl_set_create(const stl_handle *formulas, int32_t n_formulas, stl_set_handle *out);
 STL_API void stl_set_destroy(stl_set_handle s);
 

@@ -304,3 +304,35 @@ def device_status(stream=None) -> int:
     st = ctypes.c_int32()
     check(load().stl_get_device_status(stream, ctypes.byref(st)))
     return int(st.value)
+
+
+# ---------------------------------------------------------------- planning helpers (stl_plan.h)
+def plan_lib():
+    """libstl with the argument types of the stl_plan.h entry points set."""
+    lib = load()
+    if getattr(lib, "_plan_ready", False):
+        return lib
+    vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    sigs = {
+        "stl_rollout": [vp, i64, i32, f32, vp, vp],
+        "stl_plan_adam_step": [vp, vp, vp, vp, vp, i64, i32, f32, f32, f32, f32, f32, i32, vp, vp],
+        "stl_plan_check": [vp, vp, vp, i32, vp, i64, i32, vp, vp],
+        "stl_gemm_bf16": [vp, i32, i32, vp, i32, i32, i32, i32, i32, vp, i32, vp, vp, i32, vp],
+        "stl_mse_grad": [vp, vp, i64, f32, vp, vp, vp],
+        "stl_relu_backward": [vp, vp, i64, vp, vp],
+        "stl_colsum_bf16": [vp, i32, i32, vp, vp],
+        "stl_adam": [vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp],
+        "stl_to_bf16": [vp, i64, vp, vp],
+        "stl_gather_rows": [vp, i64, vp, i64, i32, vp, vp],
+    }
+    for name, args in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = i32
+    lib._plan_ready = True
+    return lib
+
+
+def plan_call(name, *args):
+    """Call one stl_plan.h entry point (pointers as ints or None) and raise on a bad status."""
+    check(getattr(plan_lib(), name)(*args))

@@ -592,8 +592,8 @@ extern "C" {
 stl_status stl_set_create(const stl_handle *formulas, int32_t n_formulas, stl_set_handle *out) {
   if (!out) return fail(STL_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (!formulas || n_formulas < 1 || n_formulas > 1024)
-    return fail(STL_ERR_INVALID_ARG, "n_formulas must be in [1, 1024]");
+  if (!formulas || n_formulas < 1 || n_formulas > 65536)
+    return fail(STL_ERR_INVALID_ARG, "n_formulas must be in [1, 65536]");
   stl_program_set *s = new (std::nothrow) stl_program_set;
   if (!s) return fail(STL_ERR_INVALID_ARG, "out of host memory");
   for (int i = 0; i < n_formulas; ++i) {
@@ -652,7 +652,7 @@ stl_status stl_set_prepare(stl_set_handle s, int64_t n_traces, int64_t T_max, co
     P.smem_words = smem;   // every program sees the launch's shared arena
   }
   if (!st.dtable) {
-    cudaError_t ce = cudaMalloc((void **)&st.dtable, sizeof(KProgram) * 1024);
+    cudaError_t ce = cudaMalloc((void **)&st.dtable, sizeof(KProgram) * (size_t)nf);
     if (ce != cudaSuccess) { st.dtable = nullptr; return cuda_fail((int)ce, "cudaMalloc(program table)"); }
   }
   cudaError_t ce = cudaMemcpy(st.dtable, progs.data(), sizeof(KProgram) * nf, cudaMemcpyHostToDevice);

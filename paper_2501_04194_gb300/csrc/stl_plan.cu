@@ -1,0 +1,397 @@
+// stl_plan.cu -- trajectory-optimisation helpers (include/stl_plan.h): the rollout of the
+// saturated single integrator and its adjoint fused with Adam, the solved/active bookkeeping,
+// and the BF16 tensor-core matrix products and elementwise steps of the warm-start MLP.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "stl_internal.cuh"
+#include "stl_plan.h"
+
+stl_status stl_internal_fail(stl_status st, const char *msg);
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+stl_status cuda_status(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return STL_OK;
+  return stl_internal_fail(STL_ERR_CUDA, what);
+}
+
+// exclusive prefix sum over the lanes of a warp (lane order)
+__device__ __forceinline__ float warp_excl_prefix(float v) {
+  const int lane = threadIdx.x & 31;
+  float inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float n = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += n;
+  }
+  return inc - v;
+}
+
+// exclusive suffix sum over the lanes of a warp (reverse lane order)
+__device__ __forceinline__ float warp_excl_suffix(float v) {
+  const int lane = threadIdx.x & 31;
+  float inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float n = __shfl_down_sync(FULL, inc, o);
+    if (lane + o < 32) inc += n;
+  }
+  return inc - v;
+}
+
+// x_t = sum_{s<=t} dt tanh(u_s) for one problem, by one warp: each lane owns a chunk of
+// consecutive steps (local sums, a warp scan of the chunk totals, then the running sums)
+__device__ __forceinline__ void rollout_warp(const float *u, float *x, int T, float dt) {
+  const int lane = threadIdx.x & 31;
+  const int c = (T + 31) / 32;
+  const int t0 = min(lane * c, T), t1 = min(t0 + c, T);
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    float s = 0.f;
+    for (int t = t0; t < t1; ++t) s += dt * tanhf(u[2 * t + d]);
+    float run = warp_excl_prefix(s);
+    for (int t = t0; t < t1; ++t) {
+      run += dt * tanhf(u[2 * t + d]);
+      x[2 * t + d] = run;
+    }
+  }
+}
+
+__global__ void rollout_kernel(const float *__restrict__ u, long long B, int T, float dt, float *__restrict__ x) {
+  const long long b = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (b >= B) return;   // whole warps exit together
+  rollout_warp(u + b * T * 2, x + b * T * 2, T, dt);
+}
+
+__global__ void plan_adam_kernel(float *__restrict__ u, float *__restrict__ m, float *__restrict__ v,
+                                 const float *__restrict__ xbar, const int *__restrict__ active, long long B, int T,
+                                 float dt, float lr, float b1, float b2, float eps, float c1, float c2,
+                                 float *__restrict__ x) {
+  const long long b = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (b >= B || !active[b]) return;   // warp-uniform
+  const int lane = threadIdx.x & 31;
+  const int c = (T + 31) / 32;
+  const int t0 = min(lane * c, T), t1 = min(t0 + c, T);
+  const long long base = b * T * 2;
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    // suffix sums of xbar: S_t = sum_{s >= t} xbar_s
+    float s = 0.f;
+    for (int t = t0; t < t1; ++t) s += xbar[base + 2 * t + d];
+    float run = warp_excl_suffix(s);   // sum over the later chunks
+    for (int t = t1 - 1; t >= t0; --t) {
+      const long long i = base + 2 * t + d;
+      run += xbar[i];
+      const float th = tanhf(u[i]);
+      const float g = dt * (1.f - th * th) * run;
+      const float mi = b1 * m[i] + (1.f - b1) * g;
+      const float vi = b2 * v[i] + (1.f - b2) * g * g;
+      m[i] = mi;
+      v[i] = vi;
+      u[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+  }
+  __syncwarp();
+  rollout_warp(u + base, x + base, T, dt);
+}
+
+__global__ void plan_check_kernel(const float *__restrict__ rho, int *__restrict__ active, int *__restrict__ solved,
+                                  int iter, float *__restrict__ gout, long long B, int T, int *n_active) {
+  const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int still = 0;
+  if (b < B) {
+    int a = active[b];
+    if (a && rho[b * T] >= 0.f) {
+      solved[b] = iter;
+      active[b] = 0;
+      a = 0;
+    }
+    gout[b * T] = a ? -1.f : 0.f;
+    still = a;
+  }
+  if (n_active) {
+    const unsigned bal = __ballot_sync(FULL, still);
+    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(n_active, __popc(bal));
+  }
+}
+
+// ------------------------------------------------------------------ BF16 GEMM (mma.sync)
+// C[M,N] = op(A) op(B): 64 x 64 tiles, 4 warps of 32 x 32, K in steps of 16.  Tiles are staged
+// in shared memory as As[m][k] and Bs[n][k] (both K-contiguous), the layouts of the row / col
+// operands of mma.m16n8k16.
+constexpr int GT = 64, GK = 16, GPAD = 8;
+
+__device__ __forceinline__ unsigned pack2(const __nv_bfloat16 *p) {
+  return *reinterpret_cast<const unsigned *>(p);
+}
+
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *__restrict__ A, int lda, int ta,
+                                                        const __nv_bfloat16 *__restrict__ Bm, int ldb, int tb, int M,
+                                                        int N, int K, const float *__restrict__ bias, int relu,
+                                                        float *__restrict__ Cf, __nv_bfloat16 *__restrict__ Cb,
+                                                        int ldc) {
+  __shared__ __align__(16) __nv_bfloat16 As[GT][GK + GPAD];
+  __shared__ __align__(16) __nv_bfloat16 Bs[GT][GK + GPAD];
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
+  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int g = lane >> 2, t = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    // stage op(A)[m0.., k0..] and op(B)[k0.., n0..]: 1024 entries each, 8 per thread
+#pragma unroll
+    for (int e = 0; e < (GT * GK) / 128; ++e) {
+      const int idx = tid + e * 128;
+      const int r = idx / GK, kk = idx % GK;
+      const int gm = m0 + r, gk = k0 + kk;
+      __nv_bfloat16 va = zero;
+      if (gm < M && gk < K) va = ta ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+      As[r][kk] = va;
+      const int gn = n0 + r;
+      __nv_bfloat16 vb = zero;
+      if (gn < N && gk < K) vb = tb ? Bm[(long long)gn * ldb + gk] : Bm[(long long)gk * ldb + gn];
+      Bs[r][kk] = vb;
+    }
+    __syncthreads();
+    unsigned af[2][4], bf[4][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int r = wm + i * 16;
+      af[i][0] = pack2(&As[r + g][2 * t]);
+      af[i][1] = pack2(&As[r + g + 8][2 * t]);
+      af[i][2] = pack2(&As[r + g][2 * t + 8]);
+      af[i][3] = pack2(&As[r + g + 8][2 * t + 8]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = wn + j * 8;
+      bf[j][0] = pack2(&Bs[c + g][2 * t]);
+      bf[j][1] = pack2(&Bs[c + g][2 * t + 8]);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};\n"
+            : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+            : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bf[j][0]), "r"(bf[j][1]));
+    __syncthreads();
+  }
+  // epilogue: c0, c1 at (row g, cols 2t, 2t+1), c2, c3 at (row g + 8, same cols)
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int gm = m0 + wm + i * 16 + g + (r >= 2 ? 8 : 0);
+        const int gn = n0 + wn + j * 8 + 2 * t + (r & 1);
+        if (gm >= M || gn >= N) continue;
+        float val = acc[i][j][r];
+        if (bias) val += bias[gn];
+        if (relu) val = fmaxf(val, 0.f);
+        if (Cf) Cf[(long long)gm * ldc + gn] = val;
+        if (Cb) Cb[(long long)gm * ldc + gn] = __float2bfloat16_rn(val);
+      }
+}
+
+__global__ void mse_grad_kernel(const float *__restrict__ z, const float *__restrict__ y, long long n, float scale,
+                                __nv_bfloat16 *__restrict__ dz, float *loss) {
+  float s = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float d = z[i] - y[i];
+    dz[i] = __float2bfloat16_rn(scale * d);
+    s += d * d;
+  }
+  if (loss) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(FULL, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s);
+  }
+}
+
+__global__ void relu_bwd_kernel(const float *__restrict__ da, const __nv_bfloat16 *__restrict__ act, long long n,
+                                __nv_bfloat16 *__restrict__ dz) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dz[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.f ? da[i] : 0.f);
+}
+
+// one thread per column, rows walked in order (deterministic)
+__global__ void colsum_kernel(const __nv_bfloat16 *__restrict__ dz, int M, int N, float *__restrict__ db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int m = 0; m < M; ++m) s += __bfloat162float(dz[(long long)m * N + n]);
+  db[n] = s;
+}
+
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                            float c2, __nv_bfloat16 *__restrict__ pb) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    p[i] = pi;
+    if (pb) pb[i] = __float2bfloat16_rn(pi);
+  }
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ x, long long n, __nv_bfloat16 *__restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+
+__global__ void gather_rows_kernel(const float *__restrict__ src, long long n_src, const long long *__restrict__ idx,
+                                   long long n_rows, int cols, float *__restrict__ dst) {
+  const long long total = n_rows * cols;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / cols;
+    const long long s = idx[r];
+    dst[i] = (s >= 0 && s < n_src) ? src[s * cols + (i - r * cols)] : 0.f;
+  }
+}
+
+int grid_for(long long n, int threads) {
+  long long g = (n + threads - 1) / threads;
+  if (g > 152LL * 16) g = 152LL * 16;
+  return (int)(g < 1 ? 1 : g);
+}
+
+float powi(float b, int e) {
+  float r = 1.f;
+  for (int i = 0; i < e && r > 0.f; ++i) r *= b;
+  return r;
+}
+
+}  // namespace
+
+extern "C" {
+
+stl_status stl_rollout(const float *u, int64_t B, int32_t T, float dt, float *x, void *stream) {
+  if (B < 0 || T < 1 || T > 65536) return stl_internal_fail(STL_ERR_INVALID_ARG, "need B >= 0 and T in [1, 65536]");
+  if (B == 0) return STL_OK;
+  if (!u || !x) return stl_internal_fail(STL_ERR_INVALID_ARG, "u / x is NULL");
+  const int wpb = 4;
+  rollout_kernel<<<(unsigned)((B + wpb - 1) / wpb), 32 * wpb, 0, (cudaStream_t)stream>>>(u, B, T, dt, x);
+  return cuda_status(cudaGetLastError(), "rollout launch failed");
+}
+
+stl_status stl_plan_adam_step(float *u, float *m, float *v, const float *xbar, const int32_t *active, int64_t B,
+                              int32_t T, float dt, float lr, float beta1, float beta2, float eps, int32_t step,
+                              float *x, void *stream) {
+  if (B < 0 || T < 1 || T > 65536) return stl_internal_fail(STL_ERR_INVALID_ARG, "need B >= 0 and T in [1, 65536]");
+  if (step < 1) return stl_internal_fail(STL_ERR_INVALID_ARG, "step must be >= 1");
+  if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f))
+    return stl_internal_fail(STL_ERR_INVALID_ARG, "need 0 <= beta < 1 and eps > 0");
+  if (B == 0) return STL_OK;
+  if (!u || !m || !v || !xbar || !active || !x) return stl_internal_fail(STL_ERR_INVALID_ARG, "NULL argument");
+  const float c1 = 1.f / (1.f - powi(beta1, step)), c2 = 1.f / (1.f - powi(beta2, step));
+  const int wpb = 4;
+  plan_adam_kernel<<<(unsigned)((B + wpb - 1) / wpb), 32 * wpb, 0, (cudaStream_t)stream>>>(
+      u, m, v, xbar, active, B, T, dt, lr, beta1, beta2, eps, c1, c2, x);
+  return cuda_status(cudaGetLastError(), "plan Adam launch failed");
+}
+
+stl_status stl_plan_check(const float *rho_hard, int32_t *active, int32_t *solved_iter, int32_t iter, float *grad_out,
+                          int64_t B, int32_t T, int32_t *n_active, void *stream) {
+  if (B < 0 || T < 1) return stl_internal_fail(STL_ERR_INVALID_ARG, "need B >= 0 and T >= 1");
+  if (B == 0) return STL_OK;
+  if (!rho_hard || !active || !solved_iter || !grad_out) return stl_internal_fail(STL_ERR_INVALID_ARG, "NULL argument");
+  plan_check_kernel<<<(unsigned)((B + 255) / 256), 256, 0, (cudaStream_t)stream>>>(rho_hard, active, solved_iter, iter,
+                                                                                  grad_out, B, T, n_active);
+  return cuda_status(cudaGetLastError(), "plan check launch failed");
+}
+
+stl_status stl_gemm_bf16(const uint16_t *a, int32_t lda, int32_t trans_a, const uint16_t *b, int32_t ldb,
+                         int32_t trans_b, int32_t M, int32_t N, int32_t K, const float *bias, int32_t relu, float *c_f32,
+                         uint16_t *c_bf16, int32_t ldc, void *stream) {
+  const int lim = 1 << 20;
+  if (M < 1 || N < 1 || K < 1 || M > lim || N > lim || K > lim)
+    return stl_internal_fail(STL_ERR_INVALID_ARG, "M, N, K must be in [1, 2^20]");
+  if (!a || !b || (!c_f32 && !c_bf16)) return stl_internal_fail(STL_ERR_INVALID_ARG, "NULL argument");
+  if (lda < (trans_a ? M : K) || ldb < (trans_b ? K : N) || ldc < N)
+    return stl_internal_fail(STL_ERR_INVALID_ARG, "leading dimension too small");
+  dim3 grid((unsigned)((N + GT - 1) / GT), (unsigned)((M + GT - 1) / GT));
+  gemm_bf16_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(
+      reinterpret_cast<const __nv_bfloat16 *>(a), lda, trans_a ? 1 : 0, reinterpret_cast<const __nv_bfloat16 *>(b), ldb,
+      trans_b ? 1 : 0, M, N, K, bias, relu ? 1 : 0, c_f32, reinterpret_cast<__nv_bfloat16 *>(c_bf16), ldc);
+  return cuda_status(cudaGetLastError(), "gemm launch failed");
+}
+
+stl_status stl_mse_grad(const float *z, const float *y, int64_t n, float scale, uint16_t *dz, float *loss,
+                        void *stream) {
+  if (n < 0) return stl_internal_fail(STL_ERR_INVALID_ARG, "n must be >= 0");
+  if (n == 0) return STL_OK;
+  if (!z || !y || !dz) return stl_internal_fail(STL_ERR_INVALID_ARG, "NULL argument");
+  mse_grad_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(z, y, n, scale,
+                                                                      reinterpret_cast<__nv_bfloat16 *>(dz), loss);
+  return cuda_status(cudaGetLastError(), "mse launch failed");
+}
+
+stl_status stl_relu_backward(const float *da, const uint16_t *act, int64_t n, uint16_t *dz, void *stream) {
+  if (n < 0) return stl_internal_fail(STL_ERR_INVALID_ARG, "n must be >= 0");
+  if (n == 0) return STL_OK;
+  if (!da || !act || !dz) return stl_internal_fail(STL_ERR_INVALID_ARG, "NULL argument");
+  relu_bwd_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(
+      da, reinterpret_cast<const __nv_bfloat16 *>(act), n, reinterpret_cast<__nv_bfloat16 *>(dz));
+  return cuda_status(cudaGetLastError(), "relu backward launch failed");
+}
+
+stl_status stl_colsum_bf16(const uint16_t *dz, int32_t M, int32_t N, float *db, void *stream) {
+  if (M < 0 || N < 1) return stl_internal_fail(STL_ERR_INVALID_ARG, "need M >= 0 and N >= 1");
+  if (!dz || !db) return stl_internal_fail(STL_ERR_INVALID_ARG, "NULL argument");
+  colsum_kernel<<<(unsigned)((N + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+      reinterpret_cast<const __nv_bfloat16 *>(dz), M, N, db);
+  return cuda_status(cudaGetLastError(), "colsum launch failed");
+}
+
+stl_status stl_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1, float beta2,
+                    float eps, int32_t step, uint16_t *p_bf16, void *stream) {
+  if (n < 0 || step < 1) return stl_internal_fail(STL_ERR_INVALID_ARG, "need n >= 0 and step >= 1");
+  if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f))
+    return stl_internal_fail(STL_ERR_INVALID_ARG, "need 0 <= beta < 1 and eps > 0");
+  if (n == 0) return STL_OK;
+  if (!p || !g || !m || !v) return stl_internal_fail(STL_ERR_INVALID_ARG, "NULL argument");
+  const float c1 = 1.f / (1.f - powi(beta1, step)), c2 = 1.f / (1.f - powi(beta2, step));
+  adam_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(p, g, m, v, n, lr, beta1, beta2, eps, c1, c2,
+                                                                  reinterpret_cast<__nv_bfloat16 *>(p_bf16));
+  return cuda_status(cudaGetLastError(), "adam launch failed");
+}
+
+stl_status stl_to_bf16(const float *x, int64_t n, uint16_t *y, void *stream) {
+  if (n < 0) return stl_internal_fail(STL_ERR_INVALID_ARG, "n must be >= 0");
+  if (n == 0) return STL_OK;
+  if (!x || !y) return stl_internal_fail(STL_ERR_INVALID_ARG, "NULL argument");
+  to_bf16_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(x, n, reinterpret_cast<__nv_bfloat16 *>(y));
+  return cuda_status(cudaGetLastError(), "bf16 conversion launch failed");
+}
+
+stl_status stl_gather_rows(const float *src, int64_t n_src, const int64_t *idx, int64_t n_rows, int32_t cols,
+                           float *dst, void *stream) {
+  if (n_rows < 0 || n_src < 0 || cols < 1)
+    return stl_internal_fail(STL_ERR_INVALID_ARG, "need n_rows, n_src >= 0 and cols >= 1");
+  if (n_rows == 0) return STL_OK;
+  if (!src || !idx || !dst) return stl_internal_fail(STL_ERR_INVALID_ARG, "NULL argument");
+  gather_rows_kernel<<<grid_for(n_rows * cols, 256), 256, 0, (cudaStream_t)stream>>>(
+      src, n_src, reinterpret_cast<const long long *>(idx), n_rows, cols, dst);
+  return cuda_status(cudaGetLastError(), "gather launch failed");
+}
+
+}  // extern "C"

@@ -1,5 +1,6 @@
 """Host-side checks of the C ABI (no GPU needed): the library loads, exports every entry point
-declared in include/stl.h, and rejects malformed formulas with the documented status."""
+declared in include/*.h, and rejects malformed formulas and arguments with the documented
+status before anything is launched."""
 import ctypes
 import math
 import os
@@ -19,15 +20,22 @@ def _lib():
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "stl.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:STL_API\s+)?(?:stl_status|void|const char \*)\s*\*?\s*(stl_\w+)\s*\(", text, flags=re.M)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"^\s*(?:STL_API\s+)?(?:stl_status|void|const char \*)\s*\*?\s*(stl_\w+)\s*\(",
+                                text, flags=re.M))
+    return sorted(names)
 
 
 def test_header_declares_the_abi():
     names = declared_functions()
     for required in ("stl_compile", "stl_robustness", "stl_robustness_backward", "stl_destroy",
-                     "stl_workspace_size", "stl_status_string"):
+                     "stl_workspace_size", "stl_status_string", "stl_rollout", "stl_plan_adam_step",
+                     "stl_gemm_bf16"):
         assert required in names
 
 
