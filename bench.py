@@ -44,10 +44,11 @@ def peaks():
 
 
 def kernel_source_sha():
+    """Hash of the sources that determine the robustness kernels and their launch plans."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2501_04194_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f.startswith(("stl_interp", "stl_internal", "stl_kern_", "stl_capi")) and f.endswith((".cu", ".cuh")):
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
