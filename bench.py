@@ -231,7 +231,26 @@ def side_measurements(stl, W, torch, dev, args):
                              "unit": UNIT, "mode": "hard", "fwd+bwd": True}
     if not args.no_plan:
         out["warm_vs_cold"] = plan_measurement(W, args)
+    out.update(mining_measurements(W))
     return out
+
+
+def mining_measurements(W):
+    """The interval search of Sec. V: rho_0 of Always_[aT, bT](s > 0) for 90,000 random (a, b)
+    with a < b on one T = 20 signal, one launch; and the mining descent of Sec. VI (1000
+    signals, T = 20, 5000 steps, c and tau annealed 1 -> 20), time per gradient step."""
+    from paper_2501_04194_gb300 import mining as M
+    rng = np.random.default_rng(0)
+    ab = np.sort(rng.uniform(0.0, 1.0, size=(90000, 2)), axis=1)
+    sig = W.mining_dataset(1, T=20, seed=1)[0, :, 0]
+    _, ms = M.interval_sweep(sig, ab[:, 0], ab[:, 1])
+    data = W.mining_dataset(1000, T=20, seed=4)
+    res = M.mine_interval(data, steps=5000, lr=1e-2, gamma=0.1, record_every=0)
+    return {"interval_sweep_90k": {"ms": ms, "intervals": 90000, "T": 20, "ns_per_interval": 1e6 * ms / 90000,
+                                   "paper_context": "1.87 ms on an M2 MacBook Pro (JAX, CPU)"},
+            "mining_descent": {"us_per_step": res["us_per_step"], "steps": 5000, "signals": 1000, "T": 20,
+                               "found": [res["a"], res["b"]], "data_interval": [0.23, 0.59],
+                               "paper_context": "122 us per step on an M2 MacBook Pro (JAX, CPU)"}}
 
 
 def plan_measurement(W, args):

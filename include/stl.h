@@ -109,7 +109,7 @@ typedef struct {
  * one was registered with stl_set_launch, else a heuristic). */
 typedef struct {
   int32_t tile;      /* samples advanced per streaming step (multiple of 32) */
-  int32_t threads;   /* CTA size: 256 or 512 */
+  int32_t threads;   /* CTA size: 64, 256 or 512 */
   int32_t segment;   /* samples per work item (a trace is split into segments) */
   int32_t reserved;
 } stl_launch;

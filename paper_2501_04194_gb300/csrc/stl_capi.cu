@@ -170,8 +170,12 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
   const int win_r = 7;    // thread-run length of the windows (odd: conflict-free strides)
   P.win_r = win_r;
   // measured defaults: forward launches prefer several 256-thread CTAs per SM, backward
-  // launches (larger per-sample state) one or two 512-thread CTAs
-  int threads = force_threads ? force_threads : h->launch.threads ? h->launch.threads : (bwd ? 512 : 256);
+  // launches (larger per-sample state) one or two 512-thread CTAs; short traces (one step of
+  // at most two 64-thread passes) run many 64-thread CTAs per SM
+  int threads = force_threads ? force_threads
+                : h->launch.threads ? h->launch.threads
+                : T <= 2 * 64 * win_r ? 64
+                : (bwd ? 512 : 256);
   int tile = h->launch.tile ? h->launch.tile : threads * win_r;
   tile = std::min(tile, round_up(T, 32));
   tile = std::max(32, round_up(tile, 32));
@@ -450,8 +454,8 @@ void stl_destroy(stl_handle h) { delete h; }
 
 stl_status stl_set_launch(stl_handle h, const stl_launch *launch) {
   if (!h || !launch) return fail(STL_ERR_INVALID_ARG, "NULL argument");
-  if (launch->threads && launch->threads != 256 && launch->threads != 512)
-    return fail(STL_ERR_INVALID_ARG, "threads must be 0, 256 or 512");
+  if (launch->threads && launch->threads != 64 && launch->threads != 256 && launch->threads != 512)
+    return fail(STL_ERR_INVALID_ARG, "threads must be 0, 64, 256 or 512");
   if (launch->tile < 0 || (launch->tile && launch->tile % 32) || launch->segment < 0)
     return fail(STL_ERR_INVALID_ARG, "tile must be a non-negative multiple of 32; segment >= 0");
   h->launch_dir[0] = h->launch_dir[1] = *launch;
@@ -625,7 +629,7 @@ stl_status stl_set_prepare(stl_set_handle s, int64_t n_traces, int64_t T_max, co
   SetState &st = s->st[backward ? 1 : 0];
   const int nf = (int)s->formulas.size();
   std::vector<KProgram> progs(nf);
-  const int threads = backward ? 512 : 256;
+  const int threads = T_max <= 2 * 64 * 7 ? 64 : backward ? 512 : 256;
   int smem = 0, gwords = 0, ut_len = 0;
   for (int k = 0; k < nf; ++k) {
     stl_status e = check_params(s->formulas[k], p);
@@ -832,8 +836,9 @@ stl_status stl_autotune(stl_handle h, const float *sig, int64_t B, int64_t T, co
   }
   const stl_launch saved = h->launch_dir[bwd ? 1 : 0];
   std::vector<stl_launch> cands;
-  for (int nt : {256, 512})
+  for (int nt : {64, 256, 512})
     for (int mult : {4, 7, 14}) {
+      if (nt == 64 && T > 8192) continue;   // 64-thread CTAs are for short traces
       stl_launch l{};
       l.threads = nt;
       l.tile = std::max(256, (nt * mult / 32) * 32);

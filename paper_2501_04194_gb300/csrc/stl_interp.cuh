@@ -1274,8 +1274,9 @@ __device__ void signal_gradient(const Cta &C, float *gs, int pst, int j0, int j1
 // resolves to the by-value parameter (constant bank), in the ragged one to the device table.
 // No minimum-blocks hint: a register cap sized for three 256-thread CTAs per SM made the
 // forward re-load program fields inside its sample loops (measured 25-30% slower).
+// 64-thread CTAs (short traces) are held to 128 registers, the budget of the larger sizes.
 template <int NT, bool BWD, bool SMOOTH, bool RAGGED>
-__global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram Pdense, LaunchArgs A) {
+__global__ void __launch_bounds__(NT, (NT == 64 ? 8 : 1)) stl_main(const __grid_constant__ KProgram Pdense, LaunchArgs A) {
   extern __shared__ float4 smem4[];
   char *smem = reinterpret_cast<char *>(smem4);
   __shared__ long long s_item;
@@ -1455,11 +1456,13 @@ __global__ void __launch_bounds__(NT) stl_main(const __grid_constant__ KProgram 
 
 // instantiation helpers used by the per-variant translation units
 #define STL_DEFINE_VARIANT(NT, BWD, SM, RG, NAME)                                                 \
-  int stl_launch_##NAME(const KProgram &P, const LaunchArgs &A) {                                \
+  int stl_launch_##NAME(const KProgram &P, const LaunchArgs &A, bool set_smem_attr) {            \
     const size_t smem = (size_t)P.smem_words * 4;                                                 \
-    cudaError_t e = cudaFuncSetAttribute(stl_main<NT, BWD, SM, RG>,                               \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    if (e != cudaSuccess) return (int)e;                                                          \
+    if (set_smem_attr) {                                                                          \
+      cudaError_t e = cudaFuncSetAttribute(stl_main<NT, BWD, SM, RG>,                             \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+      if (e != cudaSuccess) return (int)e;                                                        \
+    }                                                                                             \
     stl_main<NT, BWD, SM, RG><<<A.grid, NT, smem, (cudaStream_t)A.stream>>>(P, A);                \
     return (int)cudaGetLastError();                                                               \
   }                                                                                               \

@@ -104,7 +104,8 @@ def test_config1_small_batch(stl, mode, tau, T):
 
 
 @pytest.mark.parametrize("launch", [dict(tile=256), dict(tile=256, segment=700), dict(tile=512, threads=256),
-                                    dict(tile=1024, threads=256, segment=1500)])
+                                    dict(tile=1024, threads=256, segment=1500), dict(tile=448, threads=64),
+                                    dict(tile=256, threads=64, segment=900)])
 @pytest.mark.parametrize("mode,tau", [("hard", 1.0), ("smooth", 10.0)])
 def test_config1_streaming_and_segments(stl, launch, mode, tau):
     sig = W.config1_inputs(B=5, T=3001, seed=4)

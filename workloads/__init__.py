@@ -309,3 +309,14 @@ def rollout(u, dt=0.1):
 def random_controls(B, T=CONFIG4_T, seed=0, scale=1.0):
     rng = np.random.default_rng(seed)
     return (scale * rng.normal(size=(B, T, 2))).astype(np.float32)
+
+
+# Specification-mining data: signals of T samples equal to 1 inside a noisy interval around
+# (a, b) (fractions of the trace) and 0 elsewhere, plus Gaussian noise on every sample.
+def mining_dataset(N=1000, T=20, a=0.23, b=0.59, edge_sigma=0.02, noise=0.05, seed=0):
+    rng = np.random.default_rng(seed)
+    an = a + edge_sigma * rng.normal(size=(N, 1))
+    bn = b + edge_sigma * rng.normal(size=(N, 1))
+    t = np.arange(T)[None, :] / T
+    s = ((t >= an) & (t <= bn)).astype(np.float64) + noise * rng.normal(size=(N, T))
+    return s.astype(np.float32)[:, :, None]
