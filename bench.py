@@ -232,12 +232,50 @@ def side_measurements(stl, W, torch, dev, args):
     if not args.no_plan:
         out["warm_vs_cold"] = plan_measurement(W, args)
     out.update(mining_measurements(W))
+    out["table3_suite"] = table3_measurement(stl, W, torch, dev)
     return out
 
 
+def table3_measurement(stl, W, torch, dev):
+    """The timing study of the paper's Table III formulas phi_1..phi_6 (batch 8, signal
+    lengths up to 512): per formula and semantics, the median over T in {64, 128, 256, 512} of
+    the time per robustness call and per robustness + gradient call, in microseconds (CUDA
+    events over 50 calls through the C ABI with preallocated buffers)."""
+    from paper_2501_04194_gb300.binding import robustness_backward_raw, robustness_raw
+    forms = W.table3_formulas(D=2)
+    res = {}
+    st = torch.cuda.current_stream(dev).cuda_stream
+    for mode in ("hard", "smooth"):
+        p = stl.params(mode, tau=10.0)
+        for k, tree in enumerate(forms):
+            f = stl.Formula(tree, D=2)
+            fw, fb = [], []
+            for T in (64, 128, 256, 512):
+                x = torch.from_numpy(W.random_walk(8, T, 2, seed=k)).to(dev)
+                g = torch.randn((8, T), device=dev)
+                out = torch.empty((8, T), device=dev)
+                gs = torch.empty((8, T, 2), device=dev)
+                nf, nb = f.workspace_size(8, T, p, False), f.workspace_size(8, T, p, True)
+                wf = torch.empty(nf // 4 + 1, device=dev)
+                wb = torch.empty(nb // 4 + 1, device=dev)
+
+                def fwd():
+                    robustness_raw(f, x.data_ptr(), 8, T, None, p, out.data_ptr(), wf.data_ptr(), nf, st)
+
+                def both():
+                    fwd()
+                    robustness_backward_raw(f, x.data_ptr(), 8, T, None, p, g.data_ptr(), gs.data_ptr(), None,
+                                            wb.data_ptr(), nb, st)
+                fw.append(1e3 * time_ms(torch, fwd, steps=50, warmup=5))
+                fb.append(1e3 * time_ms(torch, both, steps=50, warmup=5))
+            res[f"phi{k + 1}_{mode}"] = {"robustness_us": float(np.median(fw)), "with_gradient_us": float(np.median(fb))}
+    res["note"] = "B=8, median over T in {64,128,256,512}; predicates synthetic (Table III gives structures only)"
+    return res
+
+
 def mining_measurements(W):
-    """The interval search of Sec. V: rho_0 of Always_[aT, bT](s > 0) for 90,000 random (a, b)
-    with a < b on one T = 20 signal, one launch; and the mining descent of Sec. VI (1000
+    """The interval search of Sec. VI: rho_0 of Always_[aT, bT](s > 0) for 90,000 random (a, b)
+    with a < b on one T = 20 signal, one launch; and the mining descent of Sec. VII-C (1000
     signals, T = 20, 5000 steps, c and tau annealed 1 -> 20), time per gradient step."""
     from paper_2501_04194_gb300 import mining as M
     rng = np.random.default_rng(0)

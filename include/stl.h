@@ -14,7 +14,7 @@
  *   until over [a,b]: max_i min(min_{k<=i} phi_{t+k}, psi_{t+i})            (Sec. IV-C)
  *   eventually_sm / always_sm: the window weighted by the sigmoid mask
  *     m_i = max(sigma(c(i-a)) - sigma(c(i-b)) - eps, 0), entering the logsumexp as a weight,
- *     with gradients to a and b                                             (Sec. V, Eq. smooth mask)
+ *     with gradients to a and b                                             (Sec. VI, Eq. smooth mask)
  * Reads past the end of a trace return the pad (Sec. IV-B Step 1): the last sample
  * (STL_PAD_LAST, its gradient goes to sample T-1) or a constant (STL_PAD_CONST).  Smooth
  * windows count pad reads with multiplicity, as the padded unroll does.  Hard-mode ties:
@@ -74,7 +74,7 @@ typedef enum {
   STL_OP_UNTIL = 8,         /* child0 U_[a,b] child1 */
   STL_OP_EVENTUALLY_SM = 9, /* sigmoid-masked window, real a < b */
   STL_OP_ALWAYS_SM = 10,
-  STL_OP_NORM_GT = 11,      /* ||diag(s)(x - g)||_2 - r: outside a ball (Sec. VI-A regions) */
+  STL_OP_NORM_GT = 11,      /* ||diag(s)(x - g)||_2 - r: outside a ball (Sec. VII-A regions) */
   STL_OP_NORM_LT = 12       /* r - ||diag(s)(x - g)||_2: inside it */
 } stl_op;
 

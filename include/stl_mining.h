@@ -1,6 +1,6 @@
 /*
- * stl_mining.h -- C ABI of the time-interval mining helpers of libstl (Sec. V and the
- * specification-mining example of Sec. VI): gradient descent on the interval [aT, bT] of a
+ * stl_mining.h -- C ABI of the time-interval mining helpers of libstl (Sec. VI and the
+ * specification-mining example of Sec. VII-C): gradient descent on the interval [aT, bT] of a
  * smooth-masked formula over a dataset of N traces of T samples, with
  *
  *   loss(a, b) = (1/N) sum_n max(-rho_n(0), 0) + gamma (a - b),   a = sigmoid(alpha), b = sigmoid(beta),

@@ -2,7 +2,7 @@
  * stl_plan.h -- C ABI of the trajectory-optimisation helpers of libstl: the batched
  * gradient-through-robustness planner and the small BF16 MLP that predicts its warm start.
  *
- * The planning problem follows the paper's trajectory-planning use (Sec. VI-A): controls u are
+ * The planning problem follows the paper's trajectory-planning use (Sec. VII-A): controls u are
  * optimised by gradient steps on the smooth robustness of a reach/avoid specification of the
  * resulting trajectory, and a problem counts as solved once the hard robustness at t = 0 is
  * >= 0.  The dynamics are the 2-D single integrator with saturated controls,

@@ -1,7 +1,7 @@
 """TEST INFRASTRUCTURE ONLY: Python access to the FP64 CPU oracle (``stl_oracle.c``).
 
 The oracle computes STL robustness traces and their analytic (sub)gradients from the
-plain definitions of the paper (Sec. III-B Eq. "quantitative", Sec. IV-B/IV-C, Sec. V
+plain definitions of the paper (Sec. III-B Eq. "quantitative", Sec. IV-B/IV-C, Sec. VI
 Eq. "smooth mask").  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline /
 reference legs of ``bench.py`` may import this package.  It shares no code with the CUDA
 library: it parses the formula tuples of ``workloads`` with its own code below and

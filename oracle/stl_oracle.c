@@ -9,7 +9,7 @@
  *   - the logsumexp smooth max / min, Sec. III-C;
  *   - the end padding of the unrolled signal, Sec. IV-B Step 1;
  *   - the Until trace, Sec. IV-C (max over i of min(min over tau<=i of phi, psi));
- *   - the sigmoid interval mask, Sec. V, Eq. "smooth mask".
+ *   - the sigmoid interval mask, Sec. VI, Eq. "smooth mask".
  *
  * Only the test suite, the smoke check and the CPU-baseline leg of bench.py may load
  * this file.  It shares no code, header or constant with the CUDA library: it has its
@@ -36,7 +36,7 @@
  *       double rounding since 53 >= 2*24+2); ``exact`` skips the rounding.
  *       Signals and bounds arrive as double (float32 inputs widen exactly), so that
  *       finite-difference checks can perturb them in double precision;
- *   R15 a norm predicate (Sec. VI-A "inside" a region) is mu(x) = ||diag(s)(x - g)||_2 with
+ *   R15 a norm predicate (Sec. VII-A "inside" a region) is mu(x) = ||diag(s)(x - g)||_2 with
  *       per-dimension scales s (0 drops a dimension) and centre g; "<" gives r - mu(x)
  *       (inside the ball of radius r), ">" gives mu(x) - r (outside it).
  */
@@ -190,7 +190,7 @@ static void work_free(work *wk, int n) {
 
 /* mu(x) for a norm predicate: the Euclidean distance of the scaled offset from a centre,
  * mu(x) = sqrt(sum_d u_d^2), u_d = s_d (x_d - g_d), with s = w[0..D) and g = w[D..2D).  This
- * is the "inside region" predicate of the trajectory-planning example, Sec. VI-A (R15).
+ * is the "inside region" predicate of the trajectory-planning example, Sec. VII-A (R15).
  * Rounded mode: every operation in float32 order, sum left to right, then a correctly
  * rounded square root (exact under double rounding, as for the other operations). */
 static double norm_mu(const octx *cx, const onode *nd, const double *row, double *u) {

@@ -405,7 +405,7 @@ __device__ __forceinline__ void pred_batch(const float *__restrict__ xs, const f
   }
 }
 
-// Norm predicates (region membership, Sec. VI-A): mu = ||diag(s)(x - g)||_2 with the same
+// Norm predicates (region membership, Sec. VII-A): mu = ||diag(s)(x - g)||_2 with the same
 // float32 order as the affine form (difference, scale, squares summed left to right, then a
 // correctly rounded square root), value mu - r (outside) or r - mu (inside).
 template <int DD>

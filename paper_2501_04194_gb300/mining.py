@@ -1,11 +1,11 @@
-"""Time-interval search and specification mining with the smooth interval mask (Sec. V).
+"""Time-interval search and specification mining with the smooth interval mask (Sec. VI).
 
 - ``interval_sweep``: robustness at t = 0 of Always_[aT, bT](s > c0) for many (a, b) at once,
-  one trace per interval in a single launch (the vectorised sweep of Sec. V);
+  one trace per interval in a single launch (the vectorised sweep of Sec. VI);
 - ``mine_interval``: gradient descent on the largest interval [a, b] that a dataset satisfies,
   loss (1/N) sum max(-rho, 0) + gamma (a - b) with a, b = sigmoid(alpha), sigmoid(beta), the mask
   sharpness c and the temperature tau annealed on a sigmoid schedule (the mining example of
-  Sec. VI).  Each step is four launches: forward, loss seed, backward with the bound gradients,
+  Sec. VII-C).  Each step is four launches: forward, loss seed, backward with the bound gradients,
   and the parameter update (include/stl_mining.h).
 """
 from __future__ import annotations

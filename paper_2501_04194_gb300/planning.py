@@ -1,6 +1,6 @@
 """Gradient-through-robustness trajectory optimisation and its learned warm start.
 
-A batch of control-synthesis problems (one reach/avoid formula per problem, Sec. VI-A use of
+A batch of control-synthesis problems (one reach/avoid formula per problem, Sec. VII-A use of
 the smooth robustness) is solved together: every iteration evaluates the hard robustness of
 the current trajectories (one ragged launch), marks the problems whose robustness at t = 0 is
 >= 0 as solved, back-propagates the smooth robustness at t = 0 of the others (one ragged

@@ -89,7 +89,7 @@ def evaluate(f, x, hard=True, tau=1.0):
         mu = x @ torch.tensor(w, dtype=x.dtype)
         return mu - c if rel == ">" else c - mu
     if op == "norm":
-        # distance of the scaled offset from the centre (Sec. VI-A region predicates)
+        # distance of the scaled offset from the centre (Sec. VII-A region predicates)
         _, rel, sc, g, r = f
         sc = torch.tensor([float(np.float32(v)) for v in sc], dtype=x.dtype)
         g = torch.tensor([float(np.float32(v)) for v in g], dtype=x.dtype)

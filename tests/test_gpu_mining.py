@@ -1,8 +1,8 @@
 """GPU checks of the interval-mining helpers (include/stl_mining.h, mining.py).
 
 - the loss seed and the parameter update against numpy written from their definitions;
-- the vectorised interval sweep against the FP64 oracle (smooth-mask Always, Sec. V);
-- gradient descent recovering the interval of a synthetic mining dataset (Sec. VI example).
+- the vectorised interval sweep against the FP64 oracle (smooth-mask Always, Sec. VI);
+- gradient descent recovering the interval of a synthetic mining dataset (Sec. VII-C example).
 """
 import math
 

@@ -10,7 +10,7 @@
 - logsumexp flattening (Sec. IV-D) and the closed flat form of the smooth Until;
 - float32 predicate arithmetic against numpy float32;
 - FP64 central finite differences and torch autograd of the masked construction for
-  every gradient, including those of the smooth-mask bounds (Sec. V).
+  every gradient, including those of the smooth-mask bounds (Sec. VI).
 """
 import math
 import os
@@ -246,7 +246,7 @@ def test_predicate_float32_rounding():
 
 
 def test_norm_predicate_pythagorean_points():
-    """Region predicates of Sec. VI-A at points whose distances are exact integers
+    """Region predicates of Sec. VII-A at points whose distances are exact integers
     (3-4-5 and 5-12-13 triangles), so every float32 step is exact: inside = r - dist,
     outside = dist - r.  A zero scale drops its dimension."""
     g = (1.0, 2.0, 0.0)
@@ -381,7 +381,7 @@ def test_hard_tie_rules():
 
 
 def test_smooth_mask_gradients_fd():
-    """Gradients of the sigmoid-masked windows (Sec. V) w.r.t. the signal and both bounds."""
+    """Gradients of the sigmoid-masked windows (Sec. VI) w.r.t. the signal and both bounds."""
     rng = np.random.default_rng(15)
     T = 30
     s = rng.normal(size=(2, T, 1))

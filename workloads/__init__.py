@@ -6,11 +6,11 @@ of nested tuples -- and holds none of the robustness arithmetic: both the CUDA
 library's binding and the CPU oracle parse the same tuple format with their own code.
 
 Formula syntax tree (the STL grammar of Sec. III-B, Eq. "STL grammar", plus the derived
-Or / Eventually / Always and the smoothed-interval operators of Sec. V):
+Or / Eventually / Always and the smoothed-interval operators of Sec. VI):
 
     ("pred", ">", w, c)        mu(x) - c  with mu(x) = sum_d w[d] * x[d]   (Eq. quantitative)
     ("pred", "<", w, c)        c - mu(x)
-    ("norm", ">", s, g, r)     ||diag(s)(x - g)||_2 - r   (outside a ball; Sec. VI-A regions)
+    ("norm", ">", s, g, r)     ||diag(s)(x - g)||_2 - r   (outside a ball; Sec. VII-A regions)
     ("norm", "<", s, g, r)     r - ||diag(s)(x - g)||_2   (inside it)
     ("true",)                  the constant formula T (rho_max = +inf)
     ("not", f)
