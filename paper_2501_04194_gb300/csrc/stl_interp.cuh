@@ -47,6 +47,18 @@ __device__ __forceinline__ bool is_pred_op(int op) { return op == OP_PGT || op =
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int L2B = 8;   // runs per level-2 block in the window middle
 
+// Float add into a node buffer or cell, which lives in shared memory unless its ring was
+// spilled to the global workspace: a shared-space reduction when the address is shared (a
+// generic atomic on a shared address is much slower), a global atomic otherwise.
+__device__ __forceinline__ void buf_add(float *p, float v) {
+  if (__isShared(p)) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+  } else {
+    atomicAdd(p, v);
+  }
+}
+
 // ------------------------------------------------------------------ combine monoids
 struct MaxV {
   using T = float;
@@ -352,12 +364,12 @@ struct ChildAdj {
   int start, T;
   __device__ __forceinline__ void add_atomic(int j, float g) const {
     if (j < 0 || g == 0.f) return;
-    if (j >= T - 1) atomicAdd(padadj, g);
-    else atomicAdd(&a[j - start], g);
+    if (j >= T - 1) buf_add(padadj, g);
+    else buf_add(&a[j - start], g);
   }
   __device__ __forceinline__ void add_owned(int j, float g) const {
     if (j < 0) return;
-    if (j >= T - 1) { if (g != 0.f) atomicAdd(padadj, g); }
+    if (j >= T - 1) { if (g != 0.f) buf_add(padadj, g); }
     else a[j - start] += g;
   }
 };
@@ -491,6 +503,95 @@ __device__ void eval_pred(const Cta &C, int n, int F, int E) {
     float s = __fmul_rn(w[0], __ldg(x));
     for (int d = 1; d < D; ++d) s = __fadd_rn(s, __fmul_rn(w[d], __ldg(x + d)));
     out.put(q, gt ? __fsub_rn(s, pc) : __fsub_rn(pc, s));
+  }
+}
+
+// All predicates of the formula in one pass over the step (signals with D <= 4): a thread
+// loads BATCH samples of the signal once and evaluates every predicate on them, each within
+// its own range [F_k, E_k) of new samples; the arithmetic is that of eval_pred / eval_norm.
+__device__ __forceinline__ void pred_range(const Cta &C, int n, int t0, int R0, int &F, int &E) {
+  const NodeRt &r = C.rt[n];
+  const int F0 = (t0 == R0) ? R0 + r.lo : t0 + r.hi;
+  F = F0 < C.T ? F0 : C.T;
+  E = frontier(C, n);
+}
+
+template <int DD>
+__device__ void eval_preds_fused(const Cta &C, int t0, int R0) {
+  const KProgram &P = *C.P;
+  const int npred = P.npred, NT = blockDim.x;
+  const float *__restrict__ xs = C.sig + C.row0 * DD;
+  // union of the predicates' ranges; empty when every predicate is complete (late steps)
+  int F = C.T, E = 0;
+  for (int k = 0; k < npred; ++k) {
+    int f, e;
+    pred_range(C, P.pred[k], t0, R0, f, e);
+    if (f < e) {
+      F = min(F, f);
+      E = max(E, e);
+    }
+  }
+  if (F >= E) return;
+  for (int base = F + threadIdx.x; base < E; base += NT * BATCH) {
+    float x[BATCH][DD];
+#pragma unroll
+    for (int b = 0; b < BATCH; ++b) {
+      const int q = base + b * NT;
+#pragma unroll
+      for (int d = 0; d < DD; ++d) x[b][d] = q < E ? __ldg(xs + (size_t)q * DD + d) : 0.f;
+    }
+    for (int k = 0; k < npred; ++k) {
+      const int n = P.pred[k];
+      const KNode &nd = P.nd[n];
+      int f, e;
+      pred_range(C, n, t0, R0, f, e);
+      const NodeOut out = node_out(C, n);
+      const float *w = P.w + nd.w_off;
+      const float c = nd.pc;
+      if (nd.op == OP_PGT || nd.op == OP_PLT) {
+        const bool gt = nd.op == OP_PGT;
+        float wr[DD];
+#pragma unroll
+        for (int d = 0; d < DD; ++d) wr[d] = w[d];
+#pragma unroll
+        for (int b = 0; b < BATCH; ++b) {
+          const int q = base + b * NT;
+          if (q < f || q >= e) continue;
+          float s = __fmul_rn(wr[0], x[b][0]);
+#pragma unroll
+          for (int d = 1; d < DD; ++d) s = __fadd_rn(s, __fmul_rn(wr[d], x[b][d]));
+          out.put(q, gt ? __fsub_rn(s, c) : __fsub_rn(c, s));
+        }
+      } else {
+        const bool gt = nd.op == OP_NGT;
+        float sr[DD], gr[DD];
+#pragma unroll
+        for (int d = 0; d < DD; ++d) { sr[d] = w[d]; gr[d] = w[DD + d]; }
+#pragma unroll
+        for (int b = 0; b < BATCH; ++b) {
+          const int q = base + b * NT;
+          if (q < f || q >= e) continue;
+          float u = __fmul_rn(sr[0], __fsub_rn(x[b][0], gr[0]));
+          float s = __fmul_rn(u, u);
+#pragma unroll
+          for (int d = 1; d < DD; ++d) {
+            u = __fmul_rn(sr[d], __fsub_rn(x[b][d], gr[d]));
+            s = __fadd_rn(s, __fmul_rn(u, u));
+          }
+          const float mu = __fsqrt_rn(s);
+          out.put(q, gt ? __fsub_rn(mu, c) : __fsub_rn(c, mu));
+        }
+      }
+    }
+  }
+}
+
+__device__ void eval_preds(const Cta &C, int t0, int R0) {
+  switch (C.P->D) {
+    case 1: eval_preds_fused<1>(C, t0, R0); return;
+    case 2: eval_preds_fused<2>(C, t0, R0); return;
+    case 3: eval_preds_fused<3>(C, t0, R0); return;
+    default: eval_preds_fused<4>(C, t0, R0); return;
   }
 }
 
@@ -772,7 +873,7 @@ __device__ __forceinline__ void scatter_run(const ChildAdj &a0, const ChildAdj &
 __device__ __forceinline__ void accumulate_shared(float *dst, float v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
-  if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(dst, v);
+  if ((threadIdx.x & 31) == 0 && v != 0.f) buf_add(dst, v);
 }
 
 // ------------------------------------------------------------------ adjoint ops
@@ -1157,8 +1258,8 @@ __device__ void hard_walk(const Cta &C, const float *__restrict__ gout_row, int 
       }
       if (head && pk >= 0 && s != 0.f) {
         const NodeRt &r = rt[C.P->pred[pk]];
-        if (j >= T - 1) atomicAdd(const_cast<float *>(&r.padadj), s);
-        else atomicAdd(&r.adj[j - (C.t0 + r.lo)], s);
+        if (j >= T - 1) buf_add(const_cast<float *>(&r.padadj), s);
+        else buf_add(&r.adj[j - (C.t0 + r.lo)], s);
       }
     }
   }
@@ -1272,11 +1373,14 @@ __device__ void signal_gradient(const Cta &C, float *gs, int pst, int j0, int j1
 // counter, in the caller's order, and read each trace's program from the device table.
 // Dense and ragged launches are separate instantiations: in the dense one every program read
 // resolves to the by-value parameter (constant bank), in the ragged one to the device table.
-// No minimum-blocks hint: a register cap sized for three 256-thread CTAs per SM made the
-// forward re-load program fields inside its sample loops (measured 25-30% slower).
-// 64-thread CTAs (short traces) are held to 128 registers, the budget of the larger sizes.
+// A tighter register cap (three 256-thread CTAs per SM, 85 registers) made the forward
+// re-load program fields inside its sample loops (measured 25-30% slower).
+// Every size is held to 128 registers per thread (two 256-thread or eight 64-thread CTAs
+// per SM); without the hint the 256-thread variants drift just past 128 and lose half their
+// resident CTAs.
 template <int NT, bool BWD, bool SMOOTH, bool RAGGED>
-__global__ void __launch_bounds__(NT, (NT == 64 ? 8 : 1)) stl_main(const __grid_constant__ KProgram Pdense, LaunchArgs A) {
+__global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? 2 : 1))
+    stl_main(const __grid_constant__ KProgram Pdense, LaunchArgs A) {
   extern __shared__ float4 smem4[];
   char *smem = reinterpret_cast<char *>(smem4);
   __shared__ long long s_item;
@@ -1354,7 +1458,16 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : 1)) stl_main(const __grid_
       C.t0 = t0;
       C.t1 = t1;
       // forward: values of every node on its new samples
+      // (with D <= 4 every predicate is evaluated by one fused pass at the first predicate's
+      // place; predicates are leaves, so each still precedes its parent)
+      const bool fuse = P.D <= 4 && P.npred > 0;
       for (int n = 0; n < P.n; ++n) {
+        if (fuse && is_pred_op(P.nd[n].op)) {
+          if (n != P.pred[0]) continue;
+          eval_preds(C, t0, R0);
+          __syncthreads();
+          continue;
+        }
         const NodeRt &r = C.rt[n];
         const int F0 = (t0 == R0) ? R0 + r.lo : t0 + r.hi;
         const int F = F0 < T ? F0 : T;
