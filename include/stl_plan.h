@@ -49,6 +49,31 @@ STL_API stl_status stl_plan_adam_step(float *u, float *m, float *v, const float 
 STL_API stl_status stl_plan_check(const float *rho_hard, int32_t *active, int32_t *solved_iter, int32_t iter,
                                   float *grad_out, int64_t B, int32_t T, int32_t *n_active, void *stream);
 
+/* ---- Trajectory optimisation with a learnable time interval (Sec. VII-A) ----
+ * Problems b = 0..B-1, each with controls u [T, 2] of the single integrator
+ * x_{t+1} = x_t + dt u_t from x_0 = start (trace x_1..x_T) and an interval (a, b) =
+ * (sigmoid(alpha), sigmoid(beta)) of a sigmoid-masked operator whose per-trace bounds (aT, bT)
+ * live in bounds[b, slot, :] (n_slots columns), minimise
+ *   J = g1 max(-rho_0, 0) + g2 exp(2 (I_nom - b + a)) + g3 (1/T) sum_t max(|u_t| - u_max, 0)
+ *       + g4 (1/T) sum_t |u_t|^2
+ * with per-problem coefficients gam[b, 0..3] = (g1, g2, g3, g4).
+ *
+ * stl_trajopt_seed: grad_out[b, 0] = -g1 where rho[b, 0] < 0, else 0 (the rest of grad_out
+ * [B, T] is not touched).
+ * stl_trajopt_step: one Adam step on u (with xbar = dJ/dx [B, T, 2] from the robustness
+ * backward: ubar_t = dt sum_{s >= t} xbar_s + the two control terms) and on theta [B, 2] =
+ * (alpha, beta) (with the per-trace bound gradients gbounds [B, n_slots, 2] of the robustness
+ * backward and the interval term), then the new trajectory x and bounds[b, slot, :].
+ * mu, vu: Adam moments of u [B, T, 2]; mth, vth: of theta [B, 2].  step >= 1 (Adam with
+ * beta1 = 0.9, beta2 = 0.999, eps = 1e-8).  The update keeps a <= b - 1e-3. */
+STL_API stl_status stl_trajopt_seed(const float *rho, const float *gam, int64_t B, int32_t T, float *grad_out,
+                                    void *stream);
+STL_API stl_status stl_trajopt_step(float *u, float *mu, float *vu, float *theta, float *mth, float *vth,
+                                    const float *xbar, const float *gbounds, const float *gam, int64_t B, int32_t T,
+                                    int32_t n_slots, int32_t slot, float dt, float start_x, float start_y,
+                                    float u_max, float i_nom, float lr_u, float lr_theta, int32_t step, float *x,
+                                    float *bounds, void *stream);
+
 /* ---- BF16 matrix products and the pieces of an MLP training step ----
  * C[M, N] = op(A) op(B) (+ bias[N]) (then max(., 0) when relu), FP32 accumulation on the
  * tensor cores (warp-level BF16 MMA).  op(A) is A [M, K] (lda >= K) or, with trans_a, A^T for

@@ -324,6 +324,9 @@ def plan_lib():
         "stl_adam": [vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp],
         "stl_to_bf16": [vp, i64, vp, vp],
         "stl_gather_rows": [vp, i64, vp, i64, i32, vp, vp],
+        "stl_trajopt_seed": [vp, vp, i64, i32, vp, vp],
+        "stl_trajopt_step": [vp, vp, vp, vp, vp, vp, vp, vp, vp, i64, i32, i32, i32, f32, f32, f32, f32, f32, f32,
+                             f32, i32, vp, vp, vp],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)

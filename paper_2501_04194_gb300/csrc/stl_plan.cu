@@ -119,6 +119,102 @@ __global__ void plan_check_kernel(const float *__restrict__ rho, int *__restrict
   }
 }
 
+// ------------------------------------------------------------------ trajectory optimisation
+// with a learnable interval: one warp per problem (suffix scans of xbar, Adam on u, prefix
+// scan of the new trajectory), lane 0 updates the problem's interval parameters.
+__global__ void trajopt_seed_kernel(const float *__restrict__ rho, const float *__restrict__ gam, long long B, int T,
+                                    float *__restrict__ gout) {
+  const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) gout[b * T] = rho[b * T] < 0.f ? -gam[b * 4] : 0.f;
+}
+
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.f / (1.f + expf(-z)); }
+
+__global__ void trajopt_step_kernel(float *__restrict__ u, float *__restrict__ mu, float *__restrict__ vu,
+                                    float *__restrict__ theta, float *__restrict__ mth, float *__restrict__ vth,
+                                    const float *__restrict__ xbar, const float *__restrict__ gb,
+                                    const float *__restrict__ gam, long long B, int T, int n_slots, int slot, float dt,
+                                    float sx, float sy, float umax, float inom, float lr_u, float lr_th, float b1,
+                                    float b2, float eps, float c1, float c2, float *__restrict__ x,
+                                    float *__restrict__ bounds) {
+  const long long b = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (b >= B) return;   // warp-uniform
+  const int lane = threadIdx.x & 31;
+  const int c = (T + 31) / 32;
+  const int t0 = min(lane * c, T), t1 = min(t0 + c, T);
+  const long long base = b * T * 2;
+  const float g3 = gam[b * 4 + 2] / (float)T, g4 = gam[b * 4 + 3] / (float)T;
+  // controls: ubar_t = dt sum_{s >= t} xbar_s + g3 [|u_t| > umax] u_t / |u_t| + 2 g4 u_t
+  float s0 = 0.f, s1 = 0.f;
+  for (int t = t0; t < t1; ++t) {
+    s0 += xbar[base + 2 * t];
+    s1 += xbar[base + 2 * t + 1];
+  }
+  float r0 = warp_excl_suffix(s0), r1 = warp_excl_suffix(s1);
+  for (int t = t1 - 1; t >= t0; --t) {
+    const long long i = base + 2 * t;
+    r0 += xbar[i];
+    r1 += xbar[i + 1];
+    const float u0 = u[i], u1 = u[i + 1];
+    const float nrm = sqrtf(u0 * u0 + u1 * u1);
+    const float lim = nrm > umax ? g3 / nrm : 0.f;
+    const float g[2] = {dt * r0 + lim * u0 + 2.f * g4 * u0, dt * r1 + lim * u1 + 2.f * g4 * u1};
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const float mi = b1 * mu[i + d] + (1.f - b1) * g[d];
+      const float vi = b2 * vu[i + d] + (1.f - b2) * g[d] * g[d];
+      mu[i + d] = mi;
+      vu[i + d] = vi;
+      u[i + d] -= lr_u * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+  }
+  __syncwarp();
+  // new trajectory x_t = start + dt sum_{s <= t} u_s
+  float p0 = 0.f, p1 = 0.f;
+  for (int t = t0; t < t1; ++t) {
+    p0 += dt * u[base + 2 * t];
+    p1 += dt * u[base + 2 * t + 1];
+  }
+  float q0 = sx + warp_excl_prefix(p0), q1 = sy + warp_excl_prefix(p1);
+  for (int t = t0; t < t1; ++t) {
+    q0 += dt * u[base + 2 * t];
+    q1 += dt * u[base + 2 * t + 1];
+    x[base + 2 * t] = q0;
+    x[base + 2 * t + 1] = q1;
+  }
+  if (lane == 0) {
+    // interval: a = sigmoid(alpha), b = sigmoid(beta); dJ/da = T gA + 2 g2 e, dJ/db = T gB - 2 g2 e
+    const float al = theta[b * 2], be = theta[b * 2 + 1];
+    const float a = sigmoidf_(al), bb = sigmoidf_(be);
+    const float e = expf(2.f * (inom - bb + a));
+    const float g2 = gam[b * 4 + 1];
+    const long long gi = (b * n_slots + slot) * 2;
+    const float ga = ((float)T * gb[gi] + 2.f * g2 * e) * a * (1.f - a);
+    const float gbt = ((float)T * gb[gi + 1] - 2.f * g2 * e) * bb * (1.f - bb);
+    const float gth[2] = {ga, gbt};
+    float nth[2];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const float mi = b1 * mth[b * 2 + d] + (1.f - b1) * gth[d];
+      const float vi = b2 * vth[b * 2 + d] + (1.f - b2) * gth[d] * gth[d];
+      mth[b * 2 + d] = mi;
+      vth[b * 2 + d] = vi;
+      nth[d] = theta[b * 2 + d] - lr_th * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+    // keep a below b (the masked window needs a < b)
+    float na = sigmoidf_(nth[0]);
+    const float nb = sigmoidf_(nth[1]);
+    if (na > nb - 1e-3f) {
+      na = fmaxf(nb - 1e-3f, 1e-6f);
+      nth[0] = logf(na / (1.f - na));
+    }
+    theta[b * 2] = nth[0];
+    theta[b * 2 + 1] = nth[1];
+    bounds[gi] = (float)T * na;
+    bounds[gi + 1] = (float)T * nb;
+  }
+}
+
 // ------------------------------------------------------------------ BF16 GEMM (mma.sync)
 // C[M,N] = op(A) op(B): 64 x 64 tiles, 4 warps of 32 x 32, K in steps of 16.  Tiles are staged
 // in shared memory as As[m][k] and Bs[n][k] (both K-contiguous), the layouts of the row / col
@@ -317,6 +413,33 @@ stl_status stl_plan_check(const float *rho_hard, int32_t *active, int32_t *solve
   plan_check_kernel<<<(unsigned)((B + 255) / 256), 256, 0, (cudaStream_t)stream>>>(rho_hard, active, solved_iter, iter,
                                                                                   grad_out, B, T, n_active);
   return cuda_status(cudaGetLastError(), "plan check launch failed");
+}
+
+stl_status stl_trajopt_seed(const float *rho, const float *gam, int64_t B, int32_t T, float *grad_out, void *stream) {
+  if (B < 0 || T < 1) return stl_internal_fail(STL_ERR_INVALID_ARG, "need B >= 0 and T >= 1");
+  if (B == 0) return STL_OK;
+  if (!rho || !gam || !grad_out) return stl_internal_fail(STL_ERR_INVALID_ARG, "NULL argument");
+  trajopt_seed_kernel<<<(unsigned)((B + 255) / 256), 256, 0, (cudaStream_t)stream>>>(rho, gam, B, T, grad_out);
+  return cuda_status(cudaGetLastError(), "trajopt seed launch failed");
+}
+
+stl_status stl_trajopt_step(float *u, float *mu, float *vu, float *theta, float *mth, float *vth, const float *xbar,
+                            const float *gbounds, const float *gam, int64_t B, int32_t T, int32_t n_slots, int32_t slot,
+                            float dt, float start_x, float start_y, float u_max, float i_nom, float lr_u,
+                            float lr_theta, int32_t step, float *x, float *bounds, void *stream) {
+  if (B < 0 || T < 1 || T > 65536) return stl_internal_fail(STL_ERR_INVALID_ARG, "need B >= 0 and T in [1, 65536]");
+  if (n_slots < 1 || slot < 0 || slot >= n_slots || step < 1)
+    return stl_internal_fail(STL_ERR_INVALID_ARG, "need 0 <= slot < n_slots and step >= 1");
+  if (B == 0) return STL_OK;
+  if (!u || !mu || !vu || !theta || !mth || !vth || !xbar || !gbounds || !gam || !x || !bounds)
+    return stl_internal_fail(STL_ERR_INVALID_ARG, "NULL argument");
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f / (1.f - powi(b1, step)), c2 = 1.f / (1.f - powi(b2, step));
+  const int wpb = 4;
+  trajopt_step_kernel<<<(unsigned)((B + wpb - 1) / wpb), 32 * wpb, 0, (cudaStream_t)stream>>>(
+      u, mu, vu, theta, mth, vth, xbar, gbounds, gam, B, T, n_slots, slot, dt, start_x, start_y, u_max, i_nom, lr_u,
+      lr_theta, b1, b2, 1e-8f, c1, c2, x, bounds);
+  return cuda_status(cudaGetLastError(), "trajopt step launch failed");
 }
 
 stl_status stl_gemm_bf16(const uint16_t *a, int32_t lda, int32_t trans_a, const uint16_t *b, int32_t ldb,

@@ -288,3 +288,71 @@ def warm_vs_cold(mlp, problems, formulas, T: int = 200, batch: int = 4096, max_i
                      "solved_at_start": float((solved == 0).mean())}
     res["warm"]["mlp_inference_ms_per_batch"] = float(np.mean(inf_ms)) if inf_ms else None
     return res
+
+
+# ---------------------------------------------------------------- learnable time interval
+def interval_trajopt_formula(T: int, target, target_r: float, goal, goal_r: float):
+    """Always over the learnable interval (bounds slot 0, caps: the whole trace) inside the target
+    disc, and Eventually (over the rest of the trace) inside the goal disc."""
+    inside_target = ("norm", "<", (1.0, 1.0), tuple(float(v) for v in target), float(target_r))
+    inside_goal = ("norm", "<", (1.0, 1.0), tuple(float(v) for v in goal), float(goal_r))
+    return ("and", ("always_sm", (float(T), float(T), 0, None), inside_target),
+            ("eventually", (0.0, float("inf"), None, None), inside_goal))
+
+
+def interval_trajopt(formula, gam: np.ndarray, T: int = 51, steps: int = 2000, dt: float = 0.1,
+                     u_max: float = 2.0, i_nom: float = 0.2, ab0=(0.14, 0.82), lr_u: float = 0.05,
+                     lr_theta: float = 0.02, tau: float = 10.0, mask_c: float = 5.0, start=(0.0, 0.0), seed: int = 0,
+                     device="cuda"):
+    """Optimise controls and the interval (a, b) of the trajectory-planning example for B
+    coefficient settings gam [B, 4] = (g1, g2, g3, g4) at once.  Returns dict(a, b [B], hard
+    robustness at t = 0 [B], x [B, T, 2], us_per_step)."""
+    B = int(gam.shape[0])
+    dev = torch.device(device)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    f = Formula(formula, D=2, n_slots=1)
+    ps = params("smooth", tau=tau, mask_c=mask_c)
+    ph = params("hard", mask_c=mask_c)
+    rng = np.random.default_rng(seed)
+    u = torch.from_numpy(rng.normal(size=(B, T, 2)).astype(np.float32)).to(dev)
+    x = torch.empty_like(u)
+    z = lambda *s: torch.zeros(s, dtype=torch.float32, device=dev)  # noqa: E731
+    mu, vu, xbar = z(B, T, 2), z(B, T, 2), z(B, T, 2)
+    a0, b0 = ab0
+    theta = torch.tensor([[np.log(a0 / (1 - a0)), np.log(b0 / (1 - b0))]] * B, dtype=torch.float32, device=dev)
+    mth, vth = z(B, 2), z(B, 2)
+    bounds = torch.tensor([[[a0 * T, b0 * T]]] * B, dtype=torch.float32, device=dev)
+    gb = z(B, 1, 2)
+    rho, gout = z(B, T), z(B, T)
+    g = torch.from_numpy(np.ascontiguousarray(gam, dtype=np.float32)).to(dev)
+    n_ws = max(f.workspace_size(B, T, ps, False), f.workspace_size(B, T, ps, True), f.workspace_size(B, T, ph, False))
+    ws = torch.empty(n_ws // 4 + 1, dtype=torch.float32, device=dev)
+    # x from the initial controls: one step with zero gradients and zero learning rates
+    plan_call("stl_trajopt_step", _p(u), _p(mu), _p(vu), _p(theta), _p(mth), _p(vth), _p(xbar), _p(gb), _p(g), B, T, 1,
+              0, dt, start[0], start[1], u_max, i_nom, 0.0, 0.0, 1, _p(x), _p(bounds), st)
+    mu.zero_(); vu.zero_(); mth.zero_(); vth.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(1, steps + 1):
+        robustness_raw_dense(f, x, B, T, bounds, ps, rho, ws, n_ws, st)
+        plan_call("stl_trajopt_seed", _p(rho), _p(g), B, T, _p(gout), st)
+        robustness_backward_raw_dense(f, x, B, T, bounds, ps, gout, xbar, gb, ws, n_ws, st)
+        plan_call("stl_trajopt_step", _p(u), _p(mu), _p(vu), _p(theta), _p(mth), _p(vth), _p(xbar), _p(gb), _p(g), B,
+                  T, 1, 0, dt, start[0], start[1], u_max, i_nom, lr_u, lr_theta, k, _p(x), _p(bounds), st)
+    e1.record()
+    robustness_raw_dense(f, x, B, T, bounds, ph, rho, ws, n_ws, st)
+    torch.cuda.synchronize(dev)
+    th = theta.cpu().numpy()
+    ab = 1.0 / (1.0 + np.exp(-th))
+    return {"a": ab[:, 0], "b": ab[:, 1], "rho_hard": rho[:, 0].cpu().numpy(), "x": x.cpu().numpy(),
+            "bounds": bounds.cpu().numpy(), "us_per_step": 1e3 * e0.elapsed_time(e1) / steps}
+
+
+def robustness_raw_dense(f, x, B, T, bounds, p, out, ws, n_ws, stream):
+    from .binding import robustness_raw
+    robustness_raw(f, _p(x), B, T, _p(bounds), p, _p(out), _p(ws), n_ws, stream)
+
+
+def robustness_backward_raw_dense(f, x, B, T, bounds, p, gout, gsig, gb, ws, n_ws, stream):
+    from .binding import robustness_backward_raw
+    robustness_backward_raw(f, _p(x), B, T, _p(bounds), p, _p(gout), _p(gsig), _p(gb), _p(ws), n_ws, stream)

@@ -217,3 +217,72 @@ def test_warm_start_pipeline_small(stl):
     for b in range(0, 64, 4):
         ref = oracle.robustness(forms[8192 + b], x[b:b + 1])[0]
         np.testing.assert_array_equal(rho[b], ref.astype(np.float32))
+
+
+def np_trajopt_step(u, mu, vu, th, mth, vth, xbar, gb, gam, T, dt, start, umax, inom, lr_u, lr_th, step):
+    """The update of stl_trajopt_step written from its definition, in float64."""
+    b1, b2, eps = 0.9, 0.999, 1e-8
+    c1, c2 = 1 / (1 - b1 ** step), 1 / (1 - b2 ** step)
+    suf = np.cumsum(xbar[:, ::-1].astype(np.float64), axis=1)[:, ::-1]
+    nrm = np.linalg.norm(u.astype(np.float64), axis=2, keepdims=True)
+    g3, g4 = gam[:, 2, None, None] / T, gam[:, 3, None, None] / T
+    gu = dt * suf + np.where(nrm > umax, g3 / np.maximum(nrm, 1e-30), 0) * u + 2 * g4 * u
+    mu2 = b1 * mu + (1 - b1) * gu
+    vu2 = b2 * vu + (1 - b2) * gu * gu
+    u2 = u - lr_u * mu2 * c1 / (np.sqrt(vu2 * c2) + eps)
+    x2 = np.asarray(start)[None, None, :] + dt * np.cumsum(u2, axis=1)
+    a, bb = 1 / (1 + np.exp(-th[:, 0])), 1 / (1 + np.exp(-th[:, 1]))
+    e = np.exp(2 * (inom - bb + a))
+    gth = np.stack([(T * gb[:, 0, 0] + 2 * gam[:, 1] * e) * a * (1 - a),
+                    (T * gb[:, 0, 1] - 2 * gam[:, 1] * e) * bb * (1 - bb)], axis=1)
+    mth2 = b1 * mth + (1 - b1) * gth
+    vth2 = b2 * vth + (1 - b2) * gth * gth
+    th2 = th - lr_th * mth2 * c1 / (np.sqrt(vth2 * c2) + eps)
+    return u2, mu2, vu2, x2, th2
+
+
+def test_trajopt_step(stl):
+    rng = np.random.default_rng(8)
+    B, T, dt, umax, inom, lr_u, lr_th, step = 6, 51, 0.1, 2.0, 0.2, 0.05, 0.02, 4
+    u = (1.5 * rng.normal(size=(B, T, 2))).astype(np.float32)
+    mu = (0.01 * rng.normal(size=(B, T, 2))).astype(np.float32)
+    vu = (0.01 * rng.random(size=(B, T, 2))).astype(np.float32)
+    xbar = rng.normal(size=(B, T, 2)).astype(np.float32)
+    gb = (0.1 * rng.normal(size=(B, 1, 2))).astype(np.float32)
+    gam = rng.uniform(0.1, 2.0, size=(B, 4)).astype(np.float32)
+    th = np.stack([np.full(B, -1.5), np.full(B, 1.2)], axis=1).astype(np.float32)
+    mth = (0.01 * rng.normal(size=(B, 2))).astype(np.float32)
+    vth = (0.01 * rng.random(size=(B, 2))).astype(np.float32)
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in
+         dict(u=u, mu=mu, vu=vu, xbar=xbar, gb=gb, gam=gam, th=th, mth=mth, vth=vth).items()}
+    x = torch.zeros((B, T, 2), device="cuda")
+    bounds = torch.zeros((B, 1, 2), device="cuda")
+    call("stl_trajopt_step", d["u"].data_ptr(), d["mu"].data_ptr(), d["vu"].data_ptr(), d["th"].data_ptr(),
+         d["mth"].data_ptr(), d["vth"].data_ptr(), d["xbar"].data_ptr(), d["gb"].data_ptr(), d["gam"].data_ptr(),
+         B, T, 1, 0, dt, 0.5, -0.25, umax, inom, lr_u, lr_th, step, x.data_ptr(), bounds.data_ptr(), stream())
+    u2, mu2, vu2, x2, th2 = np_trajopt_step(u, mu, vu, th, mth, vth, xbar, gb, gam, T, dt, (0.5, -0.25), umax, inom,
+                                           lr_u, lr_th, step)
+    np.testing.assert_allclose(d["u"].cpu().numpy(), u2, rtol=1e-5, atol=2e-6)
+    np.testing.assert_allclose(d["mu"].cpu().numpy(), mu2, rtol=1e-4, atol=1e-6)
+    np.testing.assert_allclose(x.cpu().numpy(), x2, rtol=1e-5, atol=2e-5)
+    np.testing.assert_allclose(d["th"].cpu().numpy(), th2, rtol=1e-5, atol=1e-6)
+    ab = 1 / (1 + np.exp(-th2.astype(np.float64)))
+    np.testing.assert_allclose(bounds.cpu().numpy()[:, 0, :], T * ab, rtol=1e-5)
+
+
+def test_interval_trajopt_example(stl):
+    """The trajectory-planning example with a learnable interval (T = 51, coefficients
+    (1.1, 0.05, 2, 0.5), (a, b) from (0.14, 0.82)) over a few coefficient settings at once: the
+    interval grows past the nominal 0.2, the paper's setting ends within a small margin of
+    satisfaction (the loss only sees the smooth robustness) and one of the settings satisfies
+    the specification; the hard robustness of the final trajectories and bounds matches the
+    oracle bit for bit."""
+    from paper_2501_04194_gb300 import planning as PL
+    T = 51
+    form = PL.interval_trajopt_formula(T, (1.5, 1.0), 0.6, (3.0, 2.5), 0.3)
+    gam = np.array([[1.1, 0.05, 2.0, 0.5], [1.1, 0.2, 2.0, 0.5], [2.0, 0.05, 2.0, 0.1]], dtype=np.float32)
+    res = PL.interval_trajopt(form, gam, T=T, steps=1500)
+    assert np.all(res["b"] - res["a"] > 0.2)
+    assert res["rho_hard"][0] > -0.05 and np.any(res["rho_hard"] >= 0), res["rho_hard"]
+    ref = oracle.robustness(form, res["x"], bounds=res["bounds"])[:, 0]
+    np.testing.assert_array_equal(res["rho_hard"], ref.astype(np.float32))
