@@ -26,7 +26,7 @@ _lib = None
 # node encoding private to the oracle (mirrors the enum in stl_oracle.c)
 _OPS = {"pred>": 0, "pred<": 1, "true": 2, "not": 3, "and": 4, "or": 5, "eventually": 6,
         "always": 7, "until": 8, "eventually_sm": 9, "always_sm": 10, "norm>": 11, "norm<": 12}
-HARD, SMOOTH = 0, 1
+HARD, SMOOTH, SOFTMAX = 0, 1, 2
 
 
 class _ONode(ctypes.Structure):
@@ -239,4 +239,4 @@ def robustness_grad_ragged_multi(formulas, formula_id, sig, offsets, grad_out, b
 
 
 __all__ = ["robustness_grad_ragged_multi", "build", "robustness", "robustness_grad", "robustness_ragged_multi", "num_threads",
-           "HARD", "SMOOTH", "math"]
+           "HARD", "SMOOTH", "SOFTMAX", "math"]

@@ -38,7 +38,12 @@
  *       finite-difference checks can perturb them in double precision;
  *   R15 a norm predicate (Sec. VII-A "inside" a region) is mu(x) = ||diag(s)(x - g)||_2 with
  *       per-dimension scales s (0 drops a dimension) and centre g; "<" gives r - mu(x)
- *       (inside the ball of radius r), ">" gives mu(x) - r (outside it).
+ *       (inside the ball of radius r), ">" gives mu(x) - r (outside it);
+ *   R17 softmax-weighted mode (the "soft" approximation of Sec. III-C): every min/max over a
+ *       multiset becomes sum v e^{sgn tau v} / sum e^{sgn tau v} over that same multiset
+ *       (windows with pads counted with multiplicity; the two operands of and/or; the three
+ *       levels of the Until construction of Sec. IV-C, each reduced once, so no nesting
+ *       of the window itself, Sec. IV-D); the smooth mask enters as a weight m_i on both sums.
  */
 #include <math.h>
 #include <pthread.h>
@@ -53,7 +58,7 @@ enum {
 };
 enum { O_PAD_LAST = 0, O_PAD_CONST = 1 };
 enum { O_MAX_D = 64 };   /* largest signal dimension the oracle accepts */
-enum { O_HARD = 0, O_SMOOTH = 1 };
+enum { O_HARD = 0, O_SMOOTH = 1, O_SOFTMAX = 2 };
 
 typedef struct {
   int32_t op, c0, c1, slot;
@@ -148,6 +153,43 @@ static double lse(const double *v, const double *w, int64_t n, double tau, doubl
   return (m + log(s)) / tau;
 }
 
+/* softmax-weighted max (sgn = +1) or min (sgn = -1) of n values (Sec. III-C, the "soft"
+   approximation; R17): y = sum w_i v_i e^{sgn tau v_i} / sum w_i e^{sgn tau v_i}, weights w may be
+   NULL (all ones), entries with w_i <= 0 are absent.  Infinite entries: sgn*v = -inf carries no
+   weight; if some sgn*v = +inf, y is that infinity; with no finite weight left y = -sgn*inf.
+   p (may be NULL) receives the normalised weights p_i = w_i e^{sgn tau v_i} / sum (0 for
+   absent or infinite entries). */
+static double swm(const double *v, const double *w, int64_t n, double tau, double sgn, double *p) {
+  double m = -INFINITY;
+  for (int64_t i = 0; i < n; i++) {
+    if (p) p[i] = 0.0;
+    if (w && w[i] <= 0.0) continue;
+    double z = sgn * v[i];
+    if (z == INFINITY) return v[i];
+    if (z == -INFINITY) continue;
+    if (sgn * tau * v[i] > m) m = sgn * tau * v[i];
+  }
+  if (m == -INFINITY) return -sgn * INFINITY;
+  double s = 0.0, num = 0.0;
+  for (int64_t i = 0; i < n; i++) {
+    if (w && w[i] <= 0.0) continue;
+    if (isinf(v[i])) continue;
+    double e = (w ? w[i] : 1.0) * exp(sgn * tau * v[i] - m);
+    s += e;
+    num += e * v[i];
+    if (p) p[i] = e;
+  }
+  if (p)
+    for (int64_t i = 0; i < n; i++) p[i] /= s;
+  return num / s;
+}
+
+/* d y / d v_i of swm: p_i (1 + sgn tau (v_i - y)) (0 for absent or infinite entries) */
+static double swm_d(double p, double v, double y, double tau, double sgn) {
+  if (p == 0.0 || isinf(v) || isinf(y)) return 0.0;
+  return p * (1.0 + sgn * tau * (v - y));
+}
+
 /* two-term smooth min / max (Sec. III-C): min(x,y) - log1p(e^{-tau|x-y|})/tau */
 static double smin2(double x, double y, double tau) {
   if (x == y) return x - log(2.0) / tau;
@@ -178,7 +220,7 @@ static int work_init(work *wk, int n, int64_t T, int64_t wcap) {
   wk->cap = wcap;
   wk->tmp = calloc((size_t)wcap, sizeof(double));
   wk->tmp2 = calloc((size_t)wcap, sizeof(double));
-  wk->tmp3 = calloc((size_t)wcap, sizeof(double));
+  wk->tmp3 = calloc((size_t)wcap * 2, sizeof(double));   /* two weight vectors (softmax Until) */
   wk->itmp = calloc((size_t)wcap, sizeof(int64_t));
   return (wk->tmp && wk->tmp2 && wk->tmp3 && wk->itmp) ? 0 : -1;
 }
@@ -238,6 +280,7 @@ static void forward_node(const octx *cx, work *wk, int k, int64_t b, const doubl
   double *y = wk->val[k];
   const double tau = cx->tau;
   const int smooth = cx->mode == O_SMOOTH;
+  const int soft = cx->mode == O_SOFTMAX;
   switch (nd->op) {
     case O_PRED_GT:
     case O_PRED_LT:
@@ -256,7 +299,10 @@ static void forward_node(const octx *cx, work *wk, int k, int64_t b, const doubl
     case O_OR: {
       const double *x = wk->val[nd->c0], *z = wk->val[nd->c1];
       for (int64_t t = 0; t < T; t++) {
-        if (smooth) y[t] = nd->op == O_AND ? smin2(x[t], z[t], tau) : smax2(x[t], z[t], tau);
+        if (soft) {
+          const double v2[2] = {x[t], z[t]};
+          y[t] = swm(v2, NULL, 2, tau, nd->op == O_AND ? -1.0 : 1.0, NULL);
+        } else if (smooth) y[t] = nd->op == O_AND ? smin2(x[t], z[t], tau) : smax2(x[t], z[t], tau);
         else if (nd->op == O_AND) y[t] = x[t] <= z[t] ? x[t] : z[t];
         else y[t] = x[t] >= z[t] ? x[t] : z[t];
       }
@@ -271,7 +317,9 @@ static void forward_node(const octx *cx, work *wk, int k, int64_t b, const doubl
       for (int64_t t = 0; t < T; t++) {
         int64_t n = 0;
         for (int64_t i = ia; i <= ib; i++) wk->tmp[n++] = rd(x, T, t + i, nd, &src);
-        if (smooth) {
+        if (soft) {
+          y[t] = swm(wk->tmp, NULL, n, tau, sgn, NULL);
+        } else if (smooth) {
           y[t] = sgn * lse(wk->tmp, NULL, n, tau, sgn);
         } else {
           double best = wk->tmp[0];
@@ -287,6 +335,18 @@ static void forward_node(const octx *cx, work *wk, int k, int64_t b, const doubl
       int64_t ia, ib, src;
       int_window(cx, nd, b, T, &ia, &ib);
       for (int64_t t = 0; t < T; t++) {
+        if (soft) {
+          /* S1: softmin over phi_{t..t+i}; S2: softmin of the pair (S1, psi_{t+i}); S3: softmax
+             over i in [a, b] (each level one softmax-weighted reduction, as in Sec. IV-C) */
+          int64_t n = 0;
+          for (int64_t i = 0; i <= ib; i++) wk->tmp2[i] = rd(ph, T, t + i, nd, &src);
+          for (int64_t i = ia; i <= ib; i++) {
+            const double v2[2] = {swm(wk->tmp2, NULL, i + 1, tau, -1.0, NULL), rd(ps, T, t + i, nd, &src)};
+            wk->tmp[n++] = swm(v2, NULL, 2, tau, -1.0, NULL);
+          }
+          y[t] = swm(wk->tmp, NULL, n, tau, 1.0, NULL);
+          continue;
+        }
         if (!smooth) {
           double P = INFINITY, best = -INFINITY;
           for (int64_t i = 0; i <= ib; i++) {
@@ -329,7 +389,9 @@ static void forward_node(const octx *cx, work *wk, int k, int64_t b, const doubl
           n++;
         }
         if (n == 0) { y[t] = sgn * -INFINITY; continue; }
-        if (smooth) {
+        if (soft) {
+          y[t] = swm(wk->tmp, wk->tmp3, n, tau, sgn, NULL);
+        } else if (smooth) {
           y[t] = sgn * lse(wk->tmp, wk->tmp3, n, tau, sgn);
         } else {
           double best = wk->tmp[0];
@@ -349,6 +411,7 @@ static void backward_node(const octx *cx, work *wk, int k, int64_t b, int64_t T,
   const double *y = wk->val[k];
   const double tau = cx->tau;
   const int smooth = cx->mode == O_SMOOTH;
+  const int soft = cx->mode == O_SOFTMAX;
   switch (nd->op) {
     case O_PRED_GT:
     case O_PRED_LT:
@@ -366,6 +429,15 @@ static void backward_node(const octx *cx, work *wk, int k, int64_t b, int64_t T,
       double *xa = wk->adj[nd->c0], *za = wk->adj[nd->c1];
       for (int64_t t = 0; t < T; t++) {
         if (g[t] == 0.0) continue;
+        if (soft) {
+          const double sg = nd->op == O_AND ? -1.0 : 1.0;
+          const double v2[2] = {x[t], z[t]};
+          double p2[2];
+          swm(v2, NULL, 2, tau, sg, p2);
+          xa[t] += g[t] * swm_d(p2[0], x[t], y[t], tau, sg);
+          za[t] += g[t] * swm_d(p2[1], z[t], y[t], tau, sg);
+          continue;
+        }
         if (smooth) {
           /* d smin(x,z)/dx = sigmoid(tau (z - x)); d smax(x,z)/dx = sigmoid(tau (x - z)) */
           double s = nd->op == O_AND ? 1.0 : -1.0;
@@ -387,6 +459,17 @@ static void backward_node(const octx *cx, work *wk, int k, int64_t b, int64_t T,
       const double sgn = nd->op == O_EV ? 1.0 : -1.0;
       for (int64_t t = 0; t < T; t++) {
         if (g[t] == 0.0) continue;
+        if (soft) {
+          int64_t n = 0;
+          for (int64_t i = ia; i <= ib; i++) {
+            wk->tmp[n] = rd(x, T, t + i, nd, &wk->itmp[n]);
+            n++;
+          }
+          swm(wk->tmp, NULL, n, tau, sgn, wk->tmp3);
+          for (int64_t i = 0; i < n; i++)
+            if (wk->itmp[i] >= 0) xa[wk->itmp[i]] += g[t] * swm_d(wk->tmp3[i], wk->tmp[i], y[t], tau, sgn);
+          continue;
+        }
         if (smooth) {
           /* d/dx_{t+i} of (sgn/tau) log sum e^{sgn tau x} = e^{sgn tau (x - y)} */
           for (int64_t i = ia; i <= ib; i++) {
@@ -412,6 +495,39 @@ static void backward_node(const octx *cx, work *wk, int k, int64_t b, int64_t T,
       int_window(cx, nd, b, T, &ia, &ib);
       for (int64_t t = 0; t < T; t++) {
         if (g[t] == 0.0) continue;
+        if (soft) {
+          /* chain rule through the three levels: dU/dz_i, dz_i/dP_i and dz_i/dpsi_{t+i},
+             dP_i/dphi_{t+k} (k <= i), each the derivative of one softmax-weighted reduction */
+          int64_t n = 0, src;
+          for (int64_t i = 0; i <= ib; i++) wk->tmp2[i] = rd(ph, T, t + i, nd, &src);
+          for (int64_t i = ia; i <= ib; i++) {
+            const double v2[2] = {swm(wk->tmp2, NULL, i + 1, tau, -1.0, NULL), rd(ps, T, t + i, nd, &src)};
+            wk->tmp[n++] = swm(v2, NULL, 2, tau, -1.0, NULL);
+          }
+          swm(wk->tmp, NULL, n, tau, 1.0, wk->tmp3);   /* outer weights over i */
+          for (int64_t i = ia; i <= ib; i++) {
+            const double zi = wk->tmp[i - ia];
+            const double dUz = g[t] * swm_d(wk->tmp3[i - ia], zi, y[t], tau, 1.0);
+            if (dUz == 0.0) continue;
+            double pk[2];
+            int64_t qs;
+            const double P = swm(wk->tmp2, NULL, i + 1, tau, -1.0, NULL);
+            const double v2[2] = {P, rd(ps, T, t + i, nd, &qs)};
+            swm(v2, NULL, 2, tau, -1.0, pk);
+            if (qs >= 0) psa[qs] += dUz * swm_d(pk[1], v2[1], zi, tau, -1.0);
+            const double dzP = dUz * swm_d(pk[0], P, zi, tau, -1.0);
+            if (dzP == 0.0) continue;
+            /* inner weights over k <= i (tmp3 is busy; reuse the node scratch of n entries after it) */
+            double *pin = wk->tmp3 + n;
+            swm(wk->tmp2, NULL, i + 1, tau, -1.0, pin);
+            for (int64_t kk = 0; kk <= i; kk++) {
+              int64_t ks;
+              rd(ph, T, t + kk, nd, &ks);
+              if (ks >= 0) pha[ks] += dzP * swm_d(pin[kk], wk->tmp2[kk], P, tau, -1.0);
+            }
+          }
+          continue;
+        }
         if (!smooth) {
           /* R5: earliest maximising i; P wins ties in min(P, psi); earliest argmin in P */
           double P = INFINITY, best = -INFINITY;
@@ -468,6 +584,26 @@ static void backward_node(const octx *cx, work *wk, int k, int64_t b, int64_t T,
       double ga = 0.0, gbv = 0.0;
       for (int64_t t = 0; t < T; t++) {
         if (g[t] == 0.0) continue;
+        if (soft) {
+          /* y = sum m_i v_i e_i / sum m_i e_i: dy/dv_i = p_i (1 + sgn tau (v_i - y)),
+             dy/dm_i = p_i (v_i - y) / m_i, chained to a and b through the mask */
+          int64_t n = 0;
+          for (int64_t i = 0; i <= last; i++) {
+            wk->tmp[i] = rd(x, T, t + i, nd, &wk->itmp[i]);
+            wk->tmp2[i] = smask((double)i, a, bb, cx->mask_c, cx->mask_eps);
+            n = i + 1;
+          }
+          swm(wk->tmp, wk->tmp2, n, tau, sgn, wk->tmp3);
+          for (int64_t i = 0; i < n; i++) {
+            if (wk->tmp2[i] <= 0.0 || wk->tmp3[i] == 0.0) continue;
+            if (wk->itmp[i] >= 0) xa[wk->itmp[i]] += g[t] * swm_d(wk->tmp3[i], wk->tmp[i], y[t], tau, sgn);
+            if (isinf(y[t]) || isinf(wk->tmp[i])) continue;
+            const double dm = g[t] * wk->tmp3[i] * (wk->tmp[i] - y[t]) / wk->tmp2[i];
+            ga += dm * smask_da((double)i, a, bb, cx->mask_c, cx->mask_eps);
+            gbv += dm * smask_db((double)i, a, bb, cx->mask_c, cx->mask_eps);
+          }
+          continue;
+        }
         if (smooth) {
           for (int64_t i = 0; i <= last; i++) {
             double m = smask((double)i, a, bb, cx->mask_c, cx->mask_eps);

@@ -32,15 +32,26 @@ def _window(a, b, T):
     return ia, max(ib, ia)
 
 
+def _softw(v, dim, tau, sgn):
+    """Softmax-weighted max (sgn = 1) / min (sgn = -1) along dim; masked-out entries are
+    -sgn*inf and carry no weight."""
+    p = torch.softmax(sgn * tau * v, dim=dim)
+    return (p * torch.where(torch.isfinite(v), v, torch.zeros_like(v))).sum(dim=dim)
+
+
 def _smin(v, dim, tau, hard):
     if hard:
         return v.amin(dim=dim)
+    if hard is None:
+        return _softw(v, dim, tau, -1.0)
     return -torch.logsumexp(-tau * v, dim=dim) / tau
 
 
 def _smax(v, dim, tau, hard):
     if hard:
         return v.amax(dim=dim)
+    if hard is None:
+        return _softw(v, dim, tau, 1.0)
     return torch.logsumexp(tau * v, dim=dim) / tau
 
 
@@ -79,7 +90,8 @@ def until(p, q, a, b, pad, hard, tau):
 
 
 def evaluate(f, x, hard=True, tau=1.0):
-    """Robustness trace of formula tuple ``f`` on one trace ``x`` [T, D] (torch fp64)."""
+    """Robustness trace of formula tuple ``f`` on one trace ``x`` [T, D] (torch fp64).
+    hard=True: min/max; False: logsumexp; None: softmax-weighted min/max."""
     op = f[0]
     if op == "pred":
         # predicate parameters are float32 numbers (the libraries store them as float)

@@ -395,3 +395,123 @@ def test_smooth_mask_gradients_fd():
         loss_s = lambda x: float((oracle.robustness(f, x, bounds=bounds, **kw) * gout).sum())  # noqa: E731
         np.testing.assert_allclose(gb, _fd(loss_b, bounds), rtol=1e-6, atol=1e-7)
         np.testing.assert_allclose(g, _fd(loss_s, s), rtol=1e-6, atol=1e-7)
+
+
+# ------------------------------------------------------------------ softmax-weighted mode (R17)
+SOFTMAX = oracle.SOFTMAX
+
+
+def test_softmax_worked_values():
+    """Hand-computed: at tau = ln 2 the weights of {0, 1} are {1, 2} for the max (value 2/3)
+    and {1, 1/2} for the min (value 1/3); a window that reads past the end counts the last
+    sample once per read (the multiset {1, 1, 1})."""
+    s = one([0.0, 1.0])
+    tau = math.log(2.0)
+    ev = oracle.robustness(W.Eventually(0, 1, x_pred()), s, mode=SOFTMAX, tau=tau)[0]
+    np.testing.assert_allclose(ev, [2 / 3, 1.0], rtol=1e-14)
+    al = oracle.robustness(W.Always(0, 1, x_pred()), s, mode=SOFTMAX, tau=tau)[0]
+    np.testing.assert_allclose(al, [1 / 3, 1.0], rtol=1e-14)
+    s3 = one([0.0, 1.0, -1.0])
+    ev3 = oracle.robustness(W.Eventually(0, 2, x_pred()), s3, mode=SOFTMAX, tau=tau)[0]
+    # t = 0: {0, 1, -1} -> weights {1, 2, 1/2}; t = 2: {-1, -1, -1}
+    np.testing.assert_allclose(ev3[[0, 2]], [(0 + 2 - 0.5) / 3.5, -1.0], rtol=1e-14)
+
+
+def test_softmax_limits():
+    """tau -> 0: the arithmetic mean of the window's multiset (pads included); tau -> inf:
+    the hard value (well-separated samples)."""
+    rng = np.random.default_rng(30)
+    T = 12
+    x = rng.permutation(T).astype(np.float32)      # distinct integers
+    f = W.Eventually(2, 5, x_pred())
+    lo = oracle.robustness(f, one(x), mode=SOFTMAX, tau=1e-7)[0]
+    ext = np.concatenate([x, np.full(5, x[-1])]).astype(np.float64)
+    mean = np.array([ext[t + 2:t + 6].mean() for t in range(T)])
+    np.testing.assert_allclose(lo, mean, rtol=0, atol=1e-5)
+    hi = oracle.robustness(f, one(x), mode=SOFTMAX, tau=60.0)[0]
+    hard = oracle.robustness(f, one(x))[0]
+    np.testing.assert_allclose(hi, hard, rtol=0, atol=1e-20 + 4 * 2 * math.exp(-60.0))
+
+
+@pytest.mark.parametrize("op", ["eventually", "always"])
+@pytest.mark.parametrize("pad", [None, -3.0])
+def test_softmax_windows_match_masking(op, pad):
+    rng = np.random.default_rng(31)
+    for T in range(1, 8):
+        for s in _tiny_signals(rng, T, n=2):
+            xt = torch.tensor(s, dtype=torch.float64)
+            for a in range(0, T + 1):
+                for b in list(range(a, T + 2)) + [math.inf]:
+                    f = (op, (float(a), float(b), None, pad), x_pred())
+                    got = oracle.robustness(f, one(s), mode=SOFTMAX, tau=1.3)[0]
+                    want = mr.eventually_always(xt, a, b, pad, op, None, 1.3).numpy()
+                    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("pad", [None, 1.0])
+def test_softmax_until_matches_masking(pad):
+    rng = np.random.default_rng(32)
+    for T in range(1, 7):
+        for _ in range(2):
+            s = rng.normal(size=(T, 2)).astype(np.float32)
+            xt = torch.tensor(s, dtype=torch.float64)
+            for a in range(0, T + 1):
+                for b in list(range(a, T + 2)) + [math.inf]:
+                    f = W.Until(a, b, W.gt([1, 0], 0.0), W.gt([0, 1], 0.0), pad=pad)
+                    got = oracle.robustness(f, s[None], mode=SOFTMAX, tau=1.7)[0]
+                    want = mr.until(xt[:, 0], xt[:, 1], a, b, pad, None, 1.7).numpy()
+                    np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-11)
+
+
+def test_softmax_nested_and_duality():
+    """Nested formulas against the masking construction; Always phi = -Eventually(not phi);
+    unlike logsumexp, the softmax-weighted window is not the nesting of two-term operators
+    (Sec. IV-D): Eventually_[0,2] p differs from p or (p one step later) or (two steps later)."""
+    rng = np.random.default_rng(33)
+    for f in [W.config0_formula(), W.config1_formula()] + W.table3_formulas(D=2, I=(1, 4))[:5]:
+        D = 3 if f == W.config1_formula() else 2
+        s = rng.normal(size=(17, D)).astype(np.float32)
+        got = oracle.robustness(f, s[None], mode=SOFTMAX, tau=1.5, exact=True)[0]
+        want = mr.evaluate(f, torch.tensor(s, dtype=torch.float64), hard=None, tau=1.5).numpy()
+        np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-10)
+    s = rng.normal(size=(1, 20, 1)).astype(np.float32)
+    al = oracle.robustness(W.Always(2, 6, x_pred()), s, mode=SOFTMAX, tau=2.0)
+    ev = oracle.robustness(W.Not(W.Eventually(2, 6, W.Not(x_pred()))), s, mode=SOFTMAX, tau=2.0)
+    np.testing.assert_allclose(al, ev, rtol=1e-13, atol=1e-13)
+    flat = oracle.robustness(W.Eventually(0, 2, x_pred()), s, mode=SOFTMAX, tau=2.0)[0, :10]
+    nest = oracle.robustness(W.Or(x_pred(), W.Eventually(1, 2, x_pred())), s, mode=SOFTMAX, tau=2.0)[0, :10]
+    assert np.abs(flat - nest).max() > 1e-3
+    flat_l = oracle.robustness(W.Eventually(0, 2, x_pred()), s, mode=SMOOTH, tau=2.0)[0, :10]
+    nest_l = oracle.robustness(W.Or(x_pred(), W.Eventually(1, 2, x_pred())), s, mode=SMOOTH, tau=2.0)[0, :10]
+    np.testing.assert_allclose(flat_l, nest_l, rtol=1e-12)
+
+
+@pytest.mark.parametrize("name,f,D", GRAD_FORMULAS, ids=[g[0] for g in GRAD_FORMULAS])
+def test_softmax_gradients(name, f, D):
+    """FP64 central differences, and torch autograd of the masking construction."""
+    rng = np.random.default_rng(34)
+    T = 13
+    s = rng.normal(size=(1, T, D))
+    gout = rng.normal(size=(1, T))
+    g, _ = oracle.robustness_grad(f, s, gout, mode=SOFTMAX, tau=1.2, exact=True)
+    loss = lambda x: float((oracle.robustness(f, x, mode=SOFTMAX, tau=1.2, exact=True) * gout).sum())  # noqa: E731
+    np.testing.assert_allclose(g, _fd(loss, s), rtol=1e-6, atol=1e-6 * max(1.0, np.abs(g).max()))
+    xt = torch.tensor(s[0], dtype=torch.float64, requires_grad=True)
+    (mr.evaluate(f, xt, hard=None, tau=1.2) * torch.tensor(gout[0])).sum().backward()
+    np.testing.assert_allclose(g[0], xt.grad.numpy(), rtol=1e-9, atol=1e-9)
+
+
+def test_softmax_smooth_mask_gradients_fd():
+    rng = np.random.default_rng(35)
+    T = 30
+    s = rng.normal(size=(2, T, 1))
+    gout = rng.normal(size=(2, T))
+    bounds = np.array([[[3.3, 9.6]], [[0.4, 17.2]]])
+    for op in (W.EventuallySm, W.AlwaysSm):
+        f = op(30, 40, x_pred(), slot=0)
+        kw = dict(mode=SOFTMAX, tau=2.0, mask_c=1.5, mask_eps=1e-3, exact=True)
+        g, gb = oracle.robustness_grad(f, s, gout, bounds=bounds, **kw)
+        loss_b = lambda bb: float((oracle.robustness(f, s, bounds=bb, **kw) * gout).sum())  # noqa: E731
+        loss_s = lambda x: float((oracle.robustness(f, x, bounds=bounds, **kw) * gout).sum())  # noqa: E731
+        np.testing.assert_allclose(gb, _fd(loss_b, bounds), rtol=1e-6, atol=1e-7)
+        np.testing.assert_allclose(g, _fd(loss_s, s), rtol=1e-6, atol=1e-7)
