@@ -60,7 +60,9 @@ typedef enum {
   STL_ERR_DEVICE_CHECK = -6  /* the device found invalid per-trace data (bounds) */
 } stl_status;
 
-typedef enum { STL_HARD = 0, STL_SMOOTH = 1 } stl_mode;
+/* STL_SMOOTH: logsumexp min / max; STL_SOFTMAX: softmax-weighted min / max
+ * sum_i v_i e^{+-tau v_i} / sum_i e^{+-tau v_i} over each operator's multiset (Sec. III-C). */
+typedef enum { STL_HARD = 0, STL_SMOOTH = 1, STL_SOFTMAX = 2 } stl_mode;
 
 typedef enum {
   STL_OP_PRED_GT = 0,       /* mu(x) - c */
@@ -100,7 +102,7 @@ typedef struct {
 /* Per-call semantics. */
 typedef struct {
   int32_t mode;     /* stl_mode */
-  float tau;        /* smooth-mode temperature, > 0 (Sec. III-C) */
+  float tau;        /* temperature of the smooth modes, > 0 (Sec. III-C) */
   float mask_c;     /* smooth-mask sharpness c, > 0 (Eq. smooth mask) */
   float mask_eps;   /* smooth-mask tolerance epsilon, in (0, 1) */
 } stl_params;

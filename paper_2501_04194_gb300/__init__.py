@@ -4,8 +4,8 @@ PyTorch supplies device memory and streams; every step of the robustness trace a
 gradient runs in the hand-written CUDA kernels of ``libstl.so`` (sm_103a), reached through
 the C ABI in ``include/stl.h``.
 """
-from .binding import STL_HARD, STL_SMOOTH, Formula, FormulaSet, StlError, flatten, load, params  # noqa: F401
+from .binding import STL_HARD, STL_SMOOTH, STL_SOFTMAX, Formula, FormulaSet, StlError, flatten, load, params  # noqa: F401
 from .torch_api import RaggedBatch, STLRobustness, autotune, robustness, robustness_backward  # noqa: F401
 
 __all__ = ["Formula", "FormulaSet", "RaggedBatch", "STLRobustness", "robustness", "robustness_backward", "autotune", "params", "load", "StlError",
-           "STL_HARD", "STL_SMOOTH", "flatten"]
+           "STL_HARD", "STL_SMOOTH", "STL_SOFTMAX", "flatten"]

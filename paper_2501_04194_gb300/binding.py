@@ -14,7 +14,7 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libstl.so")
 
-STL_HARD, STL_SMOOTH = 0, 1
+STL_HARD, STL_SMOOTH, STL_SOFTMAX = 0, 1, 2
 OPS = {"pred>": 0, "pred<": 1, "true": 2, "not": 3, "and": 4, "or": 5, "eventually": 6, "always": 7,
        "until": 8, "eventually_sm": 9, "always_sm": 10, "norm>": 11, "norm<": 12}
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported", -3: "CUDA error", -4: "workspace too small",
@@ -154,7 +154,7 @@ def flatten(tree, D):
 
 def params(mode=STL_HARD, tau=1.0, mask_c=5.0, mask_eps=1e-3) -> StlParams:
     if isinstance(mode, str):
-        mode = {"hard": STL_HARD, "smooth": STL_SMOOTH}[mode]
+        mode = {"hard": STL_HARD, "smooth": STL_SMOOTH, "softmax": STL_SOFTMAX}[mode]
     return StlParams(int(mode), float(tau), float(mask_c), float(mask_eps))
 
 

@@ -40,6 +40,12 @@ bool is_temporal(int op) {
          op == STL_OP_EVENTUALLY_SM || op == STL_OP_ALWAYS_SM;
 }
 bool is_sm(int op) { return op == STL_OP_EVENTUALLY_SM || op == STL_OP_ALWAYS_SM; }
+bool is_window(int op) {
+  return op == STL_OP_EVENTUALLY || op == STL_OP_ALWAYS || op == STL_OP_EVENTUALLY_SM || op == STL_OP_ALWAYS_SM;
+}
+bool soft_mode(int mode) { return mode == STL_SMOOTH || mode == STL_SOFTMAX; }
+// per-thread arrays of the smooth Until backward, in units of (taps x threads)
+int until_arrays(int mode) { return mode == STL_SOFTMAX ? 3 : 2; }
 bool is_norm(int op) { return op == STL_OP_NORM_GT || op == STL_OP_NORM_LT; }
 bool is_pred(int op) { return op == STL_OP_PRED_GT || op == STL_OP_PRED_LT || is_norm(op); }
 int arity(int op) {
@@ -120,7 +126,7 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
   P.D = h->D;
   P.n_slots = h->n_slots;
   P.mode = p.mode;
-  P.tau = p.mode == STL_SMOOTH ? p.tau : 1.f;
+  P.tau = soft_mode(p.mode) ? p.tau : 1.f;
   P.inv_tau = 1.f / P.tau;
   P.mask_c = p.mask_c;
   P.mask_eps = p.mask_eps;
@@ -181,11 +187,13 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
   tile = std::max(32, round_up(tile, 32));
 
   auto padded = [](int cap) { return cap; };
-  // window scratch: run aggregates (threads + K/7) and their blocks of 8, 16 bytes each; the
-  // signal gradient reuses it for the predicate adjoint pointers
+  // window scratch: run aggregates (threads + K/7) and their blocks of 8, 16 bytes each (24
+  // for the double-precision sums of the softmax-weighted adjoint); the signal gradient reuses
+  // it for the predicate adjoint pointers
+  const int entry_words = (bwd && p.mode == STL_SOFTMAX) ? 6 : 4;
   auto scratch_for = [&](int nt) {
     const int runs = nt + maxK / 7 + 4;
-    return std::max((runs + runs / 8 + 8) * 4, 2 * STL_MAX_PRED);
+    return std::max((runs + runs / 8 + 8) * entry_words, 2 * STL_MAX_PRED);
   };
   auto layout = [&](int tl, std::vector<int> &space_out, int &smem_words, int &gwords) {
     // scratch for window run aggregates: (threads + maxK/R + 2) entries of up to 16 bytes
@@ -199,14 +207,16 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
       if (bwd) {
         // hard backward: only predicates keep an adjoint (selection walk), temporal nodes
         // keep their selected samples; smooth backward: every node keeps an adjoint
-        if (p.mode == STL_SMOOTH || is_pred(nd.op)) nrings += 1;
+        if (soft_mode(p.mode) || is_pred(nd.op)) nrings += 1;
         if (p.mode == STL_HARD && is_temporal(nd.op)) nrings += 1;
+        // softmax windows keep each output's log-normaliser for their adjoint
+        if (p.mode == STL_SOFTMAX && is_window(nd.op)) nrings += 1;
       }
       words[i] = nrings * padded(cap);
     }
     int tab_words = 0;
     for (int i = 0; i < n; ++i)
-      if (is_sm(h->nodes[i].op) && p.mode == STL_SMOOTH)
+      if (is_sm(h->nodes[i].op) && soft_mode(p.mode))
         tab_words += round_up(3LL * (window_hi(h->nodes[i], T, p) + 2), 4);
     space_out.assign(n, 0);
     smem_words = scratch_words + rt_words + tab_words;
@@ -262,15 +272,18 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
     k.adj_off = -1;
     k.aux_off = -1;
     if (bwd) {
-      if (p.mode == STL_SMOOTH || is_pred(nd.op)) { k.adj_off = off; off += pw; }
-      if (p.mode == STL_HARD && is_temporal(nd.op)) { k.aux_off = off; off += pw; }
+      if (soft_mode(p.mode) || is_pred(nd.op)) { k.adj_off = off; off += pw; }
+      if ((p.mode == STL_HARD && is_temporal(nd.op)) || (p.mode == STL_SOFTMAX && is_window(nd.op))) {
+        k.aux_off = off;
+        off += pw;
+      }
     }
     k.tab_off = -1;
     k.tab_len = 0;
   }
   // smooth-mask weight tables live in shared memory after the buffers
   for (int i = 0; i < n; ++i) {
-    if (!(is_sm(h->nodes[i].op) && p.mode == STL_SMOOTH)) continue;
+    if (!(is_sm(h->nodes[i].op) && soft_mode(p.mode))) continue;
     KNode &k = P.nd[i];
     k.tab_len = window_hi(h->nodes[i], T, p) + 2;
     k.tab_off = off_s;
@@ -301,7 +314,7 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
 
   // launch shape
   int bps = 0;
-  e = stl_blocks_per_sm(threads, bwd ? 1 : 0, p.mode == STL_SMOOTH ? 1 : 0, 0, P.smem_words * 4, &bps);
+  e = stl_blocks_per_sm(threads, bwd ? 1 : 0, soft_mode(p.mode) ? 1 : 0, 0, P.smem_words * 4, &bps);
   if (e) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (bps < 1) return fail(STL_ERR_UNSUPPORTED, "kernel does not fit on an SM (%d B shared)", P.smem_words * 4);
   const long long slots = (long long)sms * bps;
@@ -325,12 +338,13 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
   size_t ws_words = (size_t)P.gwords * pl.grid;
   P.ut_len = 0;
   P.ut_off = (long long)ws_words;
-  if (bwd && p.mode == STL_SMOOTH) {
+  if (bwd && soft_mode(p.mode)) {
     int ut = 0;
     for (int i = 0; i < n; ++i)
       if (h->nodes[i].op == STL_OP_UNTIL) ut = std::max(ut, window_hi(h->nodes[i], T, p) + 1);
     P.ut_len = ut;
-    ws_words += (size_t)2 * ut * pl.grid * threads;   // P_k and z_k per tap and thread
+    // per tap and thread: P_k and z_k (logsumexp); P_k, z_k and log S_k (softmax-weighted)
+    ws_words += (size_t)until_arrays(p.mode) * ut * pl.grid * threads;
   }
   pl.ws_bytes = ws_words * 4;
   return STL_OK;
@@ -338,9 +352,10 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
 
 stl_status check_params(const stl_program *h, const stl_params *p) {
   if (!p) return fail(STL_ERR_INVALID_ARG, "params is NULL");
-  if (p->mode != STL_HARD && p->mode != STL_SMOOTH) return fail(STL_ERR_INVALID_ARG, "mode must be STL_HARD or STL_SMOOTH");
-  if (p->mode == STL_SMOOTH && !(p->tau > 0.f && std::isfinite(p->tau)))
-    return fail(STL_ERR_INVALID_ARG, "tau must be finite and > 0 in smooth mode");
+  if (p->mode != STL_HARD && p->mode != STL_SMOOTH && p->mode != STL_SOFTMAX)
+    return fail(STL_ERR_INVALID_ARG, "mode must be STL_HARD, STL_SMOOTH or STL_SOFTMAX");
+  if (soft_mode(p->mode) && !(p->tau > 0.f && std::isfinite(p->tau)))
+    return fail(STL_ERR_INVALID_ARG, "tau must be finite and > 0 in the smooth modes");
   if (h->has_sm) {
     if (!(p->mask_c > 0.f && std::isfinite(p->mask_c))) return fail(STL_ERR_INVALID_ARG, "mask_c must be finite and > 0");
     if (!(p->mask_eps > 0.f && p->mask_eps < 1.f)) return fail(STL_ERR_INVALID_ARG, "mask_eps must be in (0, 1)");
@@ -573,7 +588,7 @@ stl_status stl_internal_plan_backward_capped(stl_handle h, const float *sig, int
   Plan pl;
   s = make_plan(h, B, T, *p, true, pl);
   if (s) return s;
-  const size_t per_cta_words = (size_t)pl.P.gwords + (size_t)2 * pl.P.ut_len * pl.threads;
+  const size_t per_cta_words = (size_t)pl.P.gwords + (size_t)until_arrays(p->mode) * pl.P.ut_len * pl.threads;
   if (per_cta_words * 4 > capacity_bytes)
     return fail(STL_ERR_WORKSPACE, "one CTA needs %zu bytes of scratch, the static scratch holds %zu",
                 per_cta_words * 4, capacity_bytes);
@@ -648,7 +663,7 @@ stl_status stl_set_prepare(stl_set_handle s, int64_t n_traces, int64_t T_max, co
   int sms = 0, bps = 0;
   int e = stl_num_sms(&sms);
   if (e) return cuda_fail(e, "cudaDeviceGetAttribute(multiprocessors)");
-  e = stl_blocks_per_sm(threads, backward ? 1 : 0, p->mode == STL_SMOOTH ? 1 : 0, 1, smem * 4, &bps);
+  e = stl_blocks_per_sm(threads, backward ? 1 : 0, soft_mode(p->mode) ? 1 : 0, 1, smem * 4, &bps);
   if (e) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (bps < 1) return fail(STL_ERR_UNSUPPORTED, "kernel does not fit on an SM (%d B shared)", smem * 4);
   const long long grid = std::max(1LL, std::min((long long)sms * bps, (long long)n_traces));
@@ -668,7 +683,7 @@ stl_status stl_set_prepare(stl_set_handle s, int64_t n_traces, int64_t T_max, co
   st.ut_len = ut_len;
   // workspace: [work counter: 256 B][global node buffers grid x gwords][smooth-until arrays]
   st.ut_off = (long long)gwords * grid;
-  st.ws_bytes = 256 + ((size_t)gwords * grid + (size_t)2 * ut_len * grid * threads) * 4;
+  st.ws_bytes = 256 + ((size_t)gwords * grid + (size_t)until_arrays(p->mode) * ut_len * grid * threads) * 4;
   st.T_max = T_max;
   st.p = *p;
   st.ready = true;

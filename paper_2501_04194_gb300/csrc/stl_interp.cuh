@@ -125,6 +125,115 @@ struct LseM {
   }
 };
 
+// softmax-weighted reduction (Sec. III-C "soft" max / min): (m, s, n) = (largest exponent
+// z = sgn tau v seen, sum e^{z - m}, sum v e^{z - m}); the value is n / s.  An entry with
+// z = +inf dominates (kept with s = 1, n = its value), z = -inf carries no weight.
+struct SW { float m, s, n; };
+struct SwM {
+  using T = SW;
+  static __device__ __forceinline__ T comb(T a, T b) {
+    if (b.m == -INFINITY || a.m == INFINITY) return a;
+    if (a.m == -INFINITY || b.m == INFINITY) return b;
+    T o;
+    if (b.m > a.m) {
+      const float f = __expf(a.m - b.m);
+      o.m = b.m; o.s = fmaf(a.s, f, b.s); o.n = fmaf(a.n, f, b.n);
+    } else {
+      const float f = __expf(b.m - a.m);
+      o.m = a.m; o.s = fmaf(b.s, f, a.s); o.n = fmaf(b.n, f, a.n);
+    }
+    return o;
+  }
+};
+__device__ __forceinline__ SW sw_elem(float v, float st) {
+  const float z = st * v;
+  SW r;
+  if (z == -INFINITY) { r.m = -INFINITY; r.s = 0.f; r.n = 0.f; }
+  else { r.m = z; r.s = 1.f; r.n = v; }
+  return r;
+}
+// value of a reduction with sign sgn (an empty one is -sgn inf); lse = log sum e^{z}
+__device__ __forceinline__ float sw_value(const SW &r, float sgn) {
+  if (r.m == INFINITY) return r.n;
+  if (r.m == -INFINITY) return -sgn * INFINITY;
+  return r.n / r.s;
+}
+__device__ __forceinline__ float sw_lse(const SW &r) {
+  return (r.m == INFINITY || r.m == -INFINITY) ? r.m : r.m + __logf(r.s);
+}
+// softmax-weighted min (sg = -1) or max (sg = +1) of two values, and the weight of the first
+__device__ __forceinline__ float sw2(float a, float b, float sg, float tau, float &wa) {
+  if (a == b) { wa = 0.5f; return a; }
+  if (sg * a == INFINITY || sg * b == -INFINITY) { wa = 1.f; return a; }
+  if (sg * b == INFINITY || sg * a == -INFINITY) { wa = 0.f; return b; }
+  wa = 1.f / (1.f + __expf(-sg * tau * (a - b)));
+  return fmaf(wa, a - b, b);
+}
+// a running softmax-weighted reduction with its sums in double (sequential, per thread)
+struct SWd {
+  float m = -INFINITY;
+  double s = 0.0, n = 0.0;
+  float inf_v = 0.f;
+  bool has_inf = false;
+  __device__ __forceinline__ void add(float v, float st) {
+    const float z = st * v;
+    if (z == -INFINITY) return;
+    if (z == INFINITY) { if (!has_inf) inf_v = v; has_inf = true; return; }
+    if (z > m) {
+      const double f = (double)__expf(m - z);
+      s = fma(s, f, 1.0);
+      n = fma(n, f, (double)v);
+      m = z;
+    } else {
+      const double e = (double)__expf(z - m);
+      s += e;
+      n = fma(e, (double)v, n);
+    }
+  }
+  __device__ __forceinline__ float value(float sgn) const {
+    if (has_inf) return inf_v;
+    if (m == -INFINITY) return -sgn * INFINITY;
+    return (float)(n / s);
+  }
+  __device__ __forceinline__ float lse() const {
+    if (has_inf) return INFINITY;
+    return m == -INFINITY ? -INFINITY : m + (float)log(s);
+  }
+};
+
+// d y / d v of a softmax-weighted reduction for an entry of weight w: w (1 + sgn tau (v - y))
+__device__ __forceinline__ float sw_grad(float w, float v, float y, float st) {
+  if (w == 0.f) return 0.f;
+  if (isinf(v) || isinf(y)) return w;
+  return w * fmaf(st, v - y, 1.f);
+}
+
+// two signed sums sharing one scale (the transposed softmax-weighted window).  The sums are
+// kept in double: the adjoint combines them as s1 + tau x s2, which cancels by about tau |y|.
+struct LS2 { float m; double s1, s2; };
+struct Lse2M {
+  using T = LS2;
+  static __device__ __forceinline__ T comb(T a, T b) {
+    if (b.m == -INFINITY) return a;
+    if (a.m == -INFINITY) return b;
+    T o;
+    if (b.m > a.m) {
+      const double f = (double)__expf(a.m - b.m);
+      o.m = b.m; o.s1 = fma(a.s1, f, b.s1); o.s2 = fma(a.s2, f, b.s2);
+    } else {
+      const double f = (double)__expf(b.m - a.m);
+      o.m = a.m; o.s1 = fma(b.s1, f, a.s1); o.s2 = fma(b.s2, f, a.s2);
+    }
+    return o;
+  }
+};
+
+// The host sizes the window scratch for entries of 16 bytes (24 in softmax-weighted backward
+// launches, the only users of LS2).
+static_assert(sizeof(VI) <= 16 && sizeof(C2) <= 16 && sizeof(CC) <= 16 && sizeof(LS) <= 16 && sizeof(SW) <= 16,
+              "window aggregates must fit the 16-byte scratch entries");
+static_assert(sizeof(LS2) <= 24, "softmax adjoint aggregates must fit the 24-byte scratch entries");
+
 // ------------------------------------------------------------------ window framework
 // middle combine of runagg[l .. r] (inclusive, in order), directly or via level-2 blocks
 template <class M>
@@ -643,6 +752,9 @@ __device__ void eval_elementwise(const Cta &C, int n, int F, int E) {
       float v;
       if constexpr (!SMOOTH) {
         v = op == OP_AND ? (a[k] <= b[k] ? a[k] : b[k]) : (a[k] >= b[k] ? a[k] : b[k]);
+      } else if (P.mode == 2) {
+        float wa;
+        v = sw2(a[k], b[k], -sg, tau, wa);
       } else {
         // two-term logsumexp min / max: min(x,y) - log1p(e^{-tau|x-y|}) / tau
         const float xs = sg * a[k], ys = sg * b[k];
@@ -685,6 +797,13 @@ __device__ void eval_smooth_window(const Cta &C, int n, int F, int E, int ia, in
   const NodeOut o = node_out(C, n);
   const float sgn = nd.op == OP_EV ? 1.f : -1.f;
   const float st = sgn * P.tau, sit = sgn * P.inv_tau;
+  if (P.mode == 2) {
+    // softmax-weighted; the log-normaliser goes to the aux ring (backward launches)
+    auto elem = [&](int j) { return sw_elem(cv.get(j), st); };
+    auto out = [&](int q, SW r) { o.put(q, sw_value(r, sgn), __float_as_int(sw_lse(r))); };
+    window_any<SwM>(ib - ia + 1, F, E, ia, ib, elem, out, C.scratch);
+    return;
+  }
   auto elem = [&](int j) { LS r; r.m = st * cv.get(j); r.s = 1.f; return r; };
   auto out = [&](int q, LS r) { o.put(q, (r.m + __logf(r.s)) * sit); };
   window_any<LseM>(ib - ia + 1, F, E, ia, ib, elem, out, C.scratch);
@@ -785,6 +904,29 @@ __device__ void eval_smooth_until(const Cta &C, int n, int F, int E, int ia, int
   }
 }
 
+// Softmax-weighted Until (R17): P_i = softmin_{k<=i} phi_{q+k}, z_i = softmin(P_i, psi_{q+i}),
+// U = softmax_{i in [a,b]} z_i, each one softmax-weighted reduction; one output per thread.
+__device__ void eval_soft_until(const Cta &C, int n, int F, int E, int ia, int ib) {
+  const KProgram &P = *C.P;
+  const KNode &nd = P.nd[n];
+  const ChildView cp = child_view(C, nd, nd.c0);
+  const ChildView cq = child_view(C, nd, nd.c1);
+  const NodeOut o = node_out(C, n);
+  const float tau = P.tau;
+  for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
+    SW pa{-INFINITY, 0.f, 0.f}, ua{-INFINITY, 0.f, 0.f};
+    for (int i = 0; i <= ib; ++i) {
+      pa = SwM::comb(pa, sw_elem(cp.get(q + i), -tau));
+      if (i >= ia) {
+        float w;
+        const float z = sw2(sw_value(pa, -1.f), cq.get(q + i), -1.f, tau, w);
+        ua = SwM::comb(ua, sw_elem(z, tau));
+      }
+    }
+    o.put(q, sw_value(ua, 1.f));
+  }
+}
+
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.f / (1.f + expf(-z)); }
 
 __device__ __forceinline__ float smask(float i, float a, float b, float c, float eps) {
@@ -804,6 +946,39 @@ __device__ void eval_smooth_mask(const Cta &C, int n, int F, int E) {
   const float *w = me.tab;
   const float sgn = nd.op == OP_EVSM ? 1.f : -1.f;
   const float st = sgn * P.tau;
+  if (P.mode == 2) {
+    // softmax-weighted with the mask as weight: sum m_i v_i e^{st v_i} / sum m_i e^{st v_i}
+    // (sums in double: the weighted mean of up to a few hundred taps of both signs)
+    for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
+      float M = -INFINITY;
+      double S = 0.0, N = 0.0;
+      float inf_v = 0.f;
+      bool has_inf = false;
+      for (int i = 0; i < len; ++i) {
+        const float m = w[i];
+        if (m <= 0.f) continue;
+        const float x = cv.get(q + ia + i), z = st * x;
+        if (z == -INFINITY) continue;
+        if (z == INFINITY) { if (!has_inf) inf_v = x; has_inf = true; continue; }
+        if (z > M) {
+          const double f = (double)__expf(M - z);
+          S = S * f + m;
+          N = N * f + (double)m * x;
+          M = z;
+        } else {
+          const double e = (double)m * (double)__expf(z - M);
+          S += e;
+          N = fma(e, (double)x, N);
+        }
+      }
+      float y, lse;
+      if (has_inf) { y = inf_v; lse = INFINITY; }
+      else if (M == -INFINITY) { y = -sgn * INFINITY; lse = -INFINITY; }
+      else { y = (float)(N / S); lse = M + (float)log(S); }
+      o.put(q, y, __float_as_int(lse));
+    }
+    return;
+  }
   for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
     float M = -INFINITY, S = 0.f;
     for (int i = 0; i < len; ++i) {
@@ -841,7 +1016,10 @@ __device__ void eval_node(const Cta &C, int n, int F, int E) {
       else if (r.ia <= r.ib) eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
       break;
     case OP_UNTIL:
-      if constexpr (SMOOTH) eval_smooth_until(C, n, F, E, r.ia, r.ib);
+      if constexpr (SMOOTH) {
+        if (P.mode == 2) eval_soft_until(C, n, F, E, r.ia, r.ib);
+        else eval_smooth_until(C, n, F, E, r.ia, r.ib);
+      }
       else eval_hard_until<BWD>(C, n, F, E, r.ia, r.ib);
       break;
   }
@@ -876,6 +1054,13 @@ __device__ __forceinline__ void accumulate_shared(float *dst, float v) {
   if ((threadIdx.x & 31) == 0 && v != 0.f) buf_add(dst, v);
 }
 
+// the same with the warp sum in double (per-thread partial sums of both signs)
+__device__ __forceinline__ void accumulate_shared_d(float *dst, double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
+  if ((threadIdx.x & 31) == 0 && v != 0.0) buf_add(dst, (float)v);
+}
+
 // ------------------------------------------------------------------ adjoint ops
 // Adjoint of node n over its complete samples [A0, A1): adds into the children.
 // [own0, own1) are the samples whose bound gradients this work item owns.
@@ -903,6 +1088,11 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
       if constexpr (!SMOOTH) {
         const bool left = op == OP_AND ? a <= b : a >= b;
         (left ? a0 : a1).add_owned(q, g);
+      } else if (P.mode == 2) {
+        float wa;
+        const float y = sw2(a, b, -sg, tau, wa);
+        a0.add_owned(q, g * sw_grad(wa, a, y, -sg * tau));
+        a1.add_owned(q, g * sw_grad(1.f - wa, b, y, -sg * tau));
       } else {
         float wx, wy;
         if (isinf(a) && isinf(b)) { wx = 1.f; wy = 0.f; }
@@ -943,6 +1133,46 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
       const float st = sgn * tau;
       const int ia = rt.ia, ib = rt.ib, len = ib - ia + 1;
       const float *w = rt.tab, *wa = rt.tab + len, *wb = rt.tab + 2 * len;
+      if (P.mode == 2) {
+        // softmax-weighted: p_{q,i} = m_i e^{st x_{q+i} - lse_q}; signal part
+        //   x̄_j += sum_i g_q p_{q,i} (1 + st (x_j - y_q)),  q = j - i,
+        // bound part d y_q / d a = sum_i (dm_i/da) e^{st x_{q+i} - lse_q} (x_{q+i} - y_q), likewise b
+        for (int j = A0 + ia + threadIdx.x; j < A1 + ib; j += NT) {
+          int src;
+          const float x = cv.get(j, src);
+          if (src < 0 || isinf(x)) continue;
+          const int ilo = max(ia, j - (A1 - 1)), ihi = min(ib, j - A0);
+          float acc = 0.f;
+          const float sx = st * x;
+          for (int i = ilo; i <= ihi; ++i) {
+            const int q = j - i;
+            const float g = me.g(q), lse = __int_as_float(me.src(q)), y = me.val(q);
+            if (g == 0.f || isinf(lse) || isinf(y)) continue;
+            acc = fmaf(g * w[i - ia] * __expf(sx - lse), fmaf(st, x - y, 1.f), acc);
+          }
+          a0.add_owned(src, acc);
+        }
+        double ga = 0.0, gbv = 0.0;   // sums of both signs over the owned samples
+        for (int q = A0 + threadIdx.x; q < A1; q += NT) {
+          if (q < own0 || q >= own1) continue;
+          const float g = me.g(q), lse = __int_as_float(me.src(q)), y = me.val(q);
+          if (g == 0.f || isinf(lse) || isinf(y)) continue;
+          double sa = 0.0, sb = 0.0;
+          for (int i = ia; i <= rt.band_a; ++i) {
+            const float x = cv.get(q + i);
+            if (!isinf(x)) sa = fma((double)(wa[i - ia] * __expf(st * x - lse)), (double)x - (double)y, sa);
+          }
+          for (int i = rt.band_b; i <= ib; ++i) {
+            const float x = cv.get(q + i);
+            if (!isinf(x)) sb = fma((double)(wb[i - ia] * __expf(st * x - lse)), (double)x - (double)y, sb);
+          }
+          ga = fma((double)g, sa, ga);
+          gbv = fma((double)g, sb, gbv);
+        }
+        accumulate_shared_d(&rt.ga, ga);
+        accumulate_shared_d(&rt.gb, gbv);
+        return;
+      }
       for (int j = A0 + ia + threadIdx.x; j < A1 + ib; j += NT) {
         int src;
         const float x = cv.get(j, src);
@@ -978,6 +1208,35 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
     const float st = (op == OP_EV ? 1.f : -1.f) * tau;
     const NodeRt &rt = C.rt[n];
     const int ia = rt.ia, ib = rt.ib;
+    if (P.mode == 2) {
+      // softmax-weighted: with lse_q the log-normaliser of output q (aux ring),
+      // x̄_j += e^{st x_j} sum_q e^{-lse_q} (g_q (1 - st y_q) + st x_j g_q)
+      auto elem2 = [&](int q) {
+        LS2 r{-INFINITY, 0.0, 0.0};
+        if (q < A0 || q >= A1) return r;
+        const float lse = __int_as_float(me.src(q)), y = me.val(q), g = me.g(q);
+        if (g == 0.f || isinf(lse) || isinf(y)) return r;
+        r.m = -lse;
+        r.s1 = (double)g * (1.0 - (double)st * (double)y);
+        r.s2 = g;
+        return r;
+      };
+      // reads past the end all land on sample T-1: their terms are summed per thread in double
+      // and added once per warp
+      double pad_acc = 0.0;
+      auto out2 = [&](int j, LS2 r) {
+        if (r.m == -INFINITY) return;
+        int src;
+        const float x = cv.get(j, src);
+        if (src < 0 || isinf(x)) return;
+        const double v = (double)__expf(st * x + r.m) * fma((double)st * (double)x, r.s2, r.s1);
+        if (j >= C.T - 1) pad_acc += v;
+        else a0.add_owned(src, (float)v);
+      };
+      window_any<Lse2M>(ib - ia + 1, A0 + ia, A1 + ib, -ib, -ia, elem2, out2, C.scratch);
+      accumulate_shared_d(a0.padadj, pad_acc);
+      return;
+    }
     auto elem = [&](int q) {
       LS r;
       if (q < A0 || q >= A1) { r.m = -INFINITY; r.s = 0.f; return r; }
@@ -1043,6 +1302,89 @@ __device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, float 
       Pnext = Pv;
     }
   }
+}
+
+// Softmax-weighted Until adjoint (R17).  Per output q: a forward pass over the taps stores
+// P_i, L_i = log sum_{k<=i} e^{-tau phi_k} and z_i (3 per-thread workspace arrays) and yields U
+// and its log-normaliser; then
+//   dU/dz_i = e^{tau z_i - lseU} (1 + tau (z_i - U)),
+//   z_i = softmin(P_i, psi_i): dz/dP = w_P (1 - tau (P_i - z_i)), dz/dpsi = w_psi (1 - tau (psi_i - z_i)),
+//   dP_i/dphi_k = e^{-tau phi_k - L_i} (1 + tau P_i - tau phi_k)   (k <= i),
+// and a backward pass over k sums c_i = g dU/dz_i dz_i/dP_i as
+//   phi_bar_k = e^{-tau phi_k - L_k} (R1_k - tau phi_k R2_k),
+//   R1_k = sum_{i>=k} c_i e^{L_k - L_i} (1 + tau P_i),  R2_k = sum_{i>=k} c_i e^{L_k - L_i},
+// whose recursions multiply by e^{L_k - L_{k+1}} <= 1 (nothing overflows).
+__device__ void adjoint_soft_until(const Cta &C, int n, int A0, int A1, float *Pk, long long pstride) {
+  const KProgram &P = *C.P;
+  const KNode &nd = P.nd[n];
+  const OwnView me = own_view(C, n);
+  const ChildView cp = child_view(C, nd, nd.c0), cq = child_view(C, nd, nd.c1);
+  const ChildAdj ap = child_adj(C, nd.c0), aq = child_adj(C, nd.c1);
+  const float tau = P.tau;
+  const int ia = C.rt[n].ia, ib = C.rt[n].ib;
+  float *Zk = Pk + (long long)P.ut_len * pstride;
+  float *Lk = Pk + 2LL * P.ut_len * pstride;
+  const int T1 = C.T - 1;
+  double pad_p = 0.0, pad_q = 0.0;   // reads at or past sample T-1, summed per thread in double
+  for (int q = A0 + threadIdx.x; q < A1; q += blockDim.x) {
+    const float g = me.g(q);
+    if (g == 0.f) continue;
+    SWd pa, ua;   // double sums: the adjoint below differentiates these reductions
+    for (int i = 0; i <= ib; ++i) {
+      pa.add(cp.get(q + i), -tau);
+      const float Pv = pa.value(-1.f);
+      Pk[i * pstride] = Pv;
+      Lk[i * pstride] = pa.lse();
+      if (i >= ia) {
+        float w;
+        const float z = sw2(Pv, cq.get(q + i), -1.f, tau, w);
+        Zk[i * pstride] = z;
+        ua.add(z, tau);
+      }
+    }
+    const float U = ua.value(1.f), lU = ua.lse();
+    if (isinf(U) || isinf(lU)) continue;
+    double R1 = 0.0, R2 = 0.0;   // combined as R1 - tau phi R2, which cancels by about tau |phi|
+    float Lnext = 0.f;
+    for (int k = ib; k >= 0; --k) {
+      const float Pv = Pk[k * pstride], L = Lk[k * pstride];
+      if (k < ib) {
+        const double f = (isinf(L) || isinf(Lnext)) ? 0.0 : (double)__expf(L - Lnext);
+        R1 *= f;
+        R2 *= f;
+      }
+      if (k >= ia) {
+        const float z = Zk[k * pstride];
+        if (!isinf(z)) {
+          const float dUz = g * __expf(tau * z - lU) * fmaf(tau, z - U, 1.f);
+          int sq;
+          const float psi = cq.get(q + k, sq);
+          float wP;
+          sw2(Pv, psi, -1.f, tau, wP);
+          if (!isinf(psi)) {
+            const float v = dUz * sw_grad(1.f - wP, psi, z, -tau);
+            if (sq == T1) pad_q += v;
+            else aq.add_atomic(sq, v);
+          }
+          if (!isinf(Pv)) {
+            const double c = (double)dUz * (double)sw_grad(wP, Pv, z, -tau);
+            R1 = fma(c, 1.0 + (double)tau * (double)Pv, R1);
+            R2 += c;
+          }
+        }
+      }
+      int sp;
+      const float phi = cp.get(q + k, sp);
+      if (!isinf(phi) && !isinf(L)) {
+        const double v = (double)__expf(-tau * phi - L) * fma(-(double)tau * (double)phi, R2, R1);
+        if (sp == T1) pad_p += v;
+        else ap.add_atomic(sp, (float)v);
+      }
+      Lnext = L;
+    }
+  }
+  accumulate_shared_d(ap.padadj, pad_p);
+  accumulate_shared_d(aq.padadj, pad_q);
 }
 
 // ------------------------------------------------------------------ per-trace geometry
@@ -1499,8 +1841,10 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? 2 : 1))
           int A1 = t1 + r.lo;
           A1 = A1 < T - 1 ? A1 : T - 1;
           if (A0 < A1) {
-            if (P.nd[n].op == OP_UNTIL)
-              adjoint_smooth_until(C, n, A0, A1, ut, ut_stride);
+            if (P.nd[n].op == OP_UNTIL) {
+              if (P.mode == 2) adjoint_soft_until(C, n, A0, A1, ut, ut_stride);
+              else adjoint_smooth_until(C, n, A0, A1, ut, ut_stride);
+            }
             else
               adjoint_node<SMOOTH>(C, n, A0, A1, s0 + r.lo, s1 + r.lo);
           }
@@ -1530,8 +1874,10 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? 2 : 1))
         // finish sample T-1 of every node, parents first (all reads go to the T-1 cells);
         // the hard walk already delivered sample T-1 of every root sample
         for (int n = P.n - 1; SMOOTH && n >= 0; --n) {
-          if (P.nd[n].op == OP_UNTIL)
-            adjoint_smooth_until(C, n, T - 1, T, ut, ut_stride);
+          if (P.nd[n].op == OP_UNTIL) {
+            if (P.mode == 2) adjoint_soft_until(C, n, T - 1, T, ut, ut_stride);
+            else adjoint_smooth_until(C, n, T - 1, T, ut, ut_stride);
+          }
           else
             adjoint_node<SMOOTH>(C, n, T - 1, T, T - 1, T);
           __syncthreads();

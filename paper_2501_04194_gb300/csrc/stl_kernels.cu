@@ -66,7 +66,7 @@ int current_device(int *dev) { return (int)cudaGetDevice(dev); }
 }  // namespace
 
 int stl_launch_main(const KProgram &P, const LaunchArgs &A) {
-  const int v = variant(A.threads, P.bwd, P.mode == 1, A.table != nullptr);
+  const int v = variant(A.threads, P.bwd, P.mode != 0, A.table != nullptr);   // smooth kernels serve both smooth modes
   if (v < 0) return (int)cudaErrorInvalidValue;
   int dev = 0;
   int e = current_device(&dev);

@@ -73,7 +73,7 @@ def check(stl, tree, sig, bounds=None, mode="hard", tau=1.0, mask_c=5.0, mask_ep
     B, T, _ = sig.shape
     gout = rng.normal(size=(B, T)).astype(np.float32) if grad else None
     rho, gs, gb = run(stl, tree, sig, bounds, mode, tau, mask_c, mask_eps, launch, gout)
-    om = oracle.HARD if mode == "hard" else oracle.SMOOTH
+    om = {"hard": oracle.HARD, "smooth": oracle.SMOOTH, "softmax": oracle.SOFTMAX}[mode]
     ref = oracle.robustness(tree, sig, bounds=bounds, mode=om, tau=tau, mask_c=mask_c, mask_eps=mask_eps)
     if mode == "hard":
         np.testing.assert_array_equal(rho, ref.astype(np.float32))
@@ -83,7 +83,7 @@ def check(stl, tree, sig, bounds=None, mode="hard", tau=1.0, mask_c=5.0, mask_ep
         gref, gbref = oracle.robustness_grad(tree, sig, gout.astype(np.float64), bounds=bounds, mode=om, tau=tau,
                                              mask_c=mask_c, mask_eps=mask_eps)
         assert per_trace_err(gs, gref) <= GRAD_TOL
-        if gbref is not None and mode == "smooth":
+        if gbref is not None and mode != "hard":
             assert per_trace_err(gb, gbref) <= GRAD_TOL
         elif gb is not None:
             assert np.all(gb == 0)
@@ -157,6 +157,34 @@ def test_random_formulas_per_trace_bounds(stl, seed, mode, tau):
     sig = W.random_walk(B, T, 3, seed=seed)
     bounds = _random_ragged_bounds(rng, B, n_slots, 60)
     check(stl, tree, sig, bounds=bounds, mode=mode, tau=tau, launch=dict(tile=256, segment=400 if seed % 3 == 0 else 0))
+
+
+# ------------------------------------------------------------------ softmax-weighted mode
+SOFT_CASES = [
+    ("config0", W.config0_formula(), 2, 100, None),
+    ("config1", W.config1_formula(), 3, 1500, dict(tile=256)),
+    ("config1_segments", W.config1_formula(), 3, 2100, dict(tile=256, segment=700)),
+    ("until_pad", W.Until(2, 40, W.gt([1, 0], 0.0), W.lt([0, 1], 0.3), pad=0.2), 2, 333, dict(tile=64)),
+    ("until_unbounded", W.Until(0, math.inf, W.gt([1, 0], -0.3), W.gt([0, 1], 0.4)), 2, 150, None),
+    ("windows_const_pad", W.And(W.Eventually(3, 60, W.gt([1, 0], 0.0), pad=-0.5), W.Always(0, 7, W.lt([0, 1], 1.0))), 2,
+     700, dict(tile=128)),
+    ("or_not", W.Or(W.Not(W.gt([1], 0.2)), W.Always(1, 30, W.gt([1], -0.5))), 1, 400, None),
+    ("table3_phi4", W.table3_formulas(D=2, I=(2, 37))[3], 2, 600, dict(tile=256)),
+]
+
+
+@pytest.mark.parametrize("name,tree,D,T,launch", SOFT_CASES, ids=[c[0] for c in SOFT_CASES])
+@pytest.mark.parametrize("tau", [1.0, 8.0])
+def test_softmax_mode(stl, name, tree, D, T, launch, tau):
+    sig = W.random_walk(4, T, D, seed=len(name))
+    check(stl, tree, sig, mode="softmax", tau=tau, launch=launch)
+
+
+@pytest.mark.parametrize("op", ["eventually_sm", "always_sm"])
+def test_softmax_smooth_mask(stl, op):
+    sig, bounds = W.config2_inputs(B=16, T=700, seed=3)
+    tree = (op, (120.0, 450.0, 0, None), W.gt([1.0], 0.8))
+    check(stl, tree, sig, bounds=bounds, mode="softmax", tau=10.0, mask_c=5.0, launch=dict(tile=256))
 
 
 # ------------------------------------------------------------------ region (norm) predicates
