@@ -178,7 +178,8 @@ def time_ms(torch, fn, steps=3, warmup=2):
 
 def side_measurements(stl, W, torch, dev, args):
     """Secondary numbers reported beside the headline (not the metric):
-    - config 1 in smooth mode (tau = 10) at T = 10000, fwd+bwd trace-steps/s;
+    - config 1 in the smooth modes (logsumexp and softmax-weighted, tau = 10) at T = 10000,
+      fwd+bwd trace-steps/s;
     - config 3: 10,000 ragged traces (T ~ U[50, 20000], D = 4, 16 formulas, hard), fwd+bwd in
       one persistent launch each, against one launch per formula over its own traces."""
     out = {}
@@ -191,6 +192,11 @@ def side_measurements(stl, W, torch, dev, args):
     ms_b = time_ms(torch, lambda: stl.robustness_backward(f, x, g, p=p))
     out["smooth_config1_T10000"] = {"value": B1 * T1 / ((ms_f + ms_b) * 1e-3), "unit": UNIT, "fwd_ms": ms_f,
                                     "bwd_ms": ms_b, "note": "smooth Until is O(b) per sample (compute-bound)"}
+    ps = stl.params("softmax", tau=10.0)
+    ms_f = time_ms(torch, lambda: stl.robustness(f, x, p=ps))
+    ms_b = time_ms(torch, lambda: stl.robustness_backward(f, x, g, p=ps))
+    out["softmax_config1_T10000"] = {"value": B1 * T1 / ((ms_f + ms_b) * 1e-3), "unit": UNIT, "fwd_ms": ms_f,
+                                     "bwd_ms": ms_b, "note": "softmax-weighted min/max, tau = 10"}
     wl = W.config3_workload()
     fs = [stl.Formula(t, D=4, n_slots=wl["n_slots"]) for t in wl["formulas"]]
     offs = torch.from_numpy(wl["offsets"])

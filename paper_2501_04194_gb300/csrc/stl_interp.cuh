@@ -195,9 +195,9 @@ struct SWd {
     if (m == -INFINITY) return -sgn * INFINITY;
     return (float)(n / s);
   }
-  __device__ __forceinline__ float lse() const {
+  __device__ __forceinline__ float lse() const {   // float log: s is a sum of terms in (0, 1]
     if (has_inf) return INFINITY;
-    return m == -INFINITY ? -INFINITY : m + (float)log(s);
+    return m == -INFINITY ? -INFINITY : m + __logf((float)s);
   }
 };
 
