@@ -25,7 +25,8 @@ _lib = None
 
 # node encoding private to the oracle (mirrors the enum in stl_oracle.c)
 _OPS = {"pred>": 0, "pred<": 1, "true": 2, "not": 3, "and": 4, "or": 5, "eventually": 6,
-        "always": 7, "until": 8, "eventually_sm": 9, "always_sm": 10, "norm>": 11, "norm<": 12}
+        "always": 7, "until": 8, "eventually_sm": 9, "always_sm": 10, "norm>": 11, "norm<": 12,
+        "until_sm": 13}
 HARD, SMOOTH, SOFTMAX = 0, 1, 2
 
 
@@ -114,10 +115,10 @@ class _Flat:
             nd.c0 = self._add(f[1])
             nd.c1 = self._add(f[2])
             nd.op = _OPS[op]
-        elif op in ("eventually", "always", "until", "eventually_sm", "always_sm"):
+        elif op in ("eventually", "always", "until", "eventually_sm", "always_sm", "until_sm"):
             a, b, slot, pad = f[1]
             nd.c0 = self._add(f[2])
-            if op == "until":
+            if op in ("until", "until_sm"):
                 nd.c1 = self._add(f[3])
             nd.op = _OPS[op]
             nd.a, nd.b = float(a), float(b)

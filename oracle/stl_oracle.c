@@ -43,7 +43,9 @@
  *       multiset becomes sum v e^{sgn tau v} / sum e^{sgn tau v} over that same multiset
  *       (windows with pads counted with multiplicity; the two operands of and/or; the three
  *       levels of the Until construction of Sec. IV-C, each reduced once, so no nesting
- *       of the window itself, Sec. IV-D); the smooth mask enters as a weight m_i on both sums.
+ *       of the window itself, Sec. IV-D); the smooth mask enters as a weight m_i on both sums;
+ *   R20 an Until over a sigmoid-masked interval weights the offsets i of its outer max by m_i
+ *       (hard: the offsets with m_i > 0), the prefix over phi starting at i = 0 as before.
  */
 #include <math.h>
 #include <pthread.h>
@@ -54,7 +56,8 @@
 
 enum {
   O_PRED_GT = 0, O_PRED_LT = 1, O_TRUE = 2, O_NOT = 3, O_AND = 4, O_OR = 5,
-  O_EV = 6, O_ALW = 7, O_UNTIL = 8, O_EV_SM = 9, O_ALW_SM = 10, O_NORM_GT = 11, O_NORM_LT = 12
+  O_EV = 6, O_ALW = 7, O_UNTIL = 8, O_EV_SM = 9, O_ALW_SM = 10, O_NORM_GT = 11, O_NORM_LT = 12,
+  O_UNTIL_SM = 13
 };
 enum { O_PAD_LAST = 0, O_PAD_CONST = 1 };
 enum { O_MAX_D = 64 };   /* largest signal dimension the oracle accepts */
@@ -220,7 +223,7 @@ static int work_init(work *wk, int n, int64_t T, int64_t wcap) {
   wk->cap = wcap;
   wk->tmp = calloc((size_t)wcap, sizeof(double));
   wk->tmp2 = calloc((size_t)wcap, sizeof(double));
-  wk->tmp3 = calloc((size_t)wcap * 2, sizeof(double));   /* two weight vectors (softmax Until) */
+  wk->tmp3 = calloc((size_t)wcap * 3, sizeof(double));   /* up to three weight vectors (Until) */
   wk->itmp = calloc((size_t)wcap, sizeof(int64_t));
   return (wk->tmp && wk->tmp2 && wk->tmp3 && wk->itmp) ? 0 : -1;
 }
@@ -399,6 +402,43 @@ static void forward_node(const octx *cx, work *wk, int k, int64_t b, const doubl
             if (sgn * wk->tmp[i] > sgn * best) best = wk->tmp[i];
           y[t] = best;
         }
+      }
+    } break;
+    case O_UNTIL_SM: {
+      /* Until over the sigmoid-masked interval (R20): the offsets i >= 0 of the outer max carry
+         the weights m_i of Eq. "smooth mask"; the prefix over phi still starts at i = 0 */
+      const double *ph = wk->val[nd->c0], *ps = wk->val[nd->c1];
+      double a, bb;
+      int64_t last = sm_range(cx, nd, b, &a, &bb), src;
+      for (int64_t t = 0; t < T; t++) {
+        int64_t n = 0;
+        double P = INFINITY, best = -INFINITY;
+        int have = 0;
+        for (int64_t i = 0; i <= last; i++) wk->tmp2[i] = rd(ph, T, t + i, nd, &src);
+        for (int64_t i = 0; i <= last; i++) {
+          if (wk->tmp2[i] < P) P = wk->tmp2[i];
+          const double m = smask((double)i, a, bb, cx->mask_c, cx->mask_eps);
+          if (m <= 0.0) continue;
+          const double q = rd(ps, T, t + i, nd, &src);
+          double z;
+          if (soft) {
+            const double v2[2] = {swm(wk->tmp2, NULL, i + 1, tau, -1.0, NULL), q};
+            z = swm(v2, NULL, 2, tau, -1.0, NULL);
+          } else if (smooth) {
+            z = smin2(-lse(wk->tmp2, NULL, i + 1, tau, -1.0), q, tau);
+          } else {
+            z = P <= q ? P : q;
+            if (!have || z > best) best = z;
+            have = 1;
+          }
+          wk->tmp[n] = z;
+          wk->tmp3[n] = m;
+          n++;
+        }
+        if (n == 0) y[t] = -INFINITY;
+        else if (soft) y[t] = swm(wk->tmp, wk->tmp3, n, tau, 1.0, NULL);
+        else if (smooth) y[t] = lse(wk->tmp, wk->tmp3, n, tau, 1.0);
+        else y[t] = best;
       }
     } break;
   }
@@ -632,6 +672,108 @@ static void backward_node(const octx *cx, work *wk, int k, int64_t b, int64_t T,
         gb[nd->slot * 2 + 1] += gbv;
       }
     } break;
+    case O_UNTIL_SM: {
+      const double *ph = wk->val[nd->c0], *ps = wk->val[nd->c1];
+      double *pha = wk->adj[nd->c0], *psa = wk->adj[nd->c1];
+      double a, bb;
+      int64_t last = sm_range(cx, nd, b, &a, &bb);
+      double ga = 0.0, gbv = 0.0;
+      const double c = cx->mask_c, eps = cx->mask_eps;
+      for (int64_t t = 0; t < T; t++) {
+        if (g[t] == 0.0) continue;
+        int64_t src;
+        for (int64_t i = 0; i <= last; i++) wk->tmp2[i] = rd(ph, T, t + i, nd, &src);
+        if (!smooth && !soft) {
+          /* R5 with the masked offsets: earliest maximising i, P wins ties, earliest argmin */
+          double P = INFINITY, best = -INFINITY;
+          int64_t Psrc = -1, bsrc = -1;
+          int bphi = 0, have = 0;
+          for (int64_t i = 0; i <= last; i++) {
+            int64_t ks;
+            const double v = rd(ph, T, t + i, nd, &ks);
+            if (v < P) { P = v; Psrc = ks; }
+            if (smask((double)i, a, bb, c, eps) <= 0.0) continue;
+            int64_t qs;
+            const double q = rd(ps, T, t + i, nd, &qs);
+            double z;
+            int zphi;
+            int64_t zs;
+            if (P <= q) { z = P; zphi = 1; zs = Psrc; } else { z = q; zphi = 0; zs = qs; }
+            if (!have || z > best) { best = z; bphi = zphi; bsrc = zs; }
+            have = 1;
+          }
+          if (bsrc >= 0) { if (bphi) pha[bsrc] += g[t]; else psa[bsrc] += g[t]; }
+          continue;
+        }
+        /* z_i, their outer weights p_i, then the chain of Until (smooth: as O_UNTIL) */
+        int64_t n = 0;
+        for (int64_t i = 0; i <= last; i++) {
+          const double m = smask((double)i, a, bb, c, eps);
+          if (m <= 0.0) continue;
+          const double q = rd(ps, T, t + i, nd, &src);
+          double z;
+          if (soft) {
+            const double v2[2] = {swm(wk->tmp2, NULL, i + 1, tau, -1.0, NULL), q};
+            z = swm(v2, NULL, 2, tau, -1.0, NULL);
+          } else {
+            z = smin2(-lse(wk->tmp2, NULL, i + 1, tau, -1.0), q, tau);
+          }
+          wk->tmp[n] = z;
+          wk->tmp3[n] = m;
+          wk->itmp[n] = i;
+          n++;
+        }
+        if (n == 0) continue;
+        double *pw = wk->tmp3 + (last + 1);   /* outer weights */
+        if (soft) swm(wk->tmp, wk->tmp3, n, tau, 1.0, pw);
+        for (int64_t r = 0; r < n; r++) {
+          const int64_t i = wk->itmp[r];
+          const double z = wk->tmp[r], m = wk->tmp3[r];
+          double dUz, dUm;
+          if (soft) {
+            dUz = swm_d(pw[r], z, y[t], tau, 1.0);
+            dUm = (pw[r] == 0.0 || isinf(z) || isinf(y[t])) ? 0.0 : pw[r] * (z - y[t]) / m;
+          } else {
+            const double e = exp(tau * (z - y[t]));
+            dUz = m * e;
+            dUm = e / tau;
+          }
+          ga += g[t] * dUm * smask_da((double)i, a, bb, c, eps);
+          gbv += g[t] * dUm * smask_db((double)i, a, bb, c, eps);
+          if (dUz == 0.0) continue;
+          int64_t qs;
+          const double q = rd(ps, T, t + i, nd, &qs);
+          double Pv, dzP, dzq;
+          if (soft) {
+            Pv = swm(wk->tmp2, NULL, i + 1, tau, -1.0, NULL);
+            double p2[2];
+            const double v2[2] = {Pv, q};
+            swm(v2, NULL, 2, tau, -1.0, p2);
+            dzP = swm_d(p2[0], Pv, z, tau, -1.0);
+            dzq = swm_d(p2[1], q, z, tau, -1.0);
+          } else {
+            Pv = -lse(wk->tmp2, NULL, i + 1, tau, -1.0);
+            dzP = isinf(Pv) ? 0.0 : sigm(tau * (q - Pv));
+            dzq = isinf(q) ? 0.0 : sigm(tau * (Pv - q));
+          }
+          if (qs >= 0) psa[qs] += g[t] * dUz * dzq;
+          if (dzP == 0.0) continue;
+          double *pin = pw + n;   /* inner weights over k <= i */
+          if (soft) swm(wk->tmp2, NULL, i + 1, tau, -1.0, pin);
+          for (int64_t kk = 0; kk <= i; kk++) {
+            int64_t ks;
+            const double v = rd(ph, T, t + kk, nd, &ks);
+            if (ks < 0 || isinf(v)) continue;
+            const double dP = soft ? swm_d(pin[kk], v, Pv, tau, -1.0) : exp(tau * (Pv - v));
+            pha[ks] += g[t] * dUz * dzP * dP;
+          }
+        }
+      }
+      if (gb && nd->slot >= 0) {
+        gb[nd->slot * 2 + 0] += ga;
+        gb[nd->slot * 2 + 1] += gbv;
+      }
+    } break;
   }
 }
 
@@ -645,7 +787,7 @@ static int64_t node_scratch(const octx *cx, int64_t b, int64_t T) {
       int64_t ia, ib;
       int_window(cx, nd, b, T, &ia, &ib);
       n = ib + 1;
-    } else if (nd->op == O_EV_SM || nd->op == O_ALW_SM) {
+    } else if (nd->op == O_EV_SM || nd->op == O_ALW_SM || nd->op == O_UNTIL_SM) {
       double a, bb;
       n = sm_range(cx, nd, b, &a, &bb) + 1;
     }

@@ -515,3 +515,51 @@ def test_softmax_smooth_mask_gradients_fd():
         loss_s = lambda x: float((oracle.robustness(f, x, bounds=bounds, **kw) * gout).sum())  # noqa: E731
         np.testing.assert_allclose(gb, _fd(loss_b, bounds), rtol=1e-6, atol=1e-7)
         np.testing.assert_allclose(g, _fd(loss_s, s), rtol=1e-6, atol=1e-7)
+
+
+# ------------------------------------------------------------------ Until over a masked interval (R20)
+def test_until_sm_sharp_mask_reduces_to_until():
+    """With a sharp mask (c = 50) and bounds (3.3, 9.6) the support is {4, ..., 9} with weights
+    1 - eps up to e^-15: hard mode equals the Until over [4, 9] exactly, logsumexp mode equals it
+    plus log(1 - eps) / tau, and the softmax-weighted mode (equal weights cancel) equals it."""
+    rng = np.random.default_rng(40)
+    s = rng.normal(size=(3, 30, 2)).astype(np.float32)
+    phi, psi = W.gt([1, 0], 0.0), W.gt([0, 1], 0.2)
+    fsm = W.UntilSm(20, 20, phi, psi, slot=0)
+    bounds = np.tile(np.array([[[3.3, 9.6]]], dtype=np.float32), (3, 1, 1))
+    fu = W.Until(4, 9, phi, psi)
+    kw = dict(mask_c=50.0, mask_eps=1e-3)
+    np.testing.assert_array_equal(oracle.robustness(fsm, s, bounds=bounds, **kw), oracle.robustness(fu, s))
+    tau = 2.0
+    got = oracle.robustness(fsm, s, bounds=bounds, mode=SMOOTH, tau=tau, **kw)
+    want = oracle.robustness(fu, s, mode=SMOOTH, tau=tau) + math.log(1 - 1e-3) / tau
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-6)
+    got = oracle.robustness(fsm, s, bounds=bounds, mode=SOFTMAX, tau=tau, **kw)
+    np.testing.assert_allclose(got, oracle.robustness(fu, s, mode=SOFTMAX, tau=tau), rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("mode", [SMOOTH, SOFTMAX])
+def test_until_sm_gradients_fd(mode):
+    rng = np.random.default_rng(41)
+    T = 24
+    s = rng.normal(size=(2, T, 2))
+    gout = rng.normal(size=(2, T))
+    bounds = np.array([[[2.3, 7.6]], [[0.4, 11.2]]])
+    f = W.UntilSm(20, 20, W.gt([1, 0], 0.0), W.gt([0, 1], 0.1), slot=0)
+    kw = dict(mode=mode, tau=1.5, mask_c=1.5, mask_eps=1e-3, exact=True)
+    g, gb = oracle.robustness_grad(f, s, gout, bounds=bounds, **kw)
+    loss_b = lambda bb: float((oracle.robustness(f, s, bounds=bb, **kw) * gout).sum())  # noqa: E731
+    loss_s = lambda x: float((oracle.robustness(f, x, bounds=bounds, **kw) * gout).sum())  # noqa: E731
+    np.testing.assert_allclose(gb, _fd(loss_b, bounds), rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(g, _fd(loss_s, s), rtol=1e-6, atol=1e-7)
+
+
+def test_until_sm_hard_gradient_is_one_hot():
+    rng = np.random.default_rng(42)
+    s = rng.normal(size=(1, 25, 2))
+    f = W.UntilSm(20, 20, W.gt([1, 0], 0.0), W.gt([0, 1], 0.1), slot=0)
+    bounds = np.array([[[2.3, 7.6]]])
+    for t in (0, 5, 24):
+        gout = np.zeros((1, 25)); gout[0, t] = 1.0
+        g, gb = oracle.robustness_grad(f, s, gout, bounds=bounds, mask_c=50.0)
+        assert np.count_nonzero(g) == 1 and np.abs(g).sum() == 1.0 and np.all(gb == 0)

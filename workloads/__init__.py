@@ -18,6 +18,7 @@ Or / Eventually / Always and the smoothed-interval operators of Sec. VI):
     ("eventually", I, f)       ("always", I, f)
     ("until", I, f, g)         f U_I g
     ("eventually_sm", I, f)    ("always_sm", I, f)     sigmoid-masked interval (Eq. smooth mask)
+    ("until_sm", I, f, g)      f U g with the sigmoid-masked interval on the outer offsets
 
 An interval ``I`` is the tuple ``(a, b, slot, pad)``:
     a, b  -- bounds in time steps (b may be ``inf`` = the whole signal);
@@ -86,6 +87,10 @@ def Until(a, b, f, g, slot=None, pad=None):
 
 def EventuallySm(a, b, f, slot=None, pad=None):
     return ("eventually_sm", interval(a, b, slot, pad), f)
+
+
+def UntilSm(a, b, f, g, slot=None, pad=None):
+    return ("until_sm", interval(a, b, slot, pad), f, g)
 
 
 def AlwaysSm(a, b, f, slot=None, pad=None):
