@@ -77,7 +77,9 @@ typedef enum {
   STL_OP_EVENTUALLY_SM = 9, /* sigmoid-masked window, real a < b */
   STL_OP_ALWAYS_SM = 10,
   STL_OP_NORM_GT = 11,      /* ||diag(s)(x - g)||_2 - r: outside a ball (Sec. VII-A regions) */
-  STL_OP_NORM_LT = 12       /* r - ||diag(s)(x - g)||_2: inside it */
+  STL_OP_NORM_LT = 12,      /* r - ||diag(s)(x - g)||_2: inside it */
+  STL_OP_UNTIL_SM = 13      /* child0 U child1 with the sigmoid-masked interval weighting the
+                               offsets of the outer max (real a < b; hard: offsets with m > 0) */
 } stl_op;
 
 typedef enum { STL_PAD_LAST = 0, STL_PAD_CONST = 1 } stl_pad;

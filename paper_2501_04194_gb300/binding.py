@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libstl.so")
 
 STL_HARD, STL_SMOOTH, STL_SOFTMAX = 0, 1, 2
 OPS = {"pred>": 0, "pred<": 1, "true": 2, "not": 3, "and": 4, "or": 5, "eventually": 6, "always": 7,
-       "until": 8, "eventually_sm": 9, "always_sm": 10, "norm>": 11, "norm<": 12}
+       "until": 8, "eventually_sm": 9, "always_sm": 10, "norm>": 11, "norm<": 12, "until_sm": 13}
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported", -3: "CUDA error", -4: "workspace too small",
           -5: "device wait timed out", -6: "device-side data check failed"}
 
@@ -130,10 +130,10 @@ def flatten(tree, D):
             nd.child0 = add(f[1])
             nd.child1 = add(f[2])
             nd.op = OPS[op]
-        elif op in ("eventually", "always", "until", "eventually_sm", "always_sm"):
+        elif op in ("eventually", "always", "until", "eventually_sm", "always_sm", "until_sm"):
             a, b, slot, pad = f[1]
             nd.child0 = add(f[2])
-            if op == "until":
+            if op in ("until", "until_sm"):
                 nd.child1 = add(f[3])
             nd.op = OPS[op]
             nd.a = float(a)

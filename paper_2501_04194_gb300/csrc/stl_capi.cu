@@ -35,11 +35,12 @@ stl_status cuda_fail(int e, const char *what) {
   return fail(STL_ERR_CUDA, "%s: %s", what, cudaGetErrorString((cudaError_t)e));
 }
 
+bool is_until(int op) { return op == STL_OP_UNTIL || op == STL_OP_UNTIL_SM; }
 bool is_temporal(int op) {
-  return op == STL_OP_EVENTUALLY || op == STL_OP_ALWAYS || op == STL_OP_UNTIL ||
+  return op == STL_OP_EVENTUALLY || op == STL_OP_ALWAYS || is_until(op) ||
          op == STL_OP_EVENTUALLY_SM || op == STL_OP_ALWAYS_SM;
 }
-bool is_sm(int op) { return op == STL_OP_EVENTUALLY_SM || op == STL_OP_ALWAYS_SM; }
+bool is_sm(int op) { return op == STL_OP_EVENTUALLY_SM || op == STL_OP_ALWAYS_SM || op == STL_OP_UNTIL_SM; }
 bool is_window(int op) {
   return op == STL_OP_EVENTUALLY || op == STL_OP_ALWAYS || op == STL_OP_EVENTUALLY_SM || op == STL_OP_ALWAYS_SM;
 }
@@ -54,7 +55,7 @@ int arity(int op) {
     case STL_OP_TRUE: return 0;
     case STL_OP_NOT: case STL_OP_EVENTUALLY: case STL_OP_ALWAYS:
     case STL_OP_EVENTUALLY_SM: case STL_OP_ALWAYS_SM: return 1;
-    case STL_OP_AND: case STL_OP_OR: case STL_OP_UNTIL: return 2;
+    case STL_OP_AND: case STL_OP_OR: case STL_OP_UNTIL: case STL_OP_UNTIL_SM: return 2;
     default: return -1;
   }
 }
@@ -145,13 +146,13 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
     if (nd.child0 >= 0) {
       const int c = nd.child0;
       if (is_temporal(nd.op)) {
-        lo[c] = lo[i] + (nd.op == STL_OP_UNTIL ? 0 : a0);
+        lo[c] = lo[i] + (is_until(nd.op) ? 0 : a0);
         hi[c] = hi[i] + b1;
       } else { lo[c] = lo[i]; hi[c] = hi[i]; }
     }
     if (nd.child1 >= 0) {
       const int c = nd.child1;
-      if (nd.op == STL_OP_UNTIL) { lo[c] = lo[i] + a0; hi[c] = hi[i] + b1; }
+      if (is_until(nd.op)) { lo[c] = lo[i] + a0; hi[c] = hi[i] + b1; }
       else { lo[c] = lo[i]; hi[c] = hi[i]; }
     }
   }
@@ -341,7 +342,7 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
   if (bwd && soft_mode(p.mode)) {
     int ut = 0;
     for (int i = 0; i < n; ++i)
-      if (h->nodes[i].op == STL_OP_UNTIL) ut = std::max(ut, window_hi(h->nodes[i], T, p) + 1);
+      if (is_until(h->nodes[i].op)) ut = std::max(ut, window_hi(h->nodes[i], T, p) + 1);
     P.ut_len = ut;
     // per tap and thread: P_k and z_k (logsumexp); P_k, z_k and log S_k (softmax-weighted)
     ws_words += (size_t)until_arrays(p.mode) * ut * pl.grid * threads;
@@ -444,7 +445,7 @@ stl_status stl_compile(const stl_node *nodes, int32_t n_nodes, const float *pred
         return fail(STL_ERR_INVALID_ARG, "node %d: pad_mode must be STL_PAD_LAST or STL_PAD_CONST", i);
       if (nd.pad_mode == STL_PAD_CONST && !std::isfinite(nd.pad_value))
         return fail(STL_ERR_INVALID_ARG, "node %d: pad_value not finite", i);
-      if (nd.op == STL_OP_UNTIL) has_until = true;
+      if (is_until(nd.op)) has_until = true;
     }
   }
   int npred = 0;

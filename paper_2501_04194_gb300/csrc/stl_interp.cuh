@@ -39,8 +39,10 @@ namespace {
 
 enum {
   OP_PGT = 0, OP_PLT = 1, OP_TRUE = 2, OP_NOT = 3, OP_AND = 4, OP_OR = 5, OP_EV = 6,
-  OP_ALW = 7, OP_UNTIL = 8, OP_EVSM = 9, OP_ALWSM = 10, OP_NGT = 11, OP_NLT = 12
+  OP_ALW = 7, OP_UNTIL = 8, OP_EVSM = 9, OP_ALWSM = 10, OP_NGT = 11, OP_NLT = 12, OP_UNTSM = 13
 };
+
+__device__ __forceinline__ bool is_until_op(int op) { return op == OP_UNTIL || op == OP_UNTSM; }
 
 __device__ __forceinline__ bool is_pred_op(int op) { return op == OP_PGT || op == OP_PLT || op == OP_NGT || op == OP_NLT; }
 
@@ -175,17 +177,17 @@ struct SWd {
   double s = 0.0, n = 0.0;
   float inf_v = 0.f;
   bool has_inf = false;
-  __device__ __forceinline__ void add(float v, float st) {
+  __device__ __forceinline__ void add(float v, float st, float w = 1.f) {   // w: weight (> 0)
     const float z = st * v;
     if (z == -INFINITY) return;
     if (z == INFINITY) { if (!has_inf) inf_v = v; has_inf = true; return; }
     if (z > m) {
       const double f = (double)__expf(m - z);
-      s = fma(s, f, 1.0);
-      n = fma(n, f, (double)v);
+      s = fma(s, f, (double)w);
+      n = fma(n, f, (double)w * (double)v);
       m = z;
     } else {
-      const double e = (double)__expf(z - m);
+      const double e = (double)w * (double)__expf(z - m);
       s += e;
       n = fma(e, (double)v, n);
     }
@@ -886,7 +888,8 @@ __device__ __forceinline__ float log_s_plus_q(const LseAcc &acc, float zq) {
   return acc.m + __logf(acc.s + __expf(zq - acc.m));
 }
 
-__device__ void eval_smooth_until(const Cta &C, int n, int F, int E, int ia, int ib) {
+// w (masked-interval Until): weight m_i of offset i is w[i - ia]; nullptr for weights 1.
+__device__ void eval_smooth_until(const Cta &C, int n, int F, int E, int ia, int ib, const float *w) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
   const ChildView cp = child_view(C, nd, nd.c0);
@@ -894,10 +897,10 @@ __device__ void eval_smooth_until(const Cta &C, int n, int F, int E, int ia, int
   const NodeOut o = node_out(C, n);
   const float tau = P.tau, itau = P.inv_tau;
   for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
-    LseAcc S, Z;   // S: sum_k e^{-tau phi_k};  Z: sum_i e^{tau z_i}
+    LseAcc S, Z;   // S: sum_k e^{-tau phi_k};  Z: sum_i m_i e^{tau z_i}
     for (int i = 0; i <= ib; ++i) {
       S.add(-tau * cp.get(q + i));
-      if (i >= ia) Z.add(-log_s_plus_q(S, -tau * cq.get(q + i)));
+      if (i >= ia) Z.add(-log_s_plus_q(S, -tau * cq.get(q + i)) + (w ? __logf(w[i - ia]) : 0.f));
     }
     const float lz = Z.log();
     o.put(q, lz == -INFINITY ? -INFINITY : lz * itau);
@@ -906,7 +909,7 @@ __device__ void eval_smooth_until(const Cta &C, int n, int F, int E, int ia, int
 
 // Softmax-weighted Until (R17): P_i = softmin_{k<=i} phi_{q+k}, z_i = softmin(P_i, psi_{q+i}),
 // U = softmax_{i in [a,b]} z_i, each one softmax-weighted reduction; one output per thread.
-__device__ void eval_soft_until(const Cta &C, int n, int F, int E, int ia, int ib) {
+__device__ void eval_soft_until(const Cta &C, int n, int F, int E, int ia, int ib, const float *w) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
   const ChildView cp = child_view(C, nd, nd.c0);
@@ -918,9 +921,11 @@ __device__ void eval_soft_until(const Cta &C, int n, int F, int E, int ia, int i
     for (int i = 0; i <= ib; ++i) {
       pa = SwM::comb(pa, sw_elem(cp.get(q + i), -tau));
       if (i >= ia) {
-        float w;
-        const float z = sw2(sw_value(pa, -1.f), cq.get(q + i), -1.f, tau, w);
-        ua = SwM::comb(ua, sw_elem(z, tau));
+        float wp;
+        const float z = sw2(sw_value(pa, -1.f), cq.get(q + i), -1.f, tau, wp);
+        SW e = sw_elem(z, tau);
+        if (w) { e.s *= w[i - ia]; e.n *= w[i - ia]; }
+        ua = SwM::comb(ua, e);
       }
     }
     o.put(q, sw_value(ua, 1.f));
@@ -1017,10 +1022,23 @@ __device__ void eval_node(const Cta &C, int n, int F, int E) {
       break;
     case OP_UNTIL:
       if constexpr (SMOOTH) {
-        if (P.mode == 2) eval_soft_until(C, n, F, E, r.ia, r.ib);
-        else eval_smooth_until(C, n, F, E, r.ia, r.ib);
+        if (P.mode == 2) eval_soft_until(C, n, F, E, r.ia, r.ib, nullptr);
+        else eval_smooth_until(C, n, F, E, r.ia, r.ib, nullptr);
       }
       else eval_hard_until<BWD>(C, n, F, E, r.ia, r.ib);
+      break;
+    case OP_UNTSM:
+      // Until over the masked interval: the support [ia, ib] of the mask; in the smooth modes
+      // its offsets carry the mask weights (an empty support gives -inf)
+      if (r.ia > r.ib) {
+        const NodeOut o = node_out(C, n);
+        for (int q = F + threadIdx.x; q < E; q += blockDim.x) o.put(q, -INFINITY, -1);
+      } else if constexpr (SMOOTH) {
+        if (P.mode == 2) eval_soft_until(C, n, F, E, r.ia, r.ib, r.tab);
+        else eval_smooth_until(C, n, F, E, r.ia, r.ib, r.tab);
+      } else {
+        eval_hard_until<BWD>(C, n, F, E, r.ia, r.ib);
+      }
       break;
   }
 }
@@ -1106,7 +1124,7 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
     }
     return;
   }
-  const bool is_until = op == OP_UNTIL;
+  const bool is_until = is_until_op(op);
   if constexpr (!SMOOTH) {
     // hard: every complete sample sends its adjoint to the recorded source
     const ChildAdj a1 = is_until ? child_adj(C, nd.c1) : a0;
@@ -1260,20 +1278,29 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
 //   dU/dphi_{q+k} = e^{tau(P_k - phi_k)} D_k,  D_k = [k>=a] e^{tau(2 z_k - U - P_k)} + e^{tau(P_{k+1}-P_k)} D_{k+1}
 // where P_k = -(1/tau) log S_k.  A forward pass over the taps stores P_k and z_k in the
 // per-thread workspace arrays (2 (b+1) floats), a backward pass runs the D recursion; every
-// exponent above is <= 0, so nothing overflows.
-__device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, float *Pk, long long pstride) {
+// exponent above is <= 0, so nothing overflows.  Masked-interval Until: the terms of offset i
+// carry the weight m_i (the node's table), and the bound gradients add
+// g m'_i e^{tau (z_i - U)} / tau over the owned samples [own0, own1).
+__device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, int own0, int own1, float *Pk,
+                                     long long pstride) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
+  NodeRt &rt = C.rt[n];
   const OwnView me = own_view(C, n);
   const ChildView cp = child_view(C, nd, nd.c0), cq = child_view(C, nd, nd.c1);
   const ChildAdj ap = child_adj(C, nd.c0), aq = child_adj(C, nd.c1);
   const float tau = P.tau, itau = P.inv_tau;
-  const int ia = C.rt[n].ia, ib = C.rt[n].ib;
+  const int ia = rt.ia, ib = rt.ib;
+  const bool masked = nd.op == OP_UNTSM;
+  const int len = ib - ia + 1;
+  const float *w = masked ? rt.tab : nullptr, *wa = masked ? rt.tab + len : nullptr, *wb = masked ? rt.tab + 2 * len : nullptr;
   float *Zk = Pk + (long long)P.ut_len * pstride;
+  double ga = 0.0, gbv = 0.0;
   for (int q = A0 + threadIdx.x; q < A1; q += blockDim.x) {
     const float g = me.g(q);
     if (g == 0.f) continue;
     const float tU = tau * me.val(q);
+    const bool own = masked && q >= own0 && q < own1;
     LseAcc S;
     for (int k = 0; k <= ib; ++k) {
       S.add(-tau * cp.get(q + k));
@@ -1284,7 +1311,13 @@ __device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, float 
         const float zq = -tau * cq.get(q + k, sq);
         const float L = log_s_plus_q(S, zq);
         Zk[k * pstride] = -L * itau;
-        if (zq != -INFINITY && L != -INFINITY) aq.add_atomic(sq, g * __expf(-L - tU + zq - L));
+        const float m = w ? w[k - ia] : 1.f;
+        if (zq != -INFINITY && L != -INFINITY) aq.add_atomic(sq, g * m * __expf(-L - tU + zq - L));
+        if (own && L != -INFINITY) {
+          const double e = (double)__expf(-L - tU) * (double)itau * (double)g;
+          ga = fma(e, (double)wa[k - ia], ga);
+          gbv = fma(e, (double)wb[k - ia], gbv);
+        }
       }
     }
     float Dn = 0.f, Pnext = 0.f;
@@ -1293,7 +1326,7 @@ __device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, float 
       float Dk = (k < ib && !isinf(Pv)) ? __expf(tau * (Pnext - Pv)) * Dn : 0.f;
       if (k >= ia && !isinf(Pv)) {
         const float tz = tau * Zk[k * pstride];
-        Dk += __expf(2.f * tz - tU - tau * Pv);
+        Dk += (w ? w[k - ia] : 1.f) * __expf(2.f * tz - tU - tau * Pv);
       }
       int sp;
       const float pv = cp.get(q + k, sp);
@@ -1301,6 +1334,10 @@ __device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, float 
       Dn = Dk;
       Pnext = Pv;
     }
+  }
+  if (masked) {
+    accumulate_shared_d(&rt.ga, ga);
+    accumulate_shared_d(&rt.gb, gbv);
   }
 }
 
@@ -1314,14 +1351,22 @@ __device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, float 
 //   phi_bar_k = e^{-tau phi_k - L_k} (R1_k - tau phi_k R2_k),
 //   R1_k = sum_{i>=k} c_i e^{L_k - L_i} (1 + tau P_i),  R2_k = sum_{i>=k} c_i e^{L_k - L_i},
 // whose recursions multiply by e^{L_k - L_{k+1}} <= 1 (nothing overflows).
-__device__ void adjoint_soft_until(const Cta &C, int n, int A0, int A1, float *Pk, long long pstride) {
+// Masked-interval Until: U = sum m_i z_i e^{tau z_i} / sum m_i e^{tau z_i}, so dU/dz_i carries
+// m_i and dU/dm_i = e^{tau z_i - lseU} (z_i - U) gives the bound gradients (owned samples).
+__device__ void adjoint_soft_until(const Cta &C, int n, int A0, int A1, int own0, int own1, float *Pk,
+                                   long long pstride) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
+  NodeRt &rt = C.rt[n];
   const OwnView me = own_view(C, n);
   const ChildView cp = child_view(C, nd, nd.c0), cq = child_view(C, nd, nd.c1);
   const ChildAdj ap = child_adj(C, nd.c0), aq = child_adj(C, nd.c1);
   const float tau = P.tau;
-  const int ia = C.rt[n].ia, ib = C.rt[n].ib;
+  const int ia = rt.ia, ib = rt.ib;
+  const bool masked = nd.op == OP_UNTSM;
+  const int len = ib - ia + 1;
+  const float *w = masked ? rt.tab : nullptr, *wa = masked ? rt.tab + len : nullptr, *wb = masked ? rt.tab + 2 * len : nullptr;
+  double ga = 0.0, gbv = 0.0;
   float *Zk = Pk + (long long)P.ut_len * pstride;
   float *Lk = Pk + 2LL * P.ut_len * pstride;
   const int T1 = C.T - 1;
@@ -1336,10 +1381,10 @@ __device__ void adjoint_soft_until(const Cta &C, int n, int A0, int A1, float *P
       Pk[i * pstride] = Pv;
       Lk[i * pstride] = pa.lse();
       if (i >= ia) {
-        float w;
-        const float z = sw2(Pv, cq.get(q + i), -1.f, tau, w);
+        float wp;
+        const float z = sw2(Pv, cq.get(q + i), -1.f, tau, wp);
         Zk[i * pstride] = z;
-        ua.add(z, tau);
+        ua.add(z, tau, w ? w[i - ia] : 1.f);
       }
     }
     const float U = ua.value(1.f), lU = ua.lse();
@@ -1355,8 +1400,13 @@ __device__ void adjoint_soft_until(const Cta &C, int n, int A0, int A1, float *P
       }
       if (k >= ia) {
         const float z = Zk[k * pstride];
+        if (!isinf(z) && masked && q >= own0 && q < own1) {
+          const double dm = (double)g * (double)__expf(tau * z - lU) * ((double)z - (double)U);
+          ga = fma(dm, (double)wa[k - ia], ga);
+          gbv = fma(dm, (double)wb[k - ia], gbv);
+        }
         if (!isinf(z)) {
-          const float dUz = g * __expf(tau * z - lU) * fmaf(tau, z - U, 1.f);
+          const float dUz = g * (w ? w[k - ia] : 1.f) * __expf(tau * z - lU) * fmaf(tau, z - U, 1.f);
           int sq;
           const float psi = cq.get(q + k, sq);
           float wP;
@@ -1385,6 +1435,10 @@ __device__ void adjoint_soft_until(const Cta &C, int n, int A0, int A1, float *P
   }
   accumulate_shared_d(ap.padadj, pad_p);
   accumulate_shared_d(aq.padadj, pad_q);
+  if (masked) {
+    accumulate_shared_d(&rt.ga, ga);
+    accumulate_shared_d(&rt.gb, gbv);
+  }
 }
 
 // ------------------------------------------------------------------ per-trace geometry
@@ -1412,7 +1466,7 @@ __device__ void setup_geometry(Cta &C, const float *bounds, float *ws_cta, char 
       }
       r.fa = a;
       r.fb = b;
-      if (nd.op == OP_EVSM || nd.op == OP_ALWSM) {
+      if (nd.op == OP_EVSM || nd.op == OP_ALWSM || nd.op == OP_UNTSM) {
         // support {i >= 0 : sigma(c(i-a)) - sigma(c(i-b)) > eps} is an interval
         const double c = P.mask_c, eps = P.mask_eps;
         const double L = log((1.0 - eps) / eps) / c;
@@ -1580,7 +1634,7 @@ __device__ void hard_walk(const Cta &C, const float *__restrict__ gout_row, int 
           }
           const int key = j >= T - 1 ? r.lastaux : r.aux[j - (C.t0 + r.lo)];
           if (key < 0) break;
-          if (op == OP_UNTIL) { n = (key & 1) ? r.c1 : r.c0; j = key >> 1; }
+          if (is_until_op(op)) { n = (key & 1) ? r.c1 : r.c0; j = key >> 1; }
           else { n = r.c0; j = key; }
         }
       }
@@ -1842,9 +1896,9 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
           int A1 = t1 + r.lo;
           A1 = A1 < T - 1 ? A1 : T - 1;
           if (A0 < A1) {
-            if (P.nd[n].op == OP_UNTIL) {
-              if (P.mode == 2) adjoint_soft_until(C, n, A0, A1, ut, ut_stride);
-              else adjoint_smooth_until(C, n, A0, A1, ut, ut_stride);
+            if (is_until_op(P.nd[n].op)) {
+              if (P.mode == 2) adjoint_soft_until(C, n, A0, A1, s0 + r.lo, s1 + r.lo, ut, ut_stride);
+              else adjoint_smooth_until(C, n, A0, A1, s0 + r.lo, s1 + r.lo, ut, ut_stride);
             }
             else
               adjoint_node<SMOOTH>(C, n, A0, A1, s0 + r.lo, s1 + r.lo);
@@ -1875,9 +1929,9 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
         // finish sample T-1 of every node, parents first (all reads go to the T-1 cells);
         // the hard walk already delivered sample T-1 of every root sample
         for (int n = P.n - 1; SMOOTH && n >= 0; --n) {
-          if (P.nd[n].op == OP_UNTIL) {
-            if (P.mode == 2) adjoint_soft_until(C, n, T - 1, T, ut, ut_stride);
-            else adjoint_smooth_until(C, n, T - 1, T, ut, ut_stride);
+          if (is_until_op(P.nd[n].op)) {
+            if (P.mode == 2) adjoint_soft_until(C, n, T - 1, T, T - 1, T, ut, ut_stride);
+            else adjoint_smooth_until(C, n, T - 1, T, T - 1, T, ut, ut_stride);
           }
           else
             adjoint_node<SMOOTH>(C, n, T - 1, T, T - 1, T);
@@ -1900,7 +1954,7 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
       if (A.gbounds && threadIdx.x == 0) {
         for (int n = 0; n < P.n; ++n) {
           const KNode &nd = P.nd[n];
-          if ((nd.op == OP_EVSM || nd.op == OP_ALWSM) && nd.slot >= 0) {
+          if ((nd.op == OP_EVSM || nd.op == OP_ALWSM || nd.op == OP_UNTSM) && nd.slot >= 0) {
             float *gb = A.gbounds + ((size_t)C.b * P.n_slots + nd.slot) * 2;
             atomicAdd(gb, C.rt[n].ga);
             atomicAdd(gb + 1, C.rt[n].gb);

@@ -187,6 +187,22 @@ def test_softmax_smooth_mask(stl, op):
     check(stl, tree, sig, bounds=bounds, mode="softmax", tau=10.0, mask_c=5.0, launch=dict(tile=256))
 
 
+# ------------------------------------------------------------------ Until over a masked interval
+@pytest.mark.parametrize("mode,tau", [("hard", 1.0), ("smooth", 4.0), ("softmax", 4.0)])
+@pytest.mark.parametrize("nested", [False, True])
+def test_until_sm(stl, mode, tau, nested):
+    rng = np.random.default_rng(50)
+    B, T = 6, 900
+    sig = W.random_walk(B, T, 2, seed=51)
+    u = W.UntilSm(60.0, 120.0, W.gt([1, 0], 0.0), W.lt([0, 1], 0.3), slot=0)
+    tree = W.Always(0, 30, u) if nested else u
+    a = rng.uniform(0.0, 50.0, size=B)
+    b = a + rng.uniform(5.0, 60.0, size=B)
+    bounds = np.stack([a, np.minimum(b, 119.0)], axis=1).astype(np.float32)[:, None, :]
+    bounds[0, 0] = [0.0, 0.6]   # a support of one or two offsets
+    check(stl, tree, sig, bounds=bounds, mode=mode, tau=tau, mask_c=2.0, launch=dict(tile=256))
+
+
 # ------------------------------------------------------------------ region (norm) predicates
 @pytest.mark.parametrize("D", [1, 2, 3, 5])
 @pytest.mark.parametrize("mode,tau", [("hard", 1.0), ("smooth", 3.0)])
