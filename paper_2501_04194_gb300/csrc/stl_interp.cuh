@@ -33,6 +33,8 @@
 #include <cmath>
 #include <cstdint>
 
+#include <type_traits>
+
 #include "stl_internal.cuh"
 
 namespace {
@@ -341,10 +343,22 @@ __device__ __forceinline__ void window_reduce(int q0, int q1, int ia, int ib, co
 
 constexpr int RUN = 7;   // thread-run length (odd)
 
+// Short hard windows (6 <= K < 2 RUN) use runs of 3: about two child reads per output instead
+// of the K of the direct loop.
+template <class M> struct ShortRuns {
+  static constexpr bool value = std::is_same<M, MaxV>::value || std::is_same<M, MinV>::value ||
+                                std::is_same<M, MaxI>::value || std::is_same<M, MinI>::value;
+};
+
 template <class M, class Elem, class Out>
 __device__ __forceinline__ void window_any(int K, int q0, int q1, int ia, int ib, const Elem &elem,
                                            const Out &out, void *scratch) {
-  (void)K;
+  if constexpr (ShortRuns<M>::value) {
+    if (K >= 6 && K < 2 * RUN) {
+      window_reduce<M, 3>(q0, q1, ia, ib, elem, out, scratch);
+      return;
+    }
+  }
   window_reduce<M, RUN>(q0, q1, ia, ib, elem, out, scratch);
 }
 

@@ -264,6 +264,19 @@ def test_ties_follow_the_oracle(stl):
         check(stl, tree, sig, launch=dict(tile=64))
 
 
+@pytest.mark.parametrize("K", [6, 7, 9, 13, 14])
+def test_short_windows_with_ties(stl, K):
+    """Windows of 6..14 samples (runs of 3 below 14) and an Until whose first window has K
+    samples, on integer signals full of ties: values bit-exact, gradients on the oracle's
+    tie-broken samples."""
+    rng = np.random.default_rng(K)
+    sig = rng.integers(-2, 3, size=(5, 700, 2)).astype(np.float32)
+    for tree in (W.Eventually(1, K, W.gt([1, 0], 0.0)), W.Always(0, K - 1, W.lt([0, 1], 0.5)),
+                 W.Until(K - 1, K + 20, W.gt([1, 0], -1.0), W.gt([0, 1], 0.0))):
+        check(stl, tree, sig, launch=dict(tile=256))
+        check(stl, tree, sig, launch=dict(tile=448, threads=64))
+
+
 def test_empty_batch(stl):
     f = stl.Formula(W.config0_formula(), D=2)
     x = torch.zeros((0, 10, 2), device="cuda")
