@@ -202,6 +202,26 @@ STL_API stl_status stl_robustness_backward_noalloc(stl_handle h, const float *si
                                                    const float *grad_out, float *grad_sig,
                                                    float *grad_bounds, void *stream);
 
+/* ---- Host buffers: copies overlapped with compute ----
+ * Forward and/or backward of B traces whose signal, bounds, grad_out and outputs live in HOST
+ * memory (page-locked for the copies to overlap), processed in chunks of `chunk` traces on
+ * three helper streams owned by the handle: while one chunk is computed, the next chunks'
+ * inputs are copied in and earlier chunks' outputs copied out.  staging: a DEVICE buffer of
+ * stl_pipeline_staging_size() bytes (three slots of signal, bounds, grad_out, outputs and
+ * workspace for one chunk).  out (may be NULL) receives rho [B, T]; with grad_out non-NULL the
+ * backward runs and grad_sig (required) / grad_bounds (may be NULL) receive the gradients.  The
+ * call orders itself after the work already queued on `stream`, and `stream` waits for all of
+ * it: the results are in host memory once `stream` reaches the call's end.  The helper streams
+ * and events are created on the first call (the only resources the library creates on a call
+ * path).  Same semantics and errors as stl_robustness / stl_robustness_backward; calls on one
+ * handle must not overlap. */
+STL_API stl_status stl_pipeline_staging_size(stl_handle h, int64_t chunk, int64_t T, const stl_params *p,
+                                             int32_t backward, size_t *bytes);
+STL_API stl_status stl_robustness_host_pipelined(stl_handle h, const float *sig, int64_t B, int64_t T,
+                                                 const float *bounds, const stl_params *p, const float *grad_out,
+                                                 float *out, float *grad_sig, float *grad_bounds, int64_t chunk,
+                                                 void *staging, size_t staging_bytes, void *stream);
+
 /* ---- Ragged batches: many traces of different lengths and formulas in one launch ----
  * Traces are packed one after another: trace i has offsets[i+1] - offsets[i] samples starting
  * at row offsets[i] of sig [sum T, D]; outputs are packed the same way.  formula_id[i] selects

@@ -214,6 +214,34 @@ class Formula:
             self._h = None
 
 
+def _pipeline_setup(lib):
+    if getattr(lib, "_pipe_ready", False):
+        return
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    lib.stl_pipeline_staging_size.argtypes = [vp, i64, i64, ctypes.POINTER(StlParams), i32, ctypes.POINTER(sz)]
+    lib.stl_pipeline_staging_size.restype = i32
+    lib.stl_robustness_host_pipelined.argtypes = [vp, vp, i64, i64, vp, ctypes.POINTER(StlParams), vp, vp, vp, vp,
+                                                  i64, vp, sz, vp]
+    lib.stl_robustness_host_pipelined.restype = i32
+    lib._pipe_ready = True
+
+
+def pipeline_staging_size(f: Formula, chunk, T, p: StlParams, backward) -> int:
+    lib = load()
+    _pipeline_setup(lib)
+    n = ctypes.c_size_t()
+    check(lib.stl_pipeline_staging_size(f.handle, chunk, T, ctypes.byref(p), int(backward), ctypes.byref(n)))
+    return int(n.value)
+
+
+def robustness_host_pipelined_raw(f: Formula, sig_ptr, B, T, bounds_ptr, p: StlParams, gout_ptr, out_ptr, gsig_ptr,
+                                  gb_ptr, chunk, staging_ptr, staging_bytes, stream):
+    lib = load()
+    _pipeline_setup(lib)
+    check(lib.stl_robustness_host_pipelined(f.handle, sig_ptr, B, T, bounds_ptr, ctypes.byref(p), gout_ptr, out_ptr,
+                                            gsig_ptr, gb_ptr, chunk, staging_ptr, staging_bytes, stream))
+
+
 def robustness_raw(f: Formula, sig_ptr, B, T, bounds_ptr, p: StlParams, out_ptr, ws_ptr, ws_bytes, stream):
     check(load().stl_robustness(f.handle, sig_ptr, B, T, bounds_ptr, ctypes.byref(p), out_ptr, ws_ptr, ws_bytes,
                                 stream))

@@ -71,6 +71,9 @@ struct stl_program {
   bool has_sm = false, has_until = false;
   stl_launch launch_dir[2]{};   // [forward, backward]: explicit or tuned launch shapes
   stl_launch launch{};          // the shape used by the planner for the current direction
+  // the pipelined host calls: their helper streams and the events that join them
+  cudaStream_t pst[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 // A group of formulas evaluated together in one ragged launch.  The device table holds one
@@ -466,7 +469,14 @@ stl_status stl_compile(const stl_node *nodes, int32_t n_nodes, const float *pred
   return STL_OK;
 }
 
-void stl_destroy(stl_handle h) { delete h; }
+void stl_destroy(stl_handle h) {
+  if (!h) return;
+  for (cudaEvent_t e : h->pev)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t q : h->pst)
+    if (q) cudaStreamDestroy(q);
+  delete h;
+}
 
 stl_status stl_set_launch(stl_handle h, const stl_launch *launch) {
   if (!h || !launch) return fail(STL_ERR_INVALID_ARG, "NULL argument");
@@ -564,6 +574,130 @@ stl_status stl_robustness_backward(stl_handle h, const float *sig, int64_t B, in
   A.stream = stream;
   int e = stl_launch_main(pl.P, A);
   if (e) return cuda_fail(e, "robustness backward kernel launch");
+  return STL_OK;
+}
+
+// ------------------------------------------------------------------ host-buffer pipeline
+namespace {
+struct Staging {   // one slot of the double-buffered device staging area
+  size_t sig, bnd, g, out, gsig, gb, ws, bytes;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr int kPipeSlots = 3;   // chunk k: copies in, kernels, copies out on slot k mod 3
+
+stl_status staging_layout(const stl_program *h, long long chunk, long long T, const stl_params &p, bool bwd,
+                          Staging &L) {
+  const size_t c = (size_t)chunk, t = (size_t)T, D = (size_t)h->D, S = (size_t)h->n_slots;
+  size_t ws = 0;
+  Plan pl;
+  stl_status e = make_plan(h, chunk, T, p, false, pl);
+  if (e) return e;
+  ws = pl.ws_bytes;
+  if (bwd) {
+    e = make_plan(h, chunk, T, p, true, pl);
+    if (e) return e;
+    ws = std::max(ws, pl.ws_bytes);
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off += align256(bytes); return o; };
+  L.sig = take(c * t * D * 4);
+  L.bnd = take(c * S * 2 * 4);
+  L.g = take(bwd ? c * t * 4 : 0);
+  L.out = take(c * t * 4);
+  L.gsig = take(bwd ? c * t * D * 4 : 0);
+  L.gb = take(bwd ? c * S * 2 * 4 : 0);
+  L.ws = take(ws);
+  L.bytes = off;
+  return STL_OK;
+}
+}  // namespace
+
+stl_status stl_pipeline_staging_size(stl_handle h, int64_t chunk, int64_t T, const stl_params *p, int32_t backward,
+                                     size_t *bytes) {
+  if (!h || !p || !bytes) return fail(STL_ERR_INVALID_ARG, "NULL argument");
+  if (chunk < 1 || T < 1 || T > (1LL << 30)) return fail(STL_ERR_INVALID_ARG, "need chunk >= 1 and T in [1, 2^30]");
+  stl_status s = check_params(h, p);
+  if (s) return s;
+  Staging L;
+  s = staging_layout(h, chunk, T, *p, backward != 0, L);
+  if (s) return s;
+  *bytes = kPipeSlots * L.bytes;
+  return STL_OK;
+}
+
+stl_status stl_robustness_host_pipelined(stl_handle h, const float *sig, int64_t B, int64_t T, const float *bounds,
+                                         const stl_params *p, const float *grad_out, float *out, float *grad_sig,
+                                         float *grad_bounds, int64_t chunk, void *staging, size_t staging_bytes,
+                                         void *stream) {
+  stl_status s = check_call(h, sig, B, T, bounds, p);
+  if (s) return s;
+  const bool bwd = grad_out != nullptr;
+  if (bwd && !grad_sig) return fail(STL_ERR_INVALID_ARG, "grad_sig is NULL");
+  if (!bwd && !out) return fail(STL_ERR_INVALID_ARG, "nothing to compute: out and grad_out are NULL");
+  if (chunk < 1) return fail(STL_ERR_INVALID_ARG, "chunk must be >= 1");
+  if (B == 0) return STL_OK;
+  chunk = std::min<int64_t>(chunk, B);
+  Staging L;
+  s = staging_layout(h, chunk, T, *p, bwd, L);
+  if (s) return s;
+  if (!staging || staging_bytes < kPipeSlots * L.bytes)
+    return fail(STL_ERR_WORKSPACE, "staging of %zu bytes needed (stl_pipeline_staging_size)", kPipeSlots * L.bytes);
+  for (int i = 0; i < kPipeSlots; ++i)
+    if (!h->pst[i] && cudaStreamCreateWithFlags(&h->pst[i], cudaStreamNonBlocking) != cudaSuccess) {
+      h->pst[i] = nullptr;
+      return fail(STL_ERR_CUDA, "cudaStreamCreate");
+    }
+  for (int i = 0; i < kPipeSlots + 1; ++i)
+    if (!h->pev[i] && cudaEventCreateWithFlags(&h->pev[i], cudaEventDisableTiming) != cudaSuccess) {
+      h->pev[i] = nullptr;
+      return fail(STL_ERR_CUDA, "cudaEventCreate");
+    }
+  cudaStream_t caller = (cudaStream_t)stream;
+  // the helper streams start after everything already queued on the caller's stream
+  if (cudaEventRecord(h->pev[kPipeSlots], caller) != cudaSuccess) return fail(STL_ERR_CUDA, "cudaEventRecord");
+  for (int i = 0; i < kPipeSlots; ++i)
+    if (cudaStreamWaitEvent(h->pst[i], h->pev[kPipeSlots], 0) != cudaSuccess) return fail(STL_ERR_CUDA, "stream join");
+  const size_t D = (size_t)h->D, S = (size_t)h->n_slots, t = (size_t)T;
+  const auto H2D = cudaMemcpyHostToDevice, D2H = cudaMemcpyDeviceToHost;
+  for (int64_t c0 = 0, k = 0; c0 < B; c0 += chunk, ++k) {
+    const int64_t n = std::min<int64_t>(chunk, B - c0);
+    const int slot = (int)(k % kPipeSlots);
+    cudaStream_t q = h->pst[slot];
+    char *base = (char *)staging + slot * L.bytes;
+    float *dsig = (float *)(base + L.sig), *dbnd = (float *)(base + L.bnd), *dg = (float *)(base + L.g);
+    float *dout = (float *)(base + L.out), *dgs = (float *)(base + L.gsig), *dgb = (float *)(base + L.gb);
+    void *dws = base + L.ws;
+    const size_t ws_bytes = L.bytes - L.ws;
+    cudaError_t ce = cudaMemcpyAsync(dsig, sig + (size_t)c0 * t * D, (size_t)n * t * D * 4, H2D, q);
+    if (ce == cudaSuccess && S && bounds)
+      ce = cudaMemcpyAsync(dbnd, bounds + (size_t)c0 * S * 2, (size_t)n * S * 2 * 4, H2D, q);
+    if (ce == cudaSuccess && bwd) ce = cudaMemcpyAsync(dg, grad_out + (size_t)c0 * t, (size_t)n * t * 4, H2D, q);
+    if (ce != cudaSuccess) return cuda_fail((int)ce, "cudaMemcpyAsync (host to device)");
+    if (out) {
+      s = stl_robustness(h, dsig, n, T, S ? dbnd : nullptr, p, dout, dws, ws_bytes, q);
+      if (s) return s;
+    }
+    if (bwd) {
+      s = stl_robustness_backward(h, dsig, n, T, S ? dbnd : nullptr, p, dg, dgs, (S && grad_bounds) ? dgb : nullptr,
+                                  dws, ws_bytes, q);
+      if (s) return s;
+    }
+    if (out) {
+      ce = cudaMemcpyAsync(out + (size_t)c0 * t, dout, (size_t)n * t * 4, D2H, q);
+      if (ce != cudaSuccess) return cuda_fail((int)ce, "cudaMemcpyAsync (device to host)");
+    }
+    if (bwd) {
+      ce = cudaMemcpyAsync(grad_sig + (size_t)c0 * t * D, dgs, (size_t)n * t * D * 4, D2H, q);
+      if (ce == cudaSuccess && S && grad_bounds)
+        ce = cudaMemcpyAsync(grad_bounds + (size_t)c0 * S * 2, dgb, (size_t)n * S * 2 * 4, D2H, q);
+      if (ce != cudaSuccess) return cuda_fail((int)ce, "cudaMemcpyAsync (device to host)");
+    }
+  }
+  // the caller's stream completes after all three pipelines
+  for (int i = 0; i < kPipeSlots; ++i)
+    if (cudaEventRecord(h->pev[i], h->pst[i]) != cudaSuccess || cudaStreamWaitEvent(caller, h->pev[i], 0) != cudaSuccess)
+      return fail(STL_ERR_CUDA, "stream join");
   return STL_OK;
 }
 

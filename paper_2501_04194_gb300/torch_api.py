@@ -7,8 +7,9 @@ from __future__ import annotations
 
 import torch
 
-from .binding import (Formula, FormulaSet, StlParams, params as make_params, robustness_backward_raw,
-                      robustness_ragged_backward_raw, robustness_ragged_raw, robustness_raw)
+from .binding import (Formula, FormulaSet, StlParams, params as make_params, pipeline_staging_size,
+                      robustness_backward_raw, robustness_host_pipelined_raw, robustness_ragged_backward_raw,
+                      robustness_ragged_raw, robustness_raw)
 
 
 def _check_sig(f: Formula, sig: torch.Tensor):
@@ -67,6 +68,29 @@ def robustness_backward(f: Formula, sig: torch.Tensor, grad_out: torch.Tensor, b
                             gsig.data_ptr(), None if gb is None else gb.data_ptr(),
                             None if ws is None else ws.data_ptr(), nws, stream)
     return gsig, gb
+
+
+class HostPipeline:
+    """Robustness (and its gradient) of traces held in page-locked host tensors, with the
+    copies overlapped with the kernels (stl_robustness_host_pipelined): chunks of ``chunk``
+    traces rotate over three streams.  The device staging area is allocated once."""
+
+    def __init__(self, f: Formula, T: int, p: StlParams | None = None, chunk: int = 64, backward: bool = True,
+                 device="cuda"):
+        self.f, self.T, self.p, self.chunk = f, T, p or make_params(), chunk
+        self.dev = torch.device(device)
+        self.nbytes = pipeline_staging_size(f, chunk, T, self.p, backward)
+        self.staging = torch.empty(self.nbytes // 4 + 1, dtype=torch.float32, device=self.dev)
+
+    def __call__(self, sig, grad_out=None, bounds=None, out=None, grad_sig=None, grad_bounds=None):
+        """sig [B, T, D], grad_out [B, T] (optional) and the outputs are pinned CPU tensors;
+        returns (out, grad_sig, grad_bounds), filled once the current stream reaches the end."""
+        B = sig.shape[0]
+        ptr = lambda t: None if t is None else t.data_ptr()  # noqa: E731
+        robustness_host_pipelined_raw(self.f, sig.data_ptr(), B, self.T, ptr(bounds), self.p, ptr(grad_out), ptr(out),
+                                      ptr(grad_sig), ptr(grad_bounds), self.chunk, self.staging.data_ptr(),
+                                      self.nbytes, torch.cuda.current_stream(self.dev).cuda_stream)
+        return out, grad_sig, grad_bounds
 
 
 def autotune(f: Formula, sig: torch.Tensor, bounds=None, p: StlParams | None = None, backward=False,
