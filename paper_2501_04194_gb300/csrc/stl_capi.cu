@@ -190,7 +190,10 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
   tile = std::min(tile, round_up(T, 32));
   tile = std::max(32, round_up(tile, 32));
 
-  auto padded = [](int cap) { return cap; };
+  // every buffer is allocated with STL_BUF_FRONT words before and STL_BUF_BACK words after
+  // its live range: the hard-mode window passes read a few samples past the range without
+  // clamping (those reads feed no output)
+  auto padded = [](int cap) { return cap + STL_BUF_FRONT + STL_BUF_BACK; };
   // window scratch: run aggregates (threads + K/7) and their blocks of 8, 16 bytes each (24
   // for the double-precision sums of the softmax-weighted adjoint); the signal gradient reuses
   // it for the predicate adjoint pointers
@@ -272,13 +275,13 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
     k.space = space[i];
     int &off = space[i] ? off_g : off_s;
     const int pw = padded(k.cap);
-    k.val_off = off; off += pw;
+    k.val_off = off + STL_BUF_FRONT; off += pw;
     k.adj_off = -1;
     k.aux_off = -1;
     if (bwd) {
-      if (soft_mode(p.mode) || is_pred(nd.op)) { k.adj_off = off; off += pw; }
+      if (soft_mode(p.mode) || is_pred(nd.op)) { k.adj_off = off + STL_BUF_FRONT; off += pw; }
       if ((p.mode == STL_HARD && is_temporal(nd.op)) || (p.mode == STL_SOFTMAX && is_window(nd.op))) {
-        k.aux_off = off;
+        k.aux_off = off + STL_BUF_FRONT;
         off += pw;
       }
     }

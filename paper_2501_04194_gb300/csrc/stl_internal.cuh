@@ -9,6 +9,8 @@
 #define STL_MAX_WEIGHTS 256
 #define STL_MAX_D 16
 #define STL_MAX_PRED 32
+#define STL_BUF_FRONT 4    // words allocated before every node buffer
+#define STL_BUF_BACK 32    // words allocated after every node buffer (unclamped over-reads)
 
 // Node layout after compilation (per launch: the ring geometry depends on tile and bounds).
 struct KNode {

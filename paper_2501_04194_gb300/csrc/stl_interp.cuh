@@ -880,6 +880,260 @@ __device__ void eval_hard_until(const Cta &C, int n, int F, int E, int ia, int i
   }
 }
 
+// ------------------------------------------------------------------ lean hard forward passes
+// Forward launches in hard mode evaluate windows, Until and the elementwise operators with
+// direct reads of their children's buffers: no clamping and no end-of-trace test per read.
+// This is exact because
+//  (1) a child computes every sample below its frontier min(t1 + hi, T), and a live output
+//      of the parent reads only samples below that frontier or at or after T;
+//  (2) before a temporal parent runs in a step where the child's frontier has reached T,
+//      the child's samples from T on are filled with the parent's pad (the value at T-1, or
+//      the constant), which is what a read past the end returns (padded unroll, Sec. IV-B);
+//  (3) window passes may read up to R - 1 samples past a child's live range (the buffers are
+//      allocated with that slack); such reads feed only outputs that are discarded.
+// Long windows use runs of 15 samples per thread (fewer run aggregates per output).
+
+__device__ __forceinline__ bool is_temporal_op(int op) {
+  return op == OP_EV || op == OP_ALW || op == OP_EVSM || op == OP_ALWSM || op == OP_UNTIL || op == OP_UNTSM;
+}
+
+// Fill the pad samples of node n's children whose frontier has reached T; returns whether
+// anything was written (the same on every thread), so that the caller can synchronise.
+__device__ bool pad_fill(const Cta &C, int n) {
+  const KNode &nd = C.P->nd[n];
+  const int T = C.T;
+  bool any = false;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int c = s == 0 ? nd.c0 : nd.c1;
+    if (c < 0 || frontier(C, c) < T) continue;
+    const NodeRt &r = C.rt[c];
+    const int start = C.t0 + r.lo;
+    const int f0 = max(T - start, 0), f1 = r.cap + STL_BUF_BACK;
+    const float v = nd.pad_const ? nd.pad_value : r.lastval;
+    for (int i = f0 + threadIdx.x; i < f1; i += blockDim.x) r.val[i] = v;
+    any = any || f0 < f1;
+  }
+  return any;
+}
+
+// Windowed reduction over direct child reads (the decomposition of window_reduce); threads
+// whose runs no output uses read nothing, so that every read stays within the slack.
+template <class M, int R, class Elem, class Out>
+__device__ __forceinline__ void hwin(int q0, int q1, int ia, int ib, const Elem &elem, const Out &out,
+                                     void *scratch) {
+  using T = typename M::T;
+  const int K = ib - ia + 1;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  if (q1 <= q0) return;
+  if (K < 2 * R) {
+    for (int q = q0 + tid; q < q1; q += NT) {
+      T acc = elem(q + ia);
+      for (int i = ia + 1; i <= ib; ++i) acc = M::comb(acc, elem(q + i));
+      out(q, acc);
+    }
+    return;
+  }
+  T *runagg = reinterpret_cast<T *>(scratch);
+  const int nf = K / R - 1;           // whole runs strictly inside every window (>= 1)
+  const int rho = K - (nf + 1) * R;   // lead of the trailing prefix
+  const bool two = nf >= 3 * L2B;
+  for (int p0 = q0; p0 < q1; p0 += NT * R) {
+    const int u = p0 + tid * R;
+    const int nv = min(NT, (q1 - p0 + R - 1) / R);   // threads that own outputs in this pass
+    const int nr = nv + nf;                          // run aggregates the outputs use
+    const int nruns = max(NT, nr);
+    T *agg2 = runagg + nruns;
+    T hv[R];
+    if (tid < nr) {
+      hv[R - 1] = elem(u + ia + R - 1);
+#pragma unroll
+      for (int k = R - 2; k >= 0; --k) hv[k] = M::comb(elem(u + ia + k), hv[k + 1]);
+      runagg[tid] = hv[0];
+    }
+    for (int e = NT + tid; e < nr; e += NT) {
+      const int s = p0 + ia + e * R;
+      T acc = elem(s);
+#pragma unroll
+      for (int k = 1; k < R; ++k) acc = M::comb(acc, elem(s + k));
+      runagg[e] = acc;
+    }
+    __syncthreads();
+    if (two) {
+      const int nb = nr / L2B;
+      for (int m = tid; m < nb; m += NT) {
+        T acc = runagg[m * L2B];
+#pragma unroll
+        for (int k = 1; k < L2B; ++k) acc = M::comb(acc, runagg[m * L2B + k]);
+        agg2[m] = acc;
+      }
+      __syncthreads();
+    }
+    if (tid < nv) {
+      const T mid = middle<M>(runagg, agg2, tid + 1, tid + nf, two);
+      const int gs = u + ia + (nf + 1) * R;
+      T acc = mid;
+      bool have = rho > 0;
+      if (have) {
+        acc = elem(gs);
+        for (int e = 1; e < rho; ++e) acc = M::comb(acc, elem(gs + e));
+      }
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        if (u + k < q1) {
+          T r = M::comb(hv[k], mid);
+          if (have) r = M::comb(r, acc);
+          out(u + k, r);
+        }
+        if (k + 1 < R) {
+          T e = elem(gs + rho + k);
+          acc = have ? M::comb(acc, e) : e;
+          have = true;
+        }
+      }
+    }
+    if (p0 + NT * R < q1) __syncthreads();   // the caller synchronises after the last pass
+  }
+}
+
+// runs of 15 for long windows, 7 and 3 for shorter ones, a direct loop below 6
+template <class M, class Elem, class Out>
+__device__ __forceinline__ void hwin_any(int q0, int q1, int ia, int ib, const Elem &elem, const Out &out,
+                                         void *scratch) {
+  const int K = ib - ia + 1;
+  if (K >= 30) hwin<M, 15>(q0, q1, ia, ib, elem, out, scratch);
+  else if (K >= 14) hwin<M, 7>(q0, q1, ia, ib, elem, out, scratch);
+  else hwin<M, 3>(q0, q1, ia, ib, elem, out, scratch);
+}
+
+// What a lean pass needs, passed by value: the passes are separate (not inlined) functions,
+// so that each gets its own register allocation (measured faster than inlining them).
+struct Lean {
+  NodeRt *rt;          // per-node runtime table
+  void *scratch;       // window scratch
+  float *out_row;      // root output row
+  int n, c0, c1, op;
+  int t0, T, root;
+};
+__device__ __forceinline__ Lean lean_args(const Cta &C, int n) {
+  const KNode &nd = C.P->nd[n];
+  Lean L;
+  L.rt = C.rt;
+  L.scratch = C.scratch;
+  L.out_row = C.out_row;
+  L.n = n;
+  L.c0 = nd.c0;
+  L.c1 = nd.c1;
+  L.op = nd.op;
+  L.t0 = C.t0;
+  L.T = C.T;
+  L.root = C.root;
+  return L;
+}
+
+struct RawRead {       // child sample j, read directly (pad-filled past T-1)
+  const float *p;
+  int start;
+  __device__ __forceinline__ float operator()(int j) const { return p[j - start]; }
+};
+__device__ __forceinline__ RawRead raw_read(const Lean &L, int c) {
+  RawRead r;
+  r.p = L.rt[c].val;
+  r.start = L.t0 + L.rt[c].lo;
+  return r;
+}
+
+// writer of a node's hard outputs into its own buffer (a temporal root is copied out to
+// the output row by the step loop)
+struct HardOut {
+  float *v;
+  NodeRt *rt;
+  int start, T;
+  __device__ __forceinline__ void put(int q, float val) const {
+    v[q - start] = val;
+    if (q == T - 1) rt->lastval = val;
+  }
+};
+__device__ __forceinline__ HardOut hard_out(const Lean &L) {
+  NodeRt &r = L.rt[L.n];
+  HardOut o;
+  o.v = r.val;
+  o.rt = &r;
+  o.start = L.t0 + r.lo;
+  o.T = L.T;
+  return o;
+}
+
+__device__ __noinline__ void lean_hard_window(const Lean L, int F, int E, int ia, int ib) {
+  const RawRead x = raw_read(L, L.c0);
+  const HardOut o = hard_out(L);
+  auto out = [&](int q, float r) { o.put(q, r); };
+  if (L.op == OP_EV || L.op == OP_EVSM) hwin_any<MaxV>(F, E, ia, ib, x, out, L.scratch);
+  else hwin_any<MinV>(F, E, ia, ib, x, out, L.scratch);
+}
+
+// hard Until: pass 1 stores A_q = min_{k in [0,a]} phi_{q+k}, pass 2 composes the clamps over
+// [a, b] and keeps min(A_q, V_{q+a})
+__device__ __noinline__ void lean_hard_until(const Lean L, int F, int E, int ia, int ib) {
+  const RawRead xp = raw_read(L, L.c0);
+  const RawRead xq = raw_read(L, L.c1);
+  const HardOut o = hard_out(L);
+  {
+    auto out = [&](int q, float r) { o.put(q, r); };
+    hwin_any<MinV>(F, E, 0, ia, xp, out, L.scratch);
+  }
+  __syncthreads();
+  auto elem = [&](int j) {
+    C2 r;
+    const float p = xp(j), q = xq(j);
+    r.c = fminf(p, q);
+    r.d = p;
+    return r;
+  };
+  auto out = [&](int q, C2 r) {
+    const float A = o.v[q - o.start];
+    if (!(A <= r.c)) o.put(q, r.c);
+  };
+  hwin_any<ClampV>(F, E, ia, ib, elem, out, L.scratch);
+}
+
+// hard not / and / or over direct reads (a node reads its children at its own samples, all
+// below T); the root writes the output row as it goes (consecutive threads, consecutive
+// samples)
+__device__ __noinline__ void lean_hard_elementwise(const Lean L, int F, int E) {
+  const int op = L.op;
+  const int NT = blockDim.x;
+  NodeRt &r = L.rt[L.n];
+  float *ov = r.val;
+  const int ost = L.t0 + r.lo;
+  float *orow = (L.n == L.root) ? L.out_row : nullptr;
+  const int T = L.T;
+  const RawRead x = raw_read(L, L.c0);
+  const RawRead y = raw_read(L, op == OP_NOT ? L.c0 : L.c1);
+  float last = 0.f;
+  bool has_last = false;
+  for (int base = F + threadIdx.x; base < E; base += NT * BATCH) {
+    float a[BATCH], b[BATCH];
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const int q = base + k * NT;
+      a[k] = q < E ? x(q) : 0.f;
+      b[k] = q < E ? y(q) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < BATCH; ++k) {
+      const int q = base + k * NT;
+      if (q >= E) continue;
+      const float v = op == OP_NOT ? -a[k] : op == OP_AND ? (a[k] <= b[k] ? a[k] : b[k])
+                                                         : (a[k] >= b[k] ? a[k] : b[k]);
+      ov[q - ost] = v;
+      if (orow) orow[q] = v;
+      if (q == T - 1) { last = v; has_last = true; }
+    }
+  }
+  if (has_last) r.lastval = last;
+}
+
 // Smooth Until (nested logsumexp of Sec. IV-C with the smooth min/max of Sec. III-C; the
 // nesting flattens, Sec. IV-D):  U = (1/tau) log sum_{i in [a,b]} 1/(S_i + Q_i) with
 // S_i = sum_{k<=i} e^{-tau phi_k}, Q_i = e^{-tau psi_i}.  Computed in the log domain with running
@@ -1020,26 +1274,33 @@ __device__ void eval_node(const Cta &C, int n, int F, int E) {
     case OP_PLT: eval_pred(C, n, F, E); break;
     case OP_NGT:
     case OP_NLT: eval_norm(C, n, F, E); break;
-    case OP_TRUE:
+    case OP_TRUE: eval_elementwise<SMOOTH>(C, n, F, E); break;
     case OP_NOT:
     case OP_AND:
-    case OP_OR: eval_elementwise<SMOOTH>(C, n, F, E); break;
+    case OP_OR:
+      if constexpr (SMOOTH || BWD) eval_elementwise<SMOOTH>(C, n, F, E);
+      else lean_hard_elementwise(lean_args(C, n), F, E);
+      break;
     case OP_EV:
     case OP_ALW:
       if constexpr (SMOOTH) eval_smooth_window(C, n, F, E, r.ia, r.ib);
-      else eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
+      else if constexpr (BWD) eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
+      else lean_hard_window(lean_args(C, n), F, E, r.ia, r.ib);
       break;
     case OP_EVSM:
     case OP_ALWSM:
       if constexpr (SMOOTH) eval_smooth_mask(C, n, F, E);
-      else if (r.ia <= r.ib) eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
+      else if (r.ia > r.ib) break;
+      else if constexpr (BWD) eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
+      else lean_hard_window(lean_args(C, n), F, E, r.ia, r.ib);
       break;
     case OP_UNTIL:
       if constexpr (SMOOTH) {
         if (P.mode == 2) eval_soft_until(C, n, F, E, r.ia, r.ib, nullptr);
         else eval_smooth_until(C, n, F, E, r.ia, r.ib, nullptr);
       }
-      else eval_hard_until<BWD>(C, n, F, E, r.ia, r.ib);
+      else if constexpr (BWD) eval_hard_until<BWD>(C, n, F, E, r.ia, r.ib);
+      else lean_hard_until(lean_args(C, n), F, E, r.ia, r.ib);
       break;
     case OP_UNTSM:
       // Until over the masked interval: the support [ia, ib] of the mask; in the smooth modes
@@ -1050,8 +1311,10 @@ __device__ void eval_node(const Cta &C, int n, int F, int E) {
       } else if constexpr (SMOOTH) {
         if (P.mode == 2) eval_soft_until(C, n, F, E, r.ia, r.ib, r.tab);
         else eval_smooth_until(C, n, F, E, r.ia, r.ib, r.tab);
-      } else {
+      } else if constexpr (BWD) {
         eval_hard_until<BWD>(C, n, F, E, r.ia, r.ib);
+      } else {
+        lean_hard_until(lean_args(C, n), F, E, r.ia, r.ib);
       }
       break;
   }
@@ -1883,8 +2146,21 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
         const int F0 = (t0 == R0) ? R0 + r.lo : t0 + r.hi;
         const int F = F0 < T ? F0 : T;
         const int E = frontier(C, n);
-        if (F < E) eval_node<BWD, SMOOTH>(C, n, F, E);
+        constexpr bool lean = !BWD && !SMOOTH;
+        const bool temporal = lean && is_temporal_op(P.nd[n].op);
+        if (F < E) {
+          // lean passes: the children's samples past the end hold the pad before a temporal
+          // node reads them
+          if (temporal && pad_fill(C, n)) __syncthreads();
+          eval_node<BWD, SMOOTH>(C, n, F, E);
+        }
         __syncthreads();
+        if (temporal && n == C.root) {
+          // a temporal root keeps its outputs in its buffer: copy them out coalesced
+          const float *rv = r.val;
+          const int st = t0 + r.lo;
+          for (int q = F + threadIdx.x; q < E; q += NT) C.out_row[q] = rv[q - st];
+        }
       }
       if constexpr (BWD && !SMOOTH) {
         hard_walk(C, A.gout + C.row0, t0, t1);
