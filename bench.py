@@ -451,6 +451,32 @@ def main():
     ms_step = ms_total / args.steps
     value = world * B * T / (ms_step * 1e-3)
 
+    # robustness and gradient in one launch (stl_robustness_and_backward): the backward kernel
+    # recomputes rho anyway, so for a loss linear in rho (this workload's sum(g * rho)) the
+    # forward launch can be folded into it; reported beside the two-launch headline
+    from paper_2501_04194_gb300.binding import robustness_and_backward_raw
+
+    def fused_step():
+        robustness_and_backward_raw(f, x.data_ptr(), B, T, None, p, g.data_ptr(), rho.data_ptr(), gsig.data_ptr(),
+                                    None, wsb.data_ptr(), ws_b, stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        fused_step()
+    torch.cuda.synchronize(dev)
+    a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a_.record(stream)
+    for _ in range(args.steps):
+        fused_step()
+    b_.record(stream)
+    torch.cuda.synchronize(dev)
+    fused_ms = a_.elapsed_time(b_) / args.steps
+    if world > 1:
+        t = torch.tensor([fused_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        fused_ms = float(t.item())
+    fused = {"value": world * B * T / (fused_ms * 1e-3), "unit": UNIT, "ms_per_step": fused_ms,
+             "note": "rho and the gradient of sum(g * rho) in one launch (stl_robustness_and_backward)"}
+
     # end to end through the public API with host buffers (pinned), copies inside the timed
     # region: the host pipeline overlaps the copies of one chunk of traces with the kernels of
     # the next (stl_robustness_host_pipelined)
@@ -516,7 +542,7 @@ def main():
                        "tau": args.tau if args.mode == "smooth" else None,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
-            "clocks": ck, "launch": tuned, "side": extra}
+            "clocks": ck, "launch": tuned, "fused_fwd_bwd": fused, "side": extra}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

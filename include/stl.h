@@ -179,6 +179,23 @@ STL_API stl_status stl_robustness_backward(stl_handle h, const float *sig, int64
                                    const float *grad_out, float *grad_sig, float *grad_bounds,
                                    void *workspace, size_t workspace_bytes, void *stream);
 
+/* Robustness traces and their gradient in ONE launch: rho as stl_robustness (Sec. III-D,
+ * the robustness trace) and the gradient of sum grad_out * rho as stl_robustness_backward.
+ * The backward pass recomputes every node's trace on chip anyway, so rho costs only its
+ * stores.  For callers that know the upstream gradient before the forward values (a loss
+ * linear in rho, or a fixed weighting of the trace); a loss that depends on rho itself needs
+ * the two separate calls.
+ *   out          [B, T] float32 device, overwritten (NULL is rejected)
+ *   other arguments, workspace (stl_workspace_size with backward = 1) and errors as
+ *   stl_robustness_backward.  Hard-mode rho equals stl_robustness's bit for bit; smooth-mode
+ *   rho may differ from it in the last bits when the two launches use different tiles (the
+ *   window sums are then combined in a different order). */
+STL_API stl_status stl_robustness_and_backward(stl_handle h, const float *sig, int64_t B, int64_t T,
+                                               const float *bounds, const stl_params *p,
+                                               const float *grad_out, float *out, float *grad_sig,
+                                               float *grad_bounds, void *workspace,
+                                               size_t workspace_bytes, void *stream);
+
 /* Bytes of the static device scratch behind stl_robustness_backward_noalloc (32 MiB). */
 #define STL_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 

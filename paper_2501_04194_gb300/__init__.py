@@ -5,7 +5,8 @@ gradient runs in the hand-written CUDA kernels of ``libstl.so`` (sm_103a), reach
 the C ABI in ``include/stl.h``.
 """
 from .binding import STL_HARD, STL_SMOOTH, STL_SOFTMAX, Formula, FormulaSet, StlError, flatten, load, params  # noqa: F401
-from .torch_api import HostPipeline, RaggedBatch, STLRobustness, autotune, robustness, robustness_backward  # noqa: F401
+from .torch_api import (HostPipeline, RaggedBatch, STLRobustness, autotune, robustness,  # noqa: F401
+                        robustness_and_grad, robustness_backward)
 
-__all__ = ["Formula", "FormulaSet", "HostPipeline", "RaggedBatch", "STLRobustness", "robustness", "robustness_backward", "autotune", "params", "load", "StlError",
+__all__ = ["Formula", "FormulaSet", "HostPipeline", "RaggedBatch", "STLRobustness", "robustness", "robustness_backward", "robustness_and_grad", "autotune", "params", "load", "StlError",
            "STL_HARD", "STL_SMOOTH", "STL_SOFTMAX", "flatten"]

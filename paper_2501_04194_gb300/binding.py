@@ -70,13 +70,15 @@ def load(path: str = LIB_PATH):
     lib.stl_robustness.argtypes = [vp, vp, i64, i64, vp, ctypes.POINTER(StlParams), vp, vp, sz, vp]
     lib.stl_robustness_backward.argtypes = [vp, vp, i64, i64, vp, ctypes.POINTER(StlParams), vp, vp, vp, vp,
                                             sz, vp]
+    lib.stl_robustness_and_backward.argtypes = [vp, vp, i64, i64, vp, ctypes.POINTER(StlParams), vp, vp, vp,
+                                                vp, vp, sz, vp]
     lib.stl_get_device_status.argtypes = [vp, ctypes.POINTER(i32)]
     lib.stl_status_string.argtypes = [i32]
     lib.stl_status_string.restype = ctypes.c_char_p
     lib.stl_last_error.restype = ctypes.c_char_p
     lib.stl_version.restype = ctypes.c_char_p
     for name in ("stl_compile", "stl_set_launch", "stl_get_launch", "stl_workspace_size", "stl_robustness",
-                 "stl_robustness_backward", "stl_get_device_status"):
+                 "stl_robustness_backward", "stl_robustness_and_backward", "stl_get_device_status"):
         getattr(lib, name).restype = ctypes.c_int32
     _lib = lib
     return lib
@@ -251,6 +253,12 @@ def robustness_backward_raw(f: Formula, sig_ptr, B, T, bounds_ptr, p: StlParams,
                             ws_ptr, ws_bytes, stream):
     check(load().stl_robustness_backward(f.handle, sig_ptr, B, T, bounds_ptr, ctypes.byref(p), gout_ptr,
                                          gsig_ptr, gb_ptr, ws_ptr, ws_bytes, stream))
+
+
+def robustness_and_backward_raw(f: Formula, sig_ptr, B, T, bounds_ptr, p: StlParams, gout_ptr, out_ptr, gsig_ptr,
+                                gb_ptr, ws_ptr, ws_bytes, stream):
+    check(load().stl_robustness_and_backward(f.handle, sig_ptr, B, T, bounds_ptr, ctypes.byref(p), gout_ptr,
+                                             out_ptr, gsig_ptr, gb_ptr, ws_ptr, ws_bytes, stream))
 
 
 def robustness_backward_noalloc_raw(f: Formula, sig_ptr, B, T, bounds_ptr, p: StlParams, gout_ptr, gsig_ptr,

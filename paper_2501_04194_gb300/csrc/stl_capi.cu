@@ -547,9 +547,12 @@ stl_status stl_robustness(stl_handle h, const float *sig, int64_t B, int64_t T, 
   return STL_OK;
 }
 
-stl_status stl_robustness_backward(stl_handle h, const float *sig, int64_t B, int64_t T, const float *bounds,
-                                   const stl_params *p, const float *grad_out, float *grad_sig,
-                                   float *grad_bounds, void *workspace, size_t workspace_bytes, void *stream) {
+namespace {
+// backward launch; with out non-NULL the same launch also writes rho (every node's trace is
+// recomputed by the backward anyway, so rho costs only its stores)
+stl_status backward_launch(stl_handle h, const float *sig, int64_t B, int64_t T, const float *bounds,
+                           const stl_params *p, const float *grad_out, float *out, float *grad_sig,
+                           float *grad_bounds, void *workspace, size_t workspace_bytes, void *stream) {
   stl_status s = check_call(h, sig, B, T, bounds, p);
   if (s) return s;
   if (B > 0 && (!grad_out || !grad_sig)) return fail(STL_ERR_INVALID_ARG, "grad_out / grad_sig is NULL");
@@ -569,6 +572,7 @@ stl_status stl_robustness_backward(stl_handle h, const float *sig, int64_t B, in
   A.sig = sig;
   A.bounds = h->n_slots ? bounds : nullptr;
   A.gout = grad_out;
+  A.out = out;
   A.gsig = grad_sig;
   A.gbounds = h->n_slots ? grad_bounds : nullptr;
   A.ws = (float *)workspace;
@@ -578,6 +582,23 @@ stl_status stl_robustness_backward(stl_handle h, const float *sig, int64_t B, in
   int e = stl_launch_main(pl.P, A);
   if (e) return cuda_fail(e, "robustness backward kernel launch");
   return STL_OK;
+}
+}  // namespace
+
+stl_status stl_robustness_backward(stl_handle h, const float *sig, int64_t B, int64_t T, const float *bounds,
+                                   const stl_params *p, const float *grad_out, float *grad_sig,
+                                   float *grad_bounds, void *workspace, size_t workspace_bytes, void *stream) {
+  return backward_launch(h, sig, B, T, bounds, p, grad_out, nullptr, grad_sig, grad_bounds, workspace,
+                         workspace_bytes, stream);
+}
+
+stl_status stl_robustness_and_backward(stl_handle h, const float *sig, int64_t B, int64_t T, const float *bounds,
+                                       const stl_params *p, const float *grad_out, float *out, float *grad_sig,
+                                       float *grad_bounds, void *workspace, size_t workspace_bytes,
+                                       void *stream) {
+  if (B > 0 && !out) return fail(STL_ERR_INVALID_ARG, "out is NULL");
+  return backward_launch(h, sig, B, T, bounds, p, grad_out, out, grad_sig, grad_bounds, workspace,
+                         workspace_bytes, stream);
 }
 
 // ------------------------------------------------------------------ host-buffer pipeline

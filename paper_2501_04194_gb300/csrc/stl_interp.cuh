@@ -373,7 +373,8 @@ struct Cta {
   int T;
   int t0, t1;          // current root step [t0, t1)
   int root;
-  float *out_row;      // forward: out + b*T
+  float *out_row;      // out + b*T (forward; backward launches that also return rho), or null
+  int own0;            // first sample of the work item (root outputs before it are warm-up)
 };
 
 __device__ __forceinline__ int frontier(const Cta &C, int n) {
@@ -456,17 +457,17 @@ struct NodeOut {
   int *aux;
   float *out_row;
   NodeRt *rt;
-  int start, T;
+  int start, T, own0;
   __device__ __forceinline__ void put(int q, float val) const {
     v[q - start] = val;
     if (q == T - 1) rt->lastval = val;
-    if (out_row) out_row[q] = val;
+    if (out_row && q >= own0) out_row[q] = val;
   }
   __device__ __forceinline__ void put(int q, float val, int src) const {
     v[q - start] = val;
     if (aux) aux[q - start] = src;
     if (q == T - 1) { rt->lastval = val; rt->lastaux = src; }
-    if (out_row) out_row[q] = val;
+    if (out_row && q >= own0) out_row[q] = val;
   }
 };
 
@@ -476,6 +477,7 @@ __device__ __forceinline__ NodeOut node_out(const Cta &C, int n) {
   o.v = r.val;
   o.aux = r.aux;
   o.out_row = (n == C.root) ? C.out_row : nullptr;
+  o.own0 = C.own0;
   o.rt = &r;
   o.start = C.t0 + r.lo;
   o.T = C.T;
@@ -893,6 +895,9 @@ __device__ void eval_hard_until(const Cta &C, int n, int F, int E, int ia, int i
 //      allocated with that slack); such reads feed only outputs that are discarded.
 // Long windows use runs of 15 samples per thread (fewer run aggregates per output).
 
+// new samples of a node below which a step uses the clamped-read passes
+constexpr int kLeanMinSamples = 4096;
+
 __device__ __forceinline__ bool is_temporal_op(int op) {
   return op == OP_EV || op == OP_ALW || op == OP_EVSM || op == OP_ALWSM || op == OP_UNTIL || op == OP_UNTSM;
 }
@@ -909,7 +914,8 @@ __device__ bool pad_fill(const Cta &C, int n) {
     if (c < 0 || frontier(C, c) < T) continue;
     const NodeRt &r = C.rt[c];
     const int start = C.t0 + r.lo;
-    const int f0 = max(T - start, 0), f1 = r.cap + STL_BUF_BACK;
+    // live outputs read at most ib samples past T-1, window runs at most 14 more
+    const int f0 = max(T - start, 0), f1 = min(r.cap + STL_BUF_BACK, T - start + C.rt[n].ib + 16);
     const float v = nd.pad_const ? nd.pad_value : r.lastval;
     for (int i = f0 + threadIdx.x; i < f1; i += blockDim.x) r.val[i] = v;
     any = any || f0 < f1;
@@ -1264,8 +1270,10 @@ __device__ void eval_smooth_mask(const Cta &C, int n, int F, int E) {
   }
 }
 
+// lean: evaluate a hard forward node with the direct-read passes (the caller has filled the
+// children's pads); otherwise with the clamped reads
 template <bool BWD, bool SMOOTH>
-__device__ void eval_node(const Cta &C, int n, int F, int E) {
+__device__ void eval_node(const Cta &C, int n, int F, int E, bool lean) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
   const NodeRt &r = C.rt[n];
@@ -1278,20 +1286,20 @@ __device__ void eval_node(const Cta &C, int n, int F, int E) {
     case OP_NOT:
     case OP_AND:
     case OP_OR:
-      if constexpr (SMOOTH || BWD) eval_elementwise<SMOOTH>(C, n, F, E);
+      if (SMOOTH || BWD || !lean) eval_elementwise<SMOOTH>(C, n, F, E);
       else lean_hard_elementwise(lean_args(C, n), F, E);
       break;
     case OP_EV:
     case OP_ALW:
       if constexpr (SMOOTH) eval_smooth_window(C, n, F, E, r.ia, r.ib);
-      else if constexpr (BWD) eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
+      else if (BWD || !lean) eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
       else lean_hard_window(lean_args(C, n), F, E, r.ia, r.ib);
       break;
     case OP_EVSM:
     case OP_ALWSM:
       if constexpr (SMOOTH) eval_smooth_mask(C, n, F, E);
       else if (r.ia > r.ib) break;
-      else if constexpr (BWD) eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
+      else if (BWD || !lean) eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
       else lean_hard_window(lean_args(C, n), F, E, r.ia, r.ib);
       break;
     case OP_UNTIL:
@@ -1299,7 +1307,7 @@ __device__ void eval_node(const Cta &C, int n, int F, int E) {
         if (P.mode == 2) eval_soft_until(C, n, F, E, r.ia, r.ib, nullptr);
         else eval_smooth_until(C, n, F, E, r.ia, r.ib, nullptr);
       }
-      else if constexpr (BWD) eval_hard_until<BWD>(C, n, F, E, r.ia, r.ib);
+      else if (BWD || !lean) eval_hard_until<BWD>(C, n, F, E, r.ia, r.ib);
       else lean_hard_until(lean_args(C, n), F, E, r.ia, r.ib);
       break;
     case OP_UNTSM:
@@ -1311,7 +1319,7 @@ __device__ void eval_node(const Cta &C, int n, int F, int E) {
       } else if constexpr (SMOOTH) {
         if (P.mode == 2) eval_soft_until(C, n, F, E, r.ia, r.ib, r.tab);
         else eval_smooth_until(C, n, F, E, r.ia, r.ib, r.tab);
-      } else if constexpr (BWD) {
+      } else if (BWD || !lean) {
         eval_hard_until<BWD>(C, n, F, E, r.ia, r.ib);
       } else {
         lean_hard_until(lean_args(C, n), F, E, r.ia, r.ib);
@@ -2119,7 +2127,10 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
       C.scratch = smem + (size_t)P.scratch_off * 4;
       C.root = P.n - 1;
     }
-    C.out_row = BWD ? nullptr : A.out + C.row0;
+    // backward launches return rho too when given an output (robustness and gradient in one
+    // launch: the backward recomputes every node's trace anyway)
+    C.out_row = A.out ? A.out + C.row0 : nullptr;
+    C.own0 = s0;
     setup_geometry(C, A.bounds, ws_cta, smem, A.status);
     if (BWD) {
       for (int n = 0; n < P.n; ++n)
@@ -2146,13 +2157,15 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
         const int F0 = (t0 == R0) ? R0 + r.lo : t0 + r.hi;
         const int F = F0 < T ? F0 : T;
         const int E = frontier(C, n);
-        constexpr bool lean = !BWD && !SMOOTH;
+        // hard forward nodes with many new samples take the direct-read passes (separate
+        // functions: their call costs more than it saves on short steps, e.g. short traces)
+        const bool lean = !BWD && !SMOOTH && E - F >= kLeanMinSamples;
         const bool temporal = lean && is_temporal_op(P.nd[n].op);
         if (F < E) {
-          // lean passes: the children's samples past the end hold the pad before a temporal
-          // node reads them
+          // the children's samples past the end hold the pad before a lean temporal node
+          // reads them
           if (temporal && pad_fill(C, n)) __syncthreads();
-          eval_node<BWD, SMOOTH>(C, n, F, E);
+          eval_node<BWD, SMOOTH>(C, n, F, E, lean);
         }
         __syncthreads();
         if (temporal && n == C.root) {

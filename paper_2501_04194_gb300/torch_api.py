@@ -8,8 +8,8 @@ from __future__ import annotations
 import torch
 
 from .binding import (Formula, FormulaSet, StlParams, params as make_params, pipeline_staging_size,
-                      robustness_backward_raw, robustness_host_pipelined_raw, robustness_ragged_backward_raw,
-                      robustness_ragged_raw, robustness_raw)
+                      robustness_and_backward_raw, robustness_backward_raw, robustness_host_pipelined_raw,
+                      robustness_ragged_backward_raw, robustness_ragged_raw, robustness_raw)
 
 
 def _check_sig(f: Formula, sig: torch.Tensor):
@@ -68,6 +68,27 @@ def robustness_backward(f: Formula, sig: torch.Tensor, grad_out: torch.Tensor, b
                             gsig.data_ptr(), None if gb is None else gb.data_ptr(),
                             None if ws is None else ws.data_ptr(), nws, stream)
     return gsig, gb
+
+
+def robustness_and_grad(f: Formula, sig: torch.Tensor, grad_out: torch.Tensor, bounds=None,
+                        p: StlParams | None = None):
+    """(rho [B,T], grad_sig [B,T,D], grad_bounds [B,n_slots,2] or None) in one launch
+    (stl_robustness_and_backward): for an upstream gradient known before the forward values,
+    e.g. a loss linear in rho."""
+    p = p or make_params()
+    sig = _check_sig(f, sig)
+    B, T, D = sig.shape
+    b = _bounds(f, bounds, sig)
+    g = grad_out.to(device=sig.device, dtype=torch.float32).contiguous()
+    rho = torch.empty((B, T), dtype=torch.float32, device=sig.device)
+    gsig = torch.empty((B, T, D), dtype=torch.float32, device=sig.device)
+    gb = torch.empty((B, f.n_slots, 2), dtype=torch.float32, device=sig.device) if f.n_slots else None
+    ws, nws = _ws(f, B, T, p, True, sig.device)
+    stream = torch.cuda.current_stream(sig.device).cuda_stream
+    robustness_and_backward_raw(f, sig.data_ptr(), B, T, None if b is None else b.data_ptr(), p, g.data_ptr(),
+                                rho.data_ptr(), gsig.data_ptr(), None if gb is None else gb.data_ptr(),
+                                None if ws is None else ws.data_ptr(), nws, stream)
+    return rho, gsig, gb
 
 
 class HostPipeline:

@@ -122,3 +122,11 @@ def test_null_arguments_are_rejected_before_any_launch():
     assert rc == -1 and b"tau" in lib.stl_last_error()
     # B == 0 is a no-op
     assert lib.stl_robustness(f.handle, None, 0, 10, None, ctypes.byref(p), None, None, 0, None) == 0
+    # the one-launch robustness and gradient needs rho, grad_out and grad_sig
+    v = ctypes.c_void_p(16)
+    rc = lib.stl_robustness_and_backward(f.handle, v, 4, 10, None, ctypes.byref(p), v, None, v, None, None, 0, None)
+    assert rc == -1 and b"out" in lib.stl_last_error()
+    rc = lib.stl_robustness_and_backward(f.handle, v, 4, 10, None, ctypes.byref(p), None, v, v, None, None, 0, None)
+    assert rc == -1 and b"grad_out" in lib.stl_last_error()
+    assert lib.stl_robustness_and_backward(f.handle, None, 0, 10, None, ctypes.byref(p), None, None, None, None, None,
+                                           0, None) == 0

@@ -295,6 +295,44 @@ def test_bounds_outside_caps_set_the_device_status(stl):
     assert device_status() == 0
 
 
+
+# ------------------------------------------------------------------ long steps: direct-read forward
+# Hard forward steps of at least 4096 new samples per node take the direct-read passes (pads
+# filled past the end of the trace, runs of 15 for long windows); these launches force them,
+# with the last step of each trace short and long, pads of both kinds, windows past the end,
+# b = inf, per-trace and masked bounds, and traces split into segments.
+LONG_CASES = [
+    ("config1_512", W.config1_formula(), 3, 20000, dict(tile=7168, threads=512), None),
+    ("config1_256_segments", W.config1_formula(), 3, 12001, dict(tile=4096, threads=256, segment=6000), None),
+    ("until_const_pad", W.Until(2, 40, W.gt([1, 0], 0.0), W.lt([0, 1], 0.3), pad=0.2), 2, 9001,
+     dict(tile=4096, threads=512), None),
+    ("until_a0_ev", W.Eventually(0, 3000, W.Until(0, 17, W.gt([1, 0], -0.2), W.gt([0, 1], 0.1))), 2, 8192,
+     dict(tile=4096, threads=512), None),
+    ("always_to_end", W.Or(W.Always(0, math.inf, W.gt([1, 0], -2.0)), W.Not(W.lt([0, 1], 0.5))), 2, 6000,
+     dict(tile=4096, threads=512), None),
+    ("windows_past_end", W.And(W.Eventually(5000, 9000, W.gt([1, 0], 0.0), pad=-0.5),
+                               W.Always(3, 12, W.lt([0, 1], 1.0))), 2, 7000, dict(tile=7168, threads=512), None),
+    ("slots", W.Eventually(300, 900, W.Always(100, 400, W.gt([1], 0.1), slot=1), slot=0), 1, 9000,
+     dict(tile=4096, threads=512), "slots"),
+    ("masked", W.EventuallySm(100.0, 400.0, W.gt([1], 0.8), slot=0), 1, 8000, dict(tile=4096, threads=512), "masked"),
+    ("table3_phi4", W.table3_formulas(D=2, I=(2, 37))[3], 2, 10000, dict(tile=4096, threads=512), None),
+]
+
+
+@pytest.mark.parametrize("name,tree,D,T,launch,kind", LONG_CASES, ids=[c[0] for c in LONG_CASES])
+def test_long_steps_hard(stl, name, tree, D, T, launch, kind):
+    sig = W.random_walk(4, T, D, seed=len(name))
+    bounds = None
+    rng = np.random.default_rng(len(name))
+    if kind == "slots":
+        outer = np.stack([rng.uniform(0, 300, 4), rng.uniform(600, 900, 4)], 1)
+        inner = np.stack([rng.uniform(0, 100, 4), rng.uniform(200, 400, 4)], 1)
+        bounds = np.floor(np.stack([outer, inner], 1)).astype(np.float32)
+    elif kind == "masked":
+        a = rng.uniform(0, 100, 4)
+        bounds = np.stack([a, a + rng.uniform(20, 300, 4)], 1).astype(np.float32)[:, None, :]
+    check(stl, tree, sig, bounds=bounds, mode="hard", launch=launch)
+
 # ------------------------------------------------------------------ full-size spot checks
 def test_config1_full_size_sampled(stl):
     """B=1024, T=50000 (the benchmark launch): sampled traces checked against the oracle."""
