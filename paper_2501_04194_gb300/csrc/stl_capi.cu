@@ -190,10 +190,17 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
   tile = std::min(tile, round_up(T, 32));
   tile = std::max(32, round_up(tile, 32));
 
-  // every buffer is allocated with STL_BUF_FRONT words before and STL_BUF_BACK words after
-  // its live range: the hard-mode window passes read a few samples past the range without
-  // clamping (those reads feed no output)
-  auto padded = [](int cap) { return cap + STL_BUF_FRONT + STL_BUF_BACK; };
+  // hard forward plans whose node steps can reach STL_LEAN_MIN_SAMPLES samples allocate every
+  // buffer with STL_BUF_BACK words after its live range: their direct-read window passes read
+  // a few samples past the range without clamping (those reads feed no output)
+  int maxspan = 0;
+  for (int i = 0; i < n; ++i) maxspan = std::max(maxspan, hi[i] - lo[i]);
+  const bool lean_mode = !bwd && p.mode == STL_HARD;   // the 512-thread forward kernels take them
+  auto slack_for = [&](int tl) {
+    return (lean_mode && threads == 512 && (long long)tl + maxspan >= STL_LEAN_MIN_SAMPLES) ? STL_BUF_BACK : 0;
+  };
+  int slack = 0;
+  auto padded = [&](int cap) { return cap + slack; };
   // window scratch: run aggregates (threads + K/7) and their blocks of 8, 16 bytes each (24
   // for the double-precision sums of the softmax-weighted adjoint); the signal gradient reuses
   // it for the predicate adjoint pointers
@@ -203,6 +210,7 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
     return std::max((runs + runs / 8 + 8) * entry_words, 2 * STL_MAX_PRED);
   };
   auto layout = [&](int tl, std::vector<int> &space_out, int &smem_words, int &gwords) {
+    slack = slack_for(tl);
     // scratch for window run aggregates: (threads + maxK/R + 2) entries of up to 16 bytes
     const int scratch_words = scratch_for(threads);
     const int rt_words = (int)((n * sizeof(NodeRt) + 15) / 16 * 4);
@@ -252,6 +260,8 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
     if (!force_threads && !h->launch.threads && tile < 512 * win_r) threads = 256;
   }
   P.tile = tile;
+  slack = slack_for(tile);
+  P.lean = slack > 0;
 
   // assign offsets
   int off_s = 0, off_g = 0;
@@ -275,13 +285,13 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
     k.space = space[i];
     int &off = space[i] ? off_g : off_s;
     const int pw = padded(k.cap);
-    k.val_off = off + STL_BUF_FRONT; off += pw;
+    k.val_off = off; off += pw;
     k.adj_off = -1;
     k.aux_off = -1;
     if (bwd) {
-      if (soft_mode(p.mode) || is_pred(nd.op)) { k.adj_off = off + STL_BUF_FRONT; off += pw; }
+      if (soft_mode(p.mode) || is_pred(nd.op)) { k.adj_off = off; off += pw; }
       if ((p.mode == STL_HARD && is_temporal(nd.op)) || (p.mode == STL_SOFTMAX && is_window(nd.op))) {
-        k.aux_off = off + STL_BUF_FRONT;
+        k.aux_off = off;
         off += pw;
       }
     }

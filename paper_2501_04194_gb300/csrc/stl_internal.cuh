@@ -9,8 +9,8 @@
 #define STL_MAX_WEIGHTS 256
 #define STL_MAX_D 16
 #define STL_MAX_PRED 32
-#define STL_BUF_FRONT 4    // words allocated before every node buffer
-#define STL_BUF_BACK 32    // words allocated after every node buffer (unclamped over-reads)
+#define STL_LEAN_MIN_SAMPLES 4096   // hard forward node steps this long take the direct-read passes
+#define STL_BUF_BACK 16    // words after every node buffer of such plans (unclamped over-reads)
 
 // Node layout after compilation (per launch: the ring geometry depends on tile and bounds).
 struct KNode {
@@ -53,6 +53,7 @@ struct KProgram {
   long long ut_off;    // word offset of the smooth-until per-thread arrays in the workspace
   int ut_len;          // their length (max taps)
   int win_r;           // samples per thread-run of the largest windows (15)
+  int lean;            // 1: buffers carry STL_BUF_BACK words of slack, direct-read passes allowed
   int npred;           // predicate nodes
   unsigned norm_mask;  // bit k: predicate k is a norm predicate (its pw row is zero)
   int pred[STL_MAX_PRED];

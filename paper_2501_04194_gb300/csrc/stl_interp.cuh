@@ -895,9 +895,6 @@ __device__ void eval_hard_until(const Cta &C, int n, int F, int E, int ia, int i
 //      allocated with that slack); such reads feed only outputs that are discarded.
 // Long windows use runs of 15 samples per thread (fewer run aggregates per output).
 
-// new samples of a node below which a step uses the clamped-read passes
-constexpr int kLeanMinSamples = 4096;
-
 __device__ __forceinline__ bool is_temporal_op(int op) {
   return op == OP_EV || op == OP_ALW || op == OP_EVSM || op == OP_ALWSM || op == OP_UNTIL || op == OP_UNTSM;
 }
@@ -1272,7 +1269,7 @@ __device__ void eval_smooth_mask(const Cta &C, int n, int F, int E) {
 
 // lean: evaluate a hard forward node with the direct-read passes (the caller has filled the
 // children's pads); otherwise with the clamped reads
-template <bool BWD, bool SMOOTH>
+template <bool BWD, bool SMOOTH, bool LEAN>
 __device__ void eval_node(const Cta &C, int n, int F, int E, bool lean) {
   const KProgram &P = *C.P;
   const KNode &nd = P.nd[n];
@@ -1286,20 +1283,20 @@ __device__ void eval_node(const Cta &C, int n, int F, int E, bool lean) {
     case OP_NOT:
     case OP_AND:
     case OP_OR:
-      if (SMOOTH || BWD || !lean) eval_elementwise<SMOOTH>(C, n, F, E);
+      if (SMOOTH || BWD || !LEAN || !lean) eval_elementwise<SMOOTH>(C, n, F, E);
       else lean_hard_elementwise(lean_args(C, n), F, E);
       break;
     case OP_EV:
     case OP_ALW:
       if constexpr (SMOOTH) eval_smooth_window(C, n, F, E, r.ia, r.ib);
-      else if (BWD || !lean) eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
+      else if (BWD || !LEAN || !lean) eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
       else lean_hard_window(lean_args(C, n), F, E, r.ia, r.ib);
       break;
     case OP_EVSM:
     case OP_ALWSM:
       if constexpr (SMOOTH) eval_smooth_mask(C, n, F, E);
       else if (r.ia > r.ib) break;
-      else if (BWD || !lean) eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
+      else if (BWD || !LEAN || !lean) eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
       else lean_hard_window(lean_args(C, n), F, E, r.ia, r.ib);
       break;
     case OP_UNTIL:
@@ -1307,7 +1304,7 @@ __device__ void eval_node(const Cta &C, int n, int F, int E, bool lean) {
         if (P.mode == 2) eval_soft_until(C, n, F, E, r.ia, r.ib, nullptr);
         else eval_smooth_until(C, n, F, E, r.ia, r.ib, nullptr);
       }
-      else if (BWD || !lean) eval_hard_until<BWD>(C, n, F, E, r.ia, r.ib);
+      else if (BWD || !LEAN || !lean) eval_hard_until<BWD>(C, n, F, E, r.ia, r.ib);
       else lean_hard_until(lean_args(C, n), F, E, r.ia, r.ib);
       break;
     case OP_UNTSM:
@@ -1319,7 +1316,7 @@ __device__ void eval_node(const Cta &C, int n, int F, int E, bool lean) {
       } else if constexpr (SMOOTH) {
         if (P.mode == 2) eval_soft_until(C, n, F, E, r.ia, r.ib, r.tab);
         else eval_smooth_until(C, n, F, E, r.ia, r.ib, r.tab);
-      } else if (BWD || !lean) {
+      } else if (BWD || !LEAN || !lean) {
         eval_hard_until<BWD>(C, n, F, E, r.ia, r.ib);
       } else {
         lean_hard_until(lean_args(C, n), F, E, r.ia, r.ib);
@@ -2067,6 +2064,7 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
   char *smem = reinterpret_cast<char *>(smem4);
   __shared__ long long s_item;
   constexpr bool ragged = RAGGED;
+  constexpr bool kLean = !BWD && !SMOOTH && NT == 512;
   Cta C;
   C.sig = A.sig;
   const int gwords = ragged ? A.gwords : Pdense.gwords;
@@ -2159,13 +2157,15 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
         const int E = frontier(C, n);
         // hard forward nodes with many new samples take the direct-read passes (separate
         // functions: their call costs more than it saves on short steps, e.g. short traces)
-        const bool lean = !BWD && !SMOOTH && E - F >= kLeanMinSamples;
+        // (512-thread kernels only: the others serve short traces, and carrying the direct-read
+        // passes made their code slower even where the passes were not taken)
+        const bool lean = kLean && P.lean && E - F >= STL_LEAN_MIN_SAMPLES;
         const bool temporal = lean && is_temporal_op(P.nd[n].op);
         if (F < E) {
           // the children's samples past the end hold the pad before a lean temporal node
           // reads them
           if (temporal && pad_fill(C, n)) __syncthreads();
-          eval_node<BWD, SMOOTH>(C, n, F, E, lean);
+          eval_node<BWD, SMOOTH, kLean>(C, n, F, E, lean);
         }
         __syncthreads();
         if (temporal && n == C.root) {
