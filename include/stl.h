@@ -53,7 +53,7 @@ extern "C" {
 typedef enum {
   STL_OK = 0,
   STL_ERR_INVALID_ARG = -1,  /* a host-side argument check failed */
-  STL_ERR_UNSUPPORTED = -2,  /* valid but outside what this build supports (see message) */
+  STL_ERR_UNSUPPORTED = -2,  /* valid but outside what the library supports (see message) */
   STL_ERR_CUDA = -3,         /* a CUDA runtime call failed (see message) */
   STL_ERR_WORKSPACE = -4,    /* workspace missing or smaller than stl_workspace_size() */
   STL_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */

@@ -373,8 +373,7 @@ struct Cta {
   int T;
   int t0, t1;          // current root step [t0, t1)
   int root;
-  float *out_row;      // out + b*T (forward; backward launches that also return rho), or null
-  int own0;            // first sample of the work item (root outputs before it are warm-up)
+  float *out_row;      // forward: out + b*T
 };
 
 __device__ __forceinline__ int frontier(const Cta &C, int n) {
@@ -457,17 +456,17 @@ struct NodeOut {
   int *aux;
   float *out_row;
   NodeRt *rt;
-  int start, T, own0;
+  int start, T;
   __device__ __forceinline__ void put(int q, float val) const {
     v[q - start] = val;
     if (q == T - 1) rt->lastval = val;
-    if (out_row && q >= own0) out_row[q] = val;
+    if (out_row) out_row[q] = val;
   }
   __device__ __forceinline__ void put(int q, float val, int src) const {
     v[q - start] = val;
     if (aux) aux[q - start] = src;
     if (q == T - 1) { rt->lastval = val; rt->lastaux = src; }
-    if (out_row && q >= own0) out_row[q] = val;
+    if (out_row) out_row[q] = val;
   }
 };
 
@@ -477,7 +476,6 @@ __device__ __forceinline__ NodeOut node_out(const Cta &C, int n) {
   o.v = r.val;
   o.aux = r.aux;
   o.out_row = (n == C.root) ? C.out_row : nullptr;
-  o.own0 = C.own0;
   o.rt = &r;
   o.start = C.t0 + r.lo;
   o.T = C.T;
@@ -2125,10 +2123,7 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
       C.scratch = smem + (size_t)P.scratch_off * 4;
       C.root = P.n - 1;
     }
-    // backward launches return rho too when given an output (robustness and gradient in one
-    // launch: the backward recomputes every node's trace anyway)
-    C.out_row = A.out ? A.out + C.row0 : nullptr;
-    C.own0 = s0;
+    C.out_row = BWD ? nullptr : A.out + C.row0;
     setup_geometry(C, A.bounds, ws_cta, smem, A.status);
     if (BWD) {
       for (int n = 0; n < P.n; ++n)
@@ -2174,6 +2169,15 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
           const int st = t0 + r.lo;
           for (int q = F + threadIdx.x; q < E; q += NT) C.out_row[q] = rv[q - st];
         }
+      }
+      if (BWD && A.out) {
+        // robustness and gradient in one launch: the backward has just recomputed the root's
+        // values; copy out those of the samples this work item owns (not its warm-up)
+        const NodeRt &rr = C.rt[C.root];
+        const float *rv = rr.val;
+        const int st = t0 + rr.lo;
+        float *orow = A.out + C.row0;
+        for (int q = (t0 > s0 ? t0 : s0) + threadIdx.x; q < t1; q += NT) orow[q] = rv[q - st];
       }
       if constexpr (BWD && !SMOOTH) {
         hard_walk(C, A.gout + C.row0, t0, t1);
