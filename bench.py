@@ -382,6 +382,7 @@ def main():
     import paper_2501_04194_gb300 as stl
     import workloads as W
 
+    from paper_2501_04194_gb300.sharding import max_over_ranks
     B, T = args.B, args.T
     tree = W.config1_formula()
     f = stl.Formula(tree, D=D)
@@ -444,10 +445,7 @@ def main():
     ms_total = t_start.elapsed_time(t_end)
     fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     bwd_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total)
     ms_step = ms_total / args.steps
     value = world * B * T / (ms_step * 1e-3)
 
@@ -470,10 +468,7 @@ def main():
     b_.record(stream)
     torch.cuda.synchronize(dev)
     fused_ms = a_.elapsed_time(b_) / args.steps
-    if world > 1:
-        t = torch.tensor([fused_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        fused_ms = float(t.item())
+    fused_ms = max_over_ranks(fused_ms)
     fused = {"value": world * B * T / (fused_ms * 1e-3), "unit": UNIT, "ms_per_step": fused_ms,
              "note": "rho and the gradient of sum(g * rho) in one launch (stl_robustness_and_backward)"}
 
@@ -502,10 +497,7 @@ def main():
         b_.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms = a.elapsed_time(b_) / n_e2e
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e2e_ms)
         e2e = {"value": world * B * T / (e2e_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(hsig.numel() * 4 + hg.numel() * 4),
                "d2h_bytes_per_step": int(hrho.numel() * 4 + hgs.numel() * 4),
