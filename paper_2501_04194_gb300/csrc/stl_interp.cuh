@@ -19,8 +19,9 @@
 //   (max, scaled sum) pairs of logsumexp                  (smooth windows and their adjoint)
 // The hard Until rests on  rho_t = min( min_{k<=a} phi_{t+k},
 //                                       (f_{t+a} o ... o f_{t+b})(-inf) ),
-// which follows from min distributing over max in the definition of Sec. IV-C.  R = 7 is
-// odd, so the strided runs of a warp fall in distinct shared-memory banks.
+// which follows from min distributing over max in the definition of Sec. IV-C.  R = 7 (15
+// for long windows in the direct-read forward passes) is odd, so the strided runs of a warp
+// fall in distinct shared-memory banks.
 //
 // Backward launches recompute the forward trace of every node step by step (values run
 // ahead of the root by `hi`), and propagate adjoints in reverse order over the samples whose
@@ -881,9 +882,9 @@ __device__ void eval_hard_until(const Cta &C, int n, int F, int E, int ia, int i
 }
 
 // ------------------------------------------------------------------ lean hard forward passes
-// Forward launches in hard mode evaluate windows, Until and the elementwise operators with
-// direct reads of their children's buffers: no clamping and no end-of-trace test per read.
-// This is exact because
+// Hard forward steps of the 512-thread kernels with at least STL_LEAN_MIN_SAMPLES new samples
+// in a node evaluate windows, Until and the elementwise operators with direct reads of their
+// children's buffers: no clamping and no end-of-trace test per read.  This is exact because
 //  (1) a child computes every sample below its frontier min(t1 + hi, T), and a live output
 //      of the parent reads only samples below that frontier or at or after T;
 //  (2) before a temporal parent runs in a step where the child's frontier has reached T,
