@@ -1294,7 +1294,13 @@ __device__ void eval_node(const Cta &C, int n, int F, int E, bool lean) {
     case OP_EVSM:
     case OP_ALWSM:
       if constexpr (SMOOTH) eval_smooth_mask(C, n, F, E);
-      else if (r.ia > r.ib) break;
+      else if (r.ia > r.ib) {
+        // no offset has a positive mask (b - a too small for the sharpness): the max (min)
+        // over an empty set, -inf (+inf), selecting no sample
+        const NodeOut o = node_out(C, n);
+        const float v = nd.op == OP_EVSM ? -INFINITY : INFINITY;
+        for (int q = F + threadIdx.x; q < E; q += blockDim.x) o.put(q, v, -1);
+      }
       else if (BWD || !LEAN || !lean) eval_hard_window<BWD>(C, n, F, E, r.ia, r.ib);
       else lean_hard_window(lean_args(C, n), F, E, r.ia, r.ib);
       break;

@@ -40,7 +40,8 @@ def per_trace_err(got, ref):
     assert np.array_equal(fin, np.isfinite(g)) and np.array_equal(g[~fin], r[~fin])
     scale = np.where(fin, np.abs(r), 0).max(axis=1, keepdims=True)
     scale = np.maximum(scale, 1e-30)
-    d = np.where(fin, np.abs(g - r), 0) / scale
+    with np.errstate(invalid="ignore"):   # inf - inf where both are the same infinity
+        d = np.where(fin, np.abs(g - r), 0) / scale
     return d.max()
 
 
@@ -295,6 +296,21 @@ def test_bounds_outside_caps_set_the_device_status(stl):
     assert device_status() == 0
 
 
+
+
+@pytest.mark.parametrize("mode", ["hard", "smooth", "softmax"])
+def test_masked_window_with_empty_support(stl, mode):
+    """Per-trace bounds with a = b give a mask that is positive nowhere (Eq. smooth mask with
+    eps > 0): Eventually is -inf and Always +inf at every sample, with zero gradient; the other
+    traces of the batch are ordinary."""
+    rng = np.random.default_rng(11)
+    sig = rng.normal(size=(4, 600, 1)).astype(np.float32)
+    bounds = np.array([[[10.0, 10.0]], [[5.0, 60.0]], [[0.0, 0.0]], [[20.0, 90.0]]], dtype=np.float32)
+    trees = [W.EventuallySm(40, 100, W.gt([1.0], 0.1), slot=0)]
+    if mode == "hard":
+        trees.append(W.Or(W.AlwaysSm(40, 100, W.lt([1.0], 0.5), slot=0), W.gt([1.0], 2.5)))
+    for tree in trees:
+        check(stl, tree, sig, bounds=bounds, mode=mode, tau=5.0, mask_c=5.0, mask_eps=1e-3)
 
 # ------------------------------------------------------------------ long steps: direct-read forward
 # Hard forward steps of at least 4096 new samples per node take the direct-read passes (pads
