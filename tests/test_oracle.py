@@ -230,6 +230,25 @@ def test_smooth_mask_limits():
     np.testing.assert_allclose(sm, want, rtol=1e-9, atol=1e-9)
 
 
+def test_smooth_mask_empty_support():
+    """Eq. "smooth mask" with a = b: sigma(c(i-a)) - sigma(c(i-b)) = 0 for every offset, so with
+    eps > 0 no mask weight is positive and the window is empty: Eventually is the max over an
+    empty set, -inf, Always +inf, in every mode (the log of an empty sum), and nothing selects
+    a sample, so the signal and bound gradients are zero."""
+    rng = np.random.default_rng(12)
+    s = rng.normal(size=(2, 50, 1)).astype(np.float32)
+    bounds = np.array([[[7.0, 7.0]], [[3.0, 20.0]]], dtype=np.float32)
+    for mode in (HARD, SMOOTH, oracle.SOFTMAX):
+        for op, sgn in ((W.EventuallySm, 1.0), (W.AlwaysSm, -1.0)):
+            f = op(10, 30, x_pred(), slot=0)
+            r = oracle.robustness(f, s, bounds=bounds, mode=mode, tau=3.0, mask_c=5.0, mask_eps=1e-3)
+            assert np.all(r[0] == -sgn * np.inf)
+            assert np.all(np.isfinite(r[1]))
+            g, gb = oracle.robustness_grad(f, s, np.ones((2, 50)), bounds=bounds, mode=mode, tau=3.0,
+                                           mask_c=5.0, mask_eps=1e-3)
+            assert np.all(g[0] == 0) and np.all(gb[0] == 0)
+
+
 def test_predicate_float32_rounding():
     rng = np.random.default_rng(11)
     s = (rng.normal(size=(2, 64, 3)) * 1e3).astype(np.float32)
