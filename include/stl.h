@@ -205,11 +205,14 @@ STL_API stl_status stl_robustness_and_backward(stl_handle h, const float *sig, i
  * owns every device byte).  Same arguments and results as stl_robustness_backward, without
  * the workspace: the scratch comes from a file-scope static __device__ array of
  * STL_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until exit.
- *   - The first call on a device looks up that array's device address (cudaGetSymbolAddress,
- *     with the device current); make that first call before any stream capture.
+ *   - Every call looks up that array's device address (cudaGetSymbolAddress, with the call's
+ *     device current), so the address stays right after a device reset; the first call on a
+ *     device may load the library's device code, so make it before any stream capture.
  *   - If the scratch cannot hold what all resident CTAs would need, fewer CTAs are launched
- *     (they walk all work items); if a single CTA needs more, the call returns
- *     STL_ERR_WORKSPACE with a message stating both sizes.
+ *     (they walk all work items); if one CTA of the planned size needs more, the call is
+ *     planned again with 64-thread CTAs (the smooth Until's per-thread arrays shrink with the
+ *     CTA); if even that needs more, it returns STL_ERR_WORKSPACE with a message stating both
+ *     sizes.  B = 0 is checked and returns STL_OK without planning.
  *   - Every call shares the one array and leaves its last contents there; the kernels write
  *     each scratch word before reading it.  Calls whose kernels overlap on the GPU (different
  *     streams, no ordering) race on the array and give undefined results: serialise them.

@@ -19,7 +19,7 @@
  * takes the literal triple loop (max over i, running min over tau).  There is no
  * blocking, no sliding-window trick and no reordering beyond those definitions.
  *
- * Readings where the paper is silent (each is listed in the design notes):
+ * Readings where the paper is silent (numbered here; the comments below refer to them):
  *   R1  a trace has T samples, indices 0..T-1;
  *   R2  a read at j >= T returns the pad: the last sample (PAD_LAST, gradient to T-1)
  *       or a constant (PAD_CONST, no gradient); smooth windows count pad reads with

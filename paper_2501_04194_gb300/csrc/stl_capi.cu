@@ -754,10 +754,27 @@ stl_status stl_internal_plan_backward_capped(stl_handle h, const float *sig, int
                                              KProgram *prog, int *grid, int *threads, size_t *ws_bytes) {
   stl_status s = check_call(h, sig, B, T, bounds, p);
   if (s) return s;
+  if (B == 0) {   // nothing to launch: no plan, as in stl_robustness_backward
+    *grid = 0;
+    *threads = 0;
+    *ws_bytes = 0;
+    return STL_OK;
+  }
   Plan pl;
   s = make_plan(h, B, T, *p, true, pl);
   if (s) return s;
-  const size_t per_cta_words = (size_t)pl.P.gwords + (size_t)until_arrays(p->mode) * pl.P.ut_len * pl.threads;
+  size_t per_cta_words = (size_t)pl.P.gwords + (size_t)until_arrays(p->mode) * pl.P.ut_len * pl.threads;
+  if (per_cta_words * 4 > capacity_bytes && pl.threads > 64) {
+    // the smooth Until's per-thread arrays scale with the CTA size: try the smallest CTAs
+    Plan small;
+    s = make_plan(h, B, T, *p, true, small, 64);
+    if (s) return s;
+    const size_t w64 = (size_t)small.P.gwords + (size_t)until_arrays(p->mode) * small.P.ut_len * small.threads;
+    if (w64 < per_cta_words) {
+      pl = small;
+      per_cta_words = w64;
+    }
+  }
   if (per_cta_words * 4 > capacity_bytes)
     return fail(STL_ERR_WORKSPACE, "one CTA needs %zu bytes of scratch, the static scratch holds %zu",
                 per_cta_words * 4, capacity_bytes);

@@ -1177,7 +1177,8 @@ __device__ void eval_smooth_until(const Cta &C, int n, int F, int E, int ia, int
   }
 }
 
-// Softmax-weighted Until (R17): P_i = softmin_{k<=i} phi_{q+k}, z_i = softmin(P_i, psi_{q+i}),
+// Softmax-weighted Until (each of its three min/max levels is one softmax-weighted reduction
+// over its own multiset, never a nesting of two-term operators): P_i = softmin_{k<=i} phi_{q+k}, z_i = softmin(P_i, psi_{q+i}),
 // U = softmax_{i in [a,b]} z_i, each one softmax-weighted reduction; one output per thread.
 __device__ void eval_soft_until(const Cta &C, int n, int F, int E, int ia, int ib, const float *w) {
   const KProgram &P = *C.P;
@@ -1628,7 +1629,7 @@ __device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, int ow
   }
 }
 
-// Softmax-weighted Until adjoint (R17).  Per output q: a forward pass over the taps stores
+// Softmax-weighted Until adjoint (three softmax-weighted levels, as in the forward).  Per output q: a forward pass over the taps stores
 // P_i, L_i = log sum_{k<=i} e^{-tau phi_k} and z_i (3 per-thread workspace arrays) and yields U
 // and its log-normaliser; then
 //   dU/dz_i = e^{tau z_i - lseU} (1 + tau (z_i - U)),

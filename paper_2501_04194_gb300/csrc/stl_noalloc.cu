@@ -10,11 +10,10 @@
 //
 // The array is a static __device__ object of STL_NOALLOC_SCRATCH_BYTES: every GPU that loads
 // the library holds it until the process exits.  In host code its name is only a host-side
-// stand-in, so its device address is obtained with cudaGetSymbolAddress, once per device, with
-// that device current, on the first call made on that device.
+// stand-in, so its device address is obtained with cudaGetSymbolAddress, with the call's device
+// current, on every call: after a device reset the module is loaded again and the array may
+// sit at another address, so a cached address could point at freed memory.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "../../include/stl.h"
 #include "stl_internal.cuh"
@@ -29,24 +28,12 @@ namespace {
 constexpr size_t kScratchWords = STL_NOALLOC_SCRATCH_BYTES / sizeof(float);
 static __device__ __align__(256) float g_noalloc_scratch[kScratchWords];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_lock;
-void *g_addr[kMaxDevices] = {};
-
-// device address of the static scratch on the current device (looked up once per device)
+// device address of the static scratch in the current device's context (looked up per call)
 stl_status scratch_address(void **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void *ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
   if (e != cudaSuccess) return stl_internal_fail(STL_ERR_CUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return stl_internal_fail(STL_ERR_UNSUPPORTED, "device index too large");
-  std::lock_guard<std::mutex> g(g_lock);
-  if (!g_addr[dev]) {
-    void *ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return stl_internal_fail(STL_ERR_CUDA, cudaGetErrorString(e));
-    g_addr[dev] = ptr;
-  }
-  *out = g_addr[dev];
+  *out = ptr;
   return STL_OK;
 }
 
@@ -64,7 +51,7 @@ stl_status stl_robustness_backward_noalloc(stl_handle h, const float *sig, int64
   stl_status s = stl_internal_plan_backward_capped(h, sig, B, T, bounds, p, STL_NOALLOC_SCRATCH_BYTES, &prog, &grid,
                                                    &threads, &ws_bytes);
   if (s) return s;
-  if (B == 0) return STL_OK;
+  if (B == 0) return STL_OK;   // checked, nothing to launch (the planner stops before planning)
   void *scratch = nullptr;
   s = scratch_address(&scratch);
   if (s) return s;
