@@ -89,6 +89,35 @@ def until(p, q, a, b, pad, hard, tau):
     return _smax(S2, 1, tau, hard)
 
 
+def smooth_mask_window(x, a, b, c, eps, pad, op, hard, tau):
+    """Sec. VI, Eq. "smooth mask", by the unroll of Sec. IV-B with NO support cutoff: every
+    offset i = 0 .. T + b + 64 of the padded child trace gets the mask weight
+    m_i = max(sigma(c(i - a)) - sigma(c(i - b)) - eps, 0), which enters the reduction as the
+    log-weight log m_i (-inf where m_i = 0; reading R6).  ``a`` and ``b`` are torch scalars
+    (in steps), so autograd gives d/da and d/db.  hard=True: max / min over {i : m_i > 0};
+    False: logsumexp; None: softmax-weighted."""
+    T = x.shape[0]
+    N = T + int(math.ceil(float(torch.as_tensor(b).detach()))) + 64
+    xp = _pad(x, N, pad)
+    i = torch.arange(N, dtype=x.dtype)
+    m = torch.sigmoid(c * (i - a)) - torch.sigmoid(c * (i - b)) - eps
+    pos = m > 0
+    m = torch.where(pos, m, torch.ones_like(m))          # no log(0) on the autograd path
+    logm = torch.where(pos, torch.log(m), torch.full_like(m, -math.inf))
+    t = torch.arange(T)[None, :]
+    S = xp[i.long()[:, None] + t]                         # S[i, t] = padded x[t + i]
+    sgn = 1.0 if op == "eventually" else -1.0
+    if hard:
+        fill = -sgn * math.inf
+        v = S.masked_fill(~pos[:, None], fill)
+        return v.amax(dim=0) if sgn > 0 else v.amin(dim=0)
+    z = sgn * tau * S + logm[:, None]
+    if hard is None:
+        w = torch.softmax(z, dim=0)
+        return (w * torch.where(pos[:, None], S, torch.zeros_like(S))).sum(dim=0)
+    return sgn * torch.logsumexp(z, dim=0) / tau
+
+
 def evaluate(f, x, hard=True, tau=1.0):
     """Robustness trace of formula tuple ``f`` on one trace ``x`` [T, D] (torch fp64).
     hard=True: min/max; False: logsumexp; None: softmax-weighted min/max."""

@@ -249,6 +249,70 @@ def test_smooth_mask_empty_support():
             assert np.all(g[0] == 0) and np.all(gb[0] == 0)
 
 
+@pytest.mark.parametrize("c", [1.5, 5.0])
+@pytest.mark.parametrize("mode", ["hard", "smooth", "softmax"])
+@pytest.mark.parametrize("op", ["eventually", "always"])
+def test_smooth_mask_support_has_no_cutoff(c, mode, op):
+    """The smooth-mask window of Sec. VI against the unroll over EVERY offset (no support
+    cutoff; tests/masked_reference.py): at c = 1.5 the mask stays above eps = 1e-3 for about
+    4.6 steps past b and at c = 5 for about 1.4, so a support that stopped short of the last
+    positive weight would drop terms.  Values, the signal gradient and d/da, d/db (torch
+    autograd of the unroll) must agree.  Trace 1 ends inside the support (pad reads)."""
+    rng = np.random.default_rng(21)
+    T = 40
+    s = rng.normal(size=(3, T, 1))
+    s[:, :, 0] += np.linspace(0.0, 2.0, T)       # rising: the far edge of the window dominates
+    gout = rng.normal(size=(3, T))
+    bounds = np.array([[[2.3, 9.6]], [[0.4, 31.7]], [[5.0, 5.8]]])
+    hard = {"hard": True, "smooth": False, "softmax": None}[mode]
+    omode = {"hard": HARD, "smooth": SMOOTH, "softmax": oracle.SOFTMAX}[mode]
+    ctor = W.EventuallySm if op == "eventually" else W.AlwaysSm
+    f = ctor(40, 45, x_pred(), slot=0)
+    kw = dict(mode=omode, tau=2.0, mask_c=c, mask_eps=1e-3, exact=True)
+    got = oracle.robustness(f, s, bounds=bounds, **kw)
+    g, gb = oracle.robustness_grad(f, s, gout, bounds=bounds, **kw)
+    for b in range(3):
+        x = torch.tensor(s[b, :, 0], requires_grad=True)
+        a_t = torch.tensor(bounds[b, 0, 0], requires_grad=True)
+        b_t = torch.tensor(bounds[b, 0, 1], requires_grad=True)
+        y = mr.smooth_mask_window(x, a_t, b_t, c, 1e-3, None, op, hard, 2.0)
+        np.testing.assert_allclose(got[b], y.detach().numpy(), rtol=1e-12, atol=1e-12)
+        (y * torch.tensor(gout[b])).sum().backward()
+        np.testing.assert_allclose(g[b, :, 0], x.grad.numpy(), rtol=1e-9, atol=1e-12)
+        if mode == "hard":
+            assert gb[b, 0, 0] == 0 and gb[b, 0, 1] == 0
+        else:
+            np.testing.assert_allclose(gb[b, 0], [a_t.grad.item(), b_t.grad.item()], rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 5])
+def test_norm_predicate_float32_order(D):
+    """Region predicates (Sec. VII-A) at random points whose distances are not exact: the
+    oracle's rounded mode must equal numpy float32 arithmetic in the stated order (difference,
+    scale, square, squares summed left to right, correctly rounded square root, then the
+    radius), bit for bit.  A double-precision sum, another summation order or a fused
+    multiply-add would differ on some of these 2000 points."""
+    rng = np.random.default_rng(100 + D)
+    s = (rng.normal(size=(4, 500, D)) * rng.uniform(0.1, 30.0, size=(4, 1, D))).astype(np.float32)
+    sc = rng.uniform(0.2, 3.0, size=D).astype(np.float32)
+    g = rng.normal(size=D).astype(np.float32) * np.float32(5)
+    r = np.float32(rng.uniform(0.5, 4.0))
+    u = (s[..., 0] - g[0]) * sc[0]
+    q = u * u
+    for d in range(1, D):
+        u = (s[..., d] - g[d]) * sc[d]
+        q = q + u * u
+    mu = np.sqrt(q)
+    assert mu.dtype == np.float32
+    inside = oracle.robustness(W.norm_lt(sc.tolist(), g.tolist(), float(r)), s)
+    np.testing.assert_array_equal(inside, (r - mu).astype(np.float64))
+    outside = oracle.robustness(W.norm_gt(sc.tolist(), g.tolist(), float(r)), s)
+    np.testing.assert_array_equal(outside, (mu - r).astype(np.float64))
+    # the same points through a double-precision distance differ somewhere (the pin has teeth)
+    mu64 = np.sqrt((((s.astype(np.float64) - g) * sc) ** 2).sum(axis=-1)).astype(np.float32)
+    assert D == 1 or np.any(mu64 != mu)
+
+
 def test_predicate_float32_rounding():
     rng = np.random.default_rng(11)
     s = (rng.normal(size=(2, 64, 3)) * 1e3).astype(np.float32)
