@@ -203,7 +203,8 @@ def side_measurements(stl, W, torch, dev, args):
     order = torch.from_numpy(np.argsort(-np.diff(wl["offsets"]), kind="stable").astype(np.int32))
     ph = stl.params("hard")
     rb = stl.RaggedBatch(stl.FormulaSet(fs), torch.from_numpy(wl["signal"]), offs,
-                         torch.from_numpy(wl["formula_id"]), bounds=torch.from_numpy(wl["bounds"]), p=ph, order=order)
+                         torch.from_numpy(wl["formula_id"]), bounds=torch.from_numpy(wl["bounds"]), p=ph, order=order,
+                         tune=True)
     gg = torch.randn(int(wl["offsets"][-1]), device=dev)
     steps_total = int(wl["offsets"][-1])
     ms_one = time_ms(torch, lambda: (rb.forward(), rb.backward(gg)))
@@ -230,17 +231,69 @@ def side_measurements(stl, W, torch, dev, args):
             r.backward(gk)
 
     ms_per = time_ms(torch, per_formula)
+    hbm = peaks()[0]
+
+    def ragged_roofline(ms):
+        # algorithmic bytes per trace-step with D = 4: forward 4D + 4, backward 8D + 4 = 56 B
+        gbs = 56.0 * steps_total / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "bytes_per_trace_step": 56}
+
     out["ragged_config3"] = {"traces": int(len(wl["formula_id"])), "trace_steps": steps_total, "formulas": len(fs),
-                             "one_launch": {"value": steps_total / (ms_one * 1e-3), "ms": ms_one},
-                             "one_launch_graph": {"value": steps_total / (ms_graph * 1e-3), "ms": ms_graph},
-                             "per_formula_launches": {"value": steps_total / (ms_per * 1e-3), "ms": ms_per},
-                             "unit": UNIT, "mode": "hard", "fwd+bwd": True}
+                             "one_launch": {"value": steps_total / (ms_one * 1e-3), "ms": ms_one,
+                                            "roofline": ragged_roofline(ms_one)},
+                             "one_launch_graph": {"value": steps_total / (ms_graph * 1e-3), "ms": ms_graph,
+                                                  "roofline": ragged_roofline(ms_graph)},
+                             "per_formula_launches": {"value": steps_total / (ms_per * 1e-3), "ms": ms_per,
+                                                      "roofline": ragged_roofline(ms_per)},
+                             "unit": UNIT, "mode": "hard", "fwd+bwd": True,
+                             "launch": rb.shapes, "note": "one launch: shapes from stl_set_autotune; per-formula "
+                                                          "launches: the planner's default shapes"}
+    del per, gper, graph
+    for mode in ("smooth", "softmax"):
+        psm = stl.params(mode, tau=10.0)
+        rbs = stl.RaggedBatch(stl.FormulaSet(fs), torch.from_numpy(wl["signal"]), offs,
+                              torch.from_numpy(wl["formula_id"]), bounds=torch.from_numpy(wl["bounds"]), p=psm,
+                              order=order, tune=True)
+        ms_f = time_ms(torch, rbs.forward, steps=2, warmup=1)
+        ms_b = time_ms(torch, lambda: rbs.backward(gg), steps=2, warmup=1)
+        out[f"ragged_config3_{mode}"] = {"value": steps_total / ((ms_f + ms_b) * 1e-3), "unit": UNIT, "fwd_ms": ms_f,
+                                         "bwd_ms": ms_b, "tau": 10.0, "roofline": ragged_roofline(ms_f + ms_b),
+                                         "launch": rbs.shapes,
+                                         "note": "one persistent launch per direction; the smooth Until is O(b) "
+                                                 "per sample (b up to 4000), so the HBM fraction is not its bound"}
+        del rbs
+    out["config2_mining_descent"] = config2_measurement(W)
     if not args.no_plan:
         out["warm_vs_cold"] = plan_measurement(W, args)
     out.update(mining_measurements(W))
     out["interval_trajopt"] = trajopt_measurement()
     out["table3_suite"] = table3_measurement(stl, W, torch, dev)
     return out
+
+
+def config2_measurement(W):
+    """Config 2 at its stated scale: B = 4096 noisy sinusoids of T = 2000, Eventually over a
+    per-trace sigmoid-masked interval (c = 5, eps = 1e-3, tau = 10) with a ~ U[0,100],
+    b = a + U[20,300], and 200 steps of the per-trace interval descent per launch batch (each
+    step: robustness, loss seed, backward with signal and bound gradients, per-trace update)."""
+    from paper_2501_04194_gb300 import mining
+    B, T = 4096, 2000
+    sig, bounds = W.config2_inputs(B=B, T=T, seed=0)
+    mining.per_trace_descent(sig, bounds, steps=5)   # warm-up (plans, caches)
+    r = mining.per_trace_descent(sig, bounds, steps=200)
+    ms = r["ms_per_step"]
+    hbm = peaks()[0]
+    gbs = 20.0 * B * T / (ms * 1e-3) / 1e9   # D = 1: forward 4D + 4, backward 8D + 4
+    width0 = float((bounds[:, 0, 1] - bounds[:, 0, 0]).mean())
+    width = float((r["bounds"][:, 0, 1] - r["bounds"][:, 0, 0]).mean())
+    return {"value": B * T / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": r["steps"],
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "bytes_per_trace_step": 20},
+            "l2": "working set (signal 33 MB, rho, grad_out, grad 33 MB each) is L2-resident across the 200 "
+                  "steps (129 MB L2): the HBM fraction above counts the algorithmic bytes as if from DRAM",
+            "loss_before": r["loss0"], "loss_after": r["loss"], "mean_width_before": width0,
+            "mean_width_after": width}
 
 
 def trajopt_measurement():

@@ -173,7 +173,14 @@ STL_API stl_status stl_robustness(stl_handle h, const float *sig, int64_t B, int
  *   grad_out     [B, T] float32 device
  *   grad_sig     [B, T, D] float32 device, overwritten
  *   grad_bounds  [B, n_slots, 2] float32 device or NULL, overwritten (nonzero only for the
- *                sigmoid-masked operators in smooth mode) */
+ *                sigmoid-masked operators in smooth mode)
+ * Determinism.  STL_HARD: each root gradient is rounded to a 64-bit fixed-point integer
+ * (resolution 2^-29 of the trace's largest |grad_out|) before any addition, so grad_sig is
+ * bit-identical across calls, launch shapes (stl_set_launch, autotuning), segmentations,
+ * stl_robustness_and_backward, the host pipeline and the ragged path.  STL_SMOOTH /
+ * STL_SOFTMAX: adjoints are float sums whose order follows warp scheduling, so two calls may
+ * differ in the last bits (within float32 summation error; grad_bounds likewise, summed
+ * over the segments of a trace). */
 STL_API stl_status stl_robustness_backward(stl_handle h, const float *sig, int64_t B, int64_t T,
                                    const float *bounds, const stl_params *p,
                                    const float *grad_out, float *grad_sig, float *grad_bounds,
@@ -250,16 +257,18 @@ STL_API stl_status stl_robustness_host_pipelined(stl_handle h, const float *sig,
  * Interval semantics per trace as in stl_robustness (Sec. IV-E: intervals are data). */
 
 /* Group compiled formulas (same D; 1 <= n_formulas <= 65536) for ragged launches.  The set
- * refers to the handles, which must outlive it.  stl_set_prepare copies every formula's program
- * into one device table (about 10 KB per formula), allocated on the first prepare. */
+ * refers to the handles, which must outlive it.  stl_set_prepare copies every formula's programs
+ * into one device table (about 10 KB per program), allocated on the first prepare. */
 STL_API stl_status stl_set_create(const stl_handle *formulas, int32_t n_formulas, stl_set_handle *out);
 STL_API void stl_set_destroy(stl_set_handle s);
 
 /* Prepare the set for up to n_traces traces of at most T_max samples with semantics p, for
- * the forward (backward = 0) or backward (1) launch: plans every formula and uploads the
- * per-formula program table to the device (the only allocation of the ragged path, freed by
- * stl_set_destroy).  Returns the workspace size the matching ragged calls need.  Host-side,
- * synchronous; call it before any stream capture. */
+ * the forward (backward = 0) or backward (1) launch: plans every formula for length buckets
+ * T_max, T_max/2, T_max/4, ... (down to 1024 samples, at most 6 and at most 8192 programs in
+ * all) and uploads the program table to the device (the only allocation of the ragged path,
+ * freed by stl_set_destroy).  Each trace runs the plan of the smallest bucket that holds it.
+ * Returns the workspace size the matching ragged calls need.  Host-side, synchronous; call it
+ * before any stream capture. */
 STL_API stl_status stl_set_prepare(stl_set_handle s, int64_t n_traces, int64_t T_max, const stl_params *p,
                                    int32_t backward, size_t *workspace_bytes);
 
@@ -283,8 +292,26 @@ STL_API stl_status stl_robustness_ragged_backward(stl_set_handle s, const float 
                                                   float *grad_bounds, void *workspace, size_t workspace_bytes,
                                                   void *stream);
 
-/* Sticky device-side status of the current device (STL_OK or STL_ERR_DEVICE_CHECK);
- * synchronises `stream`, then reads and clears the word. */
+/* Autotuner of a formula set (the paper's static-graph batching, Sec. IV-E, over uneven
+ * traces): times candidate launch shapes -- CTA size 64 / 256 / 512 (64 only for T_max <= 8192)
+ * x tile 4, 7 or 14 samples per thread; the tile is the chunk of samples each streaming step
+ * advances, i.e. how long windows are cut into shared-memory chunks -- on the caller's ragged
+ * batch for one direction (backward = 0: out is rho [sum T]; 1: grad_out [sum T] and out =
+ * grad_sig [sum T, D]), keeps the fastest in the set and leaves the set prepared with it
+ * (as stl_set_prepare, whose workspace size it returns in *workspace_bytes).  Each candidate
+ * runs in a temporary workspace that the call allocates and frees: a setup call, synchronous,
+ * to be made before any stream capture.  STL_TUNE_CACHE (see stl_autotune) caches the result
+ * under a key of the set's formulas, D, slots, semantics, direction and the log2 buckets of
+ * n_traces and T_max.  best_ms: mean time of the winner (-1 when taken from the cache). */
+STL_API stl_status stl_set_autotune(stl_set_handle s, int64_t n_traces, int64_t T_max, const stl_params *p,
+                                    int32_t backward, const float *sig, const int64_t *offsets,
+                                    const int32_t *formula_id, const int32_t *order, const float *bounds,
+                                    int32_t n_slots, const float *grad_out, float *out, float *grad_bounds,
+                                    void *stream, stl_launch *best, float *best_ms, size_t *workspace_bytes);
+
+/* Sticky device-side status of the current device: STL_OK, STL_ERR_DEVICE_CHECK (invalid
+ * per-trace data) or STL_ERR_TIMEOUT (a bounded device-side wait gave up, e.g. in the tensor-core
+ * GEMM of stl_plan.h); synchronises `stream`, then reads and clears the word. */
 STL_API stl_status stl_get_device_status(void *stream, int32_t *status);
 
 STL_API const char *stl_status_string(int32_t status);

@@ -37,6 +37,16 @@ STL_API stl_status stl_mining_seed(const float *rho, int64_t N, int32_t T, float
 STL_API stl_status stl_mining_update(float *theta, const float *gbounds, int64_t N, int32_t n_slots, int32_t slot,
                                      int32_t T, float lr, float gamma, float *bounds, void *stream);
 
+/* Per-trace interval descent (the parameter-mining descent with one learnable interval per
+ * trace, Sec. VI): every trace n takes one gradient step on its own bounds (a_n, b_n), in steps,
+ * for the loss  max(-rho_n(0), 0) - gamma (b_n - a_n):
+ *   a_n -= lr (scale gbounds[n, slot, 0] + gamma),  b_n -= lr (scale gbounds[n, slot, 1] - gamma),
+ * then 0 <= a_n <= a_cap, a_n + min_width <= b_n <= b_cap.  scale undoes the 1/N of
+ * stl_mining_seed (scale = N).  bounds, gbounds: float32 [N, n_slots, 2]. */
+STL_API stl_status stl_mining_update_traces(float *bounds, const float *gbounds, int64_t N, int32_t n_slots,
+                                            int32_t slot, float lr, float gamma, float scale, float a_cap,
+                                            float b_cap, float min_width, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,8 +75,9 @@ STL_API stl_status stl_trajopt_step(float *u, float *mu, float *vu, float *theta
                                     float *bounds, void *stream);
 
 /* ---- BF16 matrix products and the pieces of an MLP training step ----
- * C[M, N] = op(A) op(B) (+ bias[N]) (then max(., 0) when relu), FP32 accumulation on the
- * tensor cores (warp-level BF16 MMA).  op(A) is A [M, K] (lda >= K) or, with trans_a, A^T for
+ * C[M, N] = op(A) op(B) (+ bias[N]) (then max(., 0) when relu), BF16 products accumulated in
+ * FP32 on the 5th-generation tensor cores (tcgen05.mma kind::f16, the accumulator in tensor
+ * memory, 128 x 128 tiles, one CTA each).  op(A) is A [M, K] (lda >= K) or, with trans_a, A^T for
  * A [K, M] (lda >= M); op(B) is B [K, N] (ldb >= N) or, with trans_b, B^T for B [N, K]
  * (ldb >= K); all row-major.  c_f32 and/or c_bf16 [M, N] (ldc >= N) receive the result; either
  * may be NULL, not both.  bias may be NULL.  M, N, K in [1, 2^20]. */

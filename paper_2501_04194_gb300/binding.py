@@ -305,6 +305,10 @@ class FormulaSet:
         lib.stl_robustness_ragged_backward.argtypes = [vp, vp, vp, vp, vp, i64, vp, i32, ctypes.POINTER(StlParams),
                                                        vp, vp, vp, vp, sz, vp]
         lib.stl_robustness_ragged_backward.restype = i32
+        lib.stl_set_autotune.argtypes = [vp, i64, i64, ctypes.POINTER(StlParams), i32, vp, vp, vp, vp, vp, i32, vp, vp,
+                                         vp, vp, ctypes.POINTER(StlLaunch), ctypes.POINTER(ctypes.c_float),
+                                         ctypes.POINTER(sz)]
+        lib.stl_set_autotune.restype = i32
         lib._set_ready = True
 
     @property
@@ -315,6 +319,18 @@ class FormulaSet:
         n = ctypes.c_size_t()
         check(load().stl_set_prepare(self._h, n_traces, T_max, ctypes.byref(p), int(backward), ctypes.byref(n)))
         return int(n.value)
+
+    def autotune(self, n_traces, T_max, p: StlParams, backward, sig_ptr, off_ptr, fid_ptr, order_ptr, bounds_ptr,
+                 gout_ptr, out_ptr, gb_ptr, stream):
+        """stl_set_autotune: time the candidate launch shapes on this batch, keep the fastest and
+        leave the set prepared with it.  Returns (workspace bytes, (threads, tile), best ms)."""
+        best = StlLaunch()
+        ms = ctypes.c_float()
+        n = ctypes.c_size_t()
+        check(load().stl_set_autotune(self._h, n_traces, T_max, ctypes.byref(p), int(backward), sig_ptr, off_ptr,
+                                      fid_ptr, order_ptr, bounds_ptr, self.n_slots, gout_ptr, out_ptr, gb_ptr, stream,
+                                      ctypes.byref(best), ctypes.byref(ms), ctypes.byref(n)))
+        return int(n.value), (int(best.threads), int(best.tile)), float(ms.value)
 
     def __del__(self):
         h = getattr(self, "_h", None)

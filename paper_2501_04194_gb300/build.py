@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstl.so")
-SOURCES = [f"stl_kern_{nt}_{d}{m}{r}.cu" for nt in (64, 256, 512) for d in "fb" for m in "hs" for r in ("", "_r")] + ["stl_kernels.cu", "stl_capi.cu", "stl_noalloc.cu", "stl_plan.cu", "stl_mining.cu"]
+SOURCES = [f"stl_kern_{nt}_{d}{m}{r}.cu" for nt in (64, 256, 512) for d in "fb" for m in "hs" for r in ("", "_r")] + ["stl_kernels.cu", "stl_capi.cu", "stl_noalloc.cu", "stl_plan.cu", "stl_gemm.cu", "stl_mining.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

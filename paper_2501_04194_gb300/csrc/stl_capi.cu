@@ -82,10 +82,13 @@ struct SetState {
   bool ready = false;
   long long T_max = 0;
   stl_params p{};
-  KProgram *dtable = nullptr;   // device copy (allocated at prepare time)
+  KProgram *dtable = nullptr;   // device copy (allocated at prepare time): [formula][bucket]
+  size_t table_len = 0;         // programs the device table holds
+  int n_buckets = 1;
   int threads = 256, grid = 1, smem_words = 0, gwords = 0, ut_len = 0;
   long long ut_off = 0;
   size_t ws_bytes = 0;
+  stl_launch shape{};           // threads / tile of the launch (zero: the planner's choice)
 };
 
 struct stl_program_set {
@@ -119,7 +122,7 @@ int window_lo(const stl_node &nd) {
 
 // Compute node geometry, ring layout and launch shape for one call.
 stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_params &p, bool bwd, Plan &pl,
-                     int force_threads = 0) {
+                     int force_threads = 0, int force_tile = 0) {
   stl_program hv = *hp;               // shallow copy carrying this direction's launch shape
   hv.launch = hp->launch_dir[bwd ? 1 : 0];
   const stl_program *h = &hv;
@@ -159,6 +162,13 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
       else { lo[c] = lo[i]; hi[c] = hi[i]; }
     }
   }
+  // A node never stores samples at or past T (those reads go to the per-node cells), so its
+  // live span hi - lo need not exceed T: long nested windows on short traces (ragged length
+  // buckets) keep buffers of at most tile + T samples.  Hard forward plans that may take the
+  // direct-read passes keep the full span (they fill pads past T into the buffers).
+  const bool may_lean = !bwd && p.mode == STL_HARD;
+  if (!may_lean)
+    for (int i = 0; i < n; ++i) hi[i] = (int)std::min<long long>(hi[i], (long long)lo[i] + T);
   int lp = 1 << 30;
   for (int i = 0; i < n; ++i) if (is_pred(h->nodes[i].op)) lp = std::min(lp, lo[i]);
   if (lp == (1 << 30)) lp = 0;
@@ -186,7 +196,7 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
                 : h->launch.threads ? h->launch.threads
                 : T <= 2 * 64 * win_r ? 64
                 : (bwd ? 512 : 256);
-  int tile = h->launch.tile ? h->launch.tile : threads * win_r;
+  int tile = force_tile ? force_tile : h->launch.tile ? h->launch.tile : threads * win_r;
   tile = std::min(tile, round_up(T, 32));
   tile = std::max(32, round_up(tile, 32));
 
@@ -220,9 +230,11 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
       const int cap = round_up((long long)tl + hi[i] - lo[i], 4);
       int nrings = 1;
       if (bwd) {
-        // hard backward: only predicates keep an adjoint (selection walk), temporal nodes
-        // keep their selected samples; smooth backward: every node keeps an adjoint
-        if (soft_mode(p.mode) || is_pred(nd.op)) nrings += 1;
+        // hard backward: only predicates keep an adjoint (selection walk; 64-bit fixed-point
+        // sums, two words per sample), temporal nodes keep their selected samples; smooth
+        // backward: every node keeps a float adjoint
+        if (soft_mode(p.mode)) nrings += 1;
+        else if (is_pred(nd.op)) nrings += 2;
         if (p.mode == STL_HARD && is_temporal(nd.op)) nrings += 1;
         // softmax windows keep each output's log-normaliser for their adjoint
         if (p.mode == STL_SOFTMAX && is_window(nd.op)) nrings += 1;
@@ -251,11 +263,21 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
   };
   std::vector<int> space;
   int smem_words = 0, gwords = 0;
-  // shrink the tile while rings would have to leave shared memory
+  // shrink the tile while rings would have to leave shared memory -- but only if a smaller
+  // tile avoids the spill: when even 256-sample steps spill (long nested windows), a large
+  // tile amortises the per-step cost and the spilled rings stay L2-resident
+  const bool fixed_tile = h->launch.tile || force_tile;
+  bool spill_unavoidable = false;
+  if (!fixed_tile) {
+    std::vector<int> sp;
+    int sw = 0, gw = 0;
+    const int t_min = std::min(tile, 256);
+    spill_unavoidable = layout(t_min, sp, sw, gw) && gw > 0;
+  }
   for (;;) {
     bool ok = layout(tile, space, smem_words, gwords);
     if (!ok) return fail(STL_ERR_UNSUPPORTED, "formula scratch does not fit in shared memory");
-    if (gwords == 0 || tile <= 256 || h->launch.tile) break;
+    if (gwords == 0 || tile <= 256 || fixed_tile || spill_unavoidable) break;
     tile = std::max(256, round_up(tile / 2, 32));
     if (!force_threads && !h->launch.threads && tile < 512 * win_r) threads = 256;
   }
@@ -289,7 +311,8 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
     k.adj_off = -1;
     k.aux_off = -1;
     if (bwd) {
-      if (soft_mode(p.mode) || is_pred(nd.op)) { k.adj_off = off; off += pw; }
+      if (soft_mode(p.mode)) { k.adj_off = off; off += pw; }
+      else if (is_pred(nd.op)) { k.adj_off = off; off += 2 * pw; }   // 64-bit fixed point
       if ((p.mode == STL_HARD && is_temporal(nd.op)) || (p.mode == STL_SOFTMAX && is_window(nd.op))) {
         k.aux_off = off;
         off += pw;
@@ -740,7 +763,7 @@ stl_status stl_get_device_status(void *stream, int32_t *status) {
   int st = 0;
   int e = stl_read_clear_status(stream, &st);
   if (e) return cuda_fail(e, "reading the device status");
-  *status = st ? STL_ERR_DEVICE_CHECK : STL_OK;
+  *status = st == 2 ? STL_ERR_TIMEOUT : st ? STL_ERR_DEVICE_CHECK : STL_OK;
   return STL_OK;
 }
 
@@ -829,22 +852,31 @@ stl_status stl_set_prepare(stl_set_handle s, int64_t n_traces, int64_t T_max, co
   if (n_traces < 1 || T_max < 1 || T_max > (1LL << 30)) return fail(STL_ERR_INVALID_ARG, "need n_traces >= 1 and T_max in [1, 2^30]");
   SetState &st = s->st[backward ? 1 : 0];
   const int nf = (int)s->formulas.size();
-  std::vector<KProgram> progs(nf);
-  const int threads = T_max <= 2 * 64 * 7 ? 64 : backward ? 512 : 256;
+  // length buckets: every formula is planned for traces of at most T_max, T_max/2, T_max/4, ...
+  // (down to 1024 samples, at most STL_MAX_BUCKETS plans); a trace runs the plan of the
+  // smallest bucket that holds it, whose buffers and tile fit its length
+  int nb = 1;
+  while (nb < STL_MAX_BUCKETS && (T_max >> nb) >= 1024 && (long long)nf * (nb + 1) <= 8192) ++nb;
+  std::vector<KProgram> progs((size_t)nf * nb);
+  const int threads = st.shape.threads ? st.shape.threads : T_max <= 2 * 64 * 7 ? 64 : backward ? 512 : 256;
   int smem = 0, gwords = 0, ut_len = 0;
   for (int k = 0; k < nf; ++k) {
     stl_status e = check_params(s->formulas[k], p);
     if (e) return e;
-    Plan pl;
-    e = make_plan(s->formulas[k], n_traces, T_max, *p, backward != 0, pl, threads);
-    if (e) return e;
-    pl.P.n_slots = s->n_slots;          // one bounds array for the whole set
-    pl.P.seg = (int)T_max;
-    pl.P.segs_per_trace = 1;
-    progs[k] = pl.P;
-    smem = std::max(smem, pl.P.smem_words);
-    gwords = std::max(gwords, pl.P.gwords);
-    ut_len = std::max(ut_len, pl.P.ut_len);
+    for (int bk = 0; bk < nb; ++bk) {
+      const long long Tb = T_max >> bk;
+      Plan pl;
+      e = make_plan(s->formulas[k], n_traces, Tb, *p, backward != 0, pl, threads,
+                    st.shape.tile ? (int)std::min<long long>(st.shape.tile, ((Tb + 31) / 32) * 32) : 0);
+      if (e) return e;
+      pl.P.n_slots = s->n_slots;          // one bounds array for the whole set
+      pl.P.seg = (int)Tb;
+      pl.P.segs_per_trace = 1;
+      progs[(size_t)k * nb + bk] = pl.P;
+      smem = std::max(smem, pl.P.smem_words);
+      gwords = std::max(gwords, pl.P.gwords);
+      ut_len = std::max(ut_len, pl.P.ut_len);
+    }
   }
   int sms = 0, bps = 0;
   int e = stl_num_sms(&sms);
@@ -856,13 +888,19 @@ stl_status stl_set_prepare(stl_set_handle s, int64_t n_traces, int64_t T_max, co
   for (auto &P : progs) {
     P.smem_words = smem;   // every program sees the launch's shared arena
   }
-  if (!st.dtable) {
-    cudaError_t ce = cudaMalloc((void **)&st.dtable, sizeof(KProgram) * (size_t)nf);
-    if (ce != cudaSuccess) { st.dtable = nullptr; return cuda_fail((int)ce, "cudaMalloc(program table)"); }
+  if (st.dtable && st.table_len < progs.size()) {
+    cudaFree(st.dtable);
+    st.dtable = nullptr;
   }
-  cudaError_t ce = cudaMemcpy(st.dtable, progs.data(), sizeof(KProgram) * nf, cudaMemcpyHostToDevice);
+  if (!st.dtable) {
+    cudaError_t ce = cudaMalloc((void **)&st.dtable, sizeof(KProgram) * progs.size());
+    if (ce != cudaSuccess) { st.dtable = nullptr; return cuda_fail((int)ce, "cudaMalloc(program table)"); }
+    st.table_len = progs.size();
+  }
+  cudaError_t ce = cudaMemcpy(st.dtable, progs.data(), sizeof(KProgram) * progs.size(), cudaMemcpyHostToDevice);
   if (ce != cudaSuccess) return cuda_fail((int)ce, "cudaMemcpy(program table)");
   st.threads = threads;
+  st.n_buckets = nb;
   st.grid = (int)grid;
   st.smem_words = smem;
   st.gwords = gwords;
@@ -919,6 +957,7 @@ static stl_status ragged_launch(stl_set_handle s, SetState &st, const float *sig
   A.n_traces = n_traces;
   A.n_formulas = (int)s->formulas.size();
   A.T_max = st.T_max;
+  A.n_buckets = st.n_buckets;
   A.gwords = st.gwords;
   A.ut_len = st.ut_len;
   A.ut_off = st.ut_off;
@@ -1079,6 +1118,101 @@ stl_status stl_autotune(stl_handle h, const float *sig, int64_t B, int64_t T, co
     return fail(STL_ERR_WORKSPACE, "no candidate launch shape fits the given workspace");
   }
   h->launch_dir[bwd ? 1 : 0] = best_l;
+  *best = best_l;
+  if (best_ms) *best_ms = best_t;
+  if (cache && *cache) cache_store(cache, key, best_l, best_t);
+  return STL_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ ragged-set autotuner
+namespace {
+std::string set_tune_key(const stl_program_set *s, long long n, long long T_max, const stl_params &p, bool bwd) {
+  uint64_t x = 1469598103934665603ULL;
+  for (const stl_program *h : s->formulas) {
+    x = fnv1a(h->nodes.data(), h->nodes.size() * sizeof(stl_node), x);
+    x = fnv1a(h->w.data(), h->w.size() * sizeof(float), x);
+  }
+  char buf[160];
+  snprintf(buf, sizeof buf, "set%016llx-F%zu-D%d-S%d-m%d-%s-N%d-T%d", (unsigned long long)x, s->formulas.size(), s->D,
+           s->n_slots, p.mode, bwd ? "bwd" : "fwd", log2_bucket(n), log2_bucket(T_max));
+  return buf;
+}
+}  // namespace
+
+extern "C" {
+
+stl_status stl_set_autotune(stl_set_handle s, int64_t n_traces, int64_t T_max, const stl_params *p, int32_t backward,
+                            const float *sig, const int64_t *offsets, const int32_t *formula_id, const int32_t *order,
+                            const float *bounds, int32_t n_slots, const float *grad_out, float *out,
+                            float *grad_bounds, void *stream, stl_launch *best, float *best_ms,
+                            size_t *workspace_bytes) {
+  if (!s || !p || !best || !workspace_bytes) return fail(STL_ERR_INVALID_ARG, "NULL argument");
+  if (n_traces < 1) return fail(STL_ERR_INVALID_ARG, "nothing to tune for n_traces < 1");
+  const bool bwd = backward != 0;
+  if (!sig || !offsets || !formula_id || !out || (bwd && !grad_out))
+    return fail(STL_ERR_INVALID_ARG, "input / output buffers are NULL");
+  SetState &st = s->st[bwd ? 1 : 0];
+  const char *cache = std::getenv("STL_TUNE_CACHE");
+  const std::string key = set_tune_key(s, n_traces, T_max, *p, bwd);
+  stl_launch hit{};
+  if (cache && *cache && cache_lookup(cache, key, &hit)) {
+    st.shape = hit;
+    *best = hit;
+    if (best_ms) *best_ms = -1.f;
+    return stl_set_prepare(s, n_traces, T_max, p, backward, workspace_bytes);
+  }
+  const stl_launch saved = st.shape;
+  std::vector<stl_launch> cands;
+  for (int nt : {64, 256, 512})
+    for (int mult : {4, 7, 14}) {
+      if (nt == 64 && T_max > 8192) continue;   // 64-thread CTAs are for short traces
+      stl_launch l{};
+      l.threads = nt;
+      l.tile = std::max(256, (nt * mult / 32) * 32);
+      cands.push_back(l);
+    }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(STL_ERR_CUDA, "cudaEventCreate failed");
+  float best_t = 1e30f;
+  stl_launch best_l = saved;
+  bool any = false;
+  for (const stl_launch &c : cands) {
+    st.shape = c;
+    size_t need = 0;
+    if (stl_set_prepare(s, n_traces, T_max, p, backward, &need) != STL_OK) continue;
+    void *ws = nullptr;
+    if (cudaMalloc(&ws, need) != cudaSuccess) { cudaGetLastError(); continue; }
+    auto run = [&]() {
+      return bwd ? stl_robustness_ragged_backward(s, sig, offsets, formula_id, order, n_traces, bounds, n_slots, p,
+                                                  grad_out, out, grad_bounds, ws, need, stream)
+                 : stl_robustness_ragged(s, sig, offsets, formula_id, order, n_traces, bounds, n_slots, p, out, ws,
+                                         need, stream);
+    };
+    bool ok = run() == STL_OK;
+    if (ok) {
+      cudaEventRecord(e0, (cudaStream_t)stream);
+      for (int r = 0; r < 2 && ok; ++r) ok = run() == STL_OK;
+      cudaEventRecord(e1, (cudaStream_t)stream);
+      ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+    }
+    cudaStreamSynchronize((cudaStream_t)stream);
+    cudaFree(ws);
+    if (!ok) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 2.f;
+    any = true;
+    if (ms < best_t) { best_t = ms; best_l = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  st.shape = any ? best_l : saved;
+  stl_status r = stl_set_prepare(s, n_traces, T_max, p, backward, workspace_bytes);
+  if (r) return r;
+  if (!any) return fail(STL_ERR_UNSUPPORTED, "no candidate launch shape ran");
   *best = best_l;
   if (best_ms) *best_ms = best_t;
   if (cache && *cache) cache_store(cache, key, best_l, best_t);

@@ -11,6 +11,7 @@
 #define STL_MAX_PRED 32
 #define STL_LEAN_MIN_SAMPLES 4096   // hard forward node steps this long take the direct-read passes
 #define STL_BUF_BACK 16    // words after every node buffer of such plans (unclamped over-reads)
+#define STL_MAX_BUCKETS 6  // ragged sets: length buckets (plans) per formula
 
 // Node layout after compilation (per launch: the ring geometry depends on tile and bounds).
 struct KNode {
@@ -23,7 +24,8 @@ struct KNode {
   int lo, hi;          // live offsets relative to the root step [t0, t1): [t0+lo, t1+hi)
   int cap;             // buffer length in samples (>= tile + hi - lo, multiple of 4)
   int val_off;         // word offsets of the buffers (shared arena or per-CTA global slice)
-  int adj_off;         // -1 if the node keeps no adjoint buffer
+  int adj_off;         // -1 if the node keeps no adjoint buffer (hard backward: 2 words per
+                       // sample, a 64-bit fixed-point accumulator; smooth: 1 float)
   int aux_off;         // -1 if the node keeps no selected-source buffer
   int space;           // 0: shared memory, 1: global workspace
   int tab_off;         // smooth-mask weight tables (3 x tab_len words in shared memory), -1 if none
@@ -74,6 +76,7 @@ struct NodeRt {
   float lastval;       // value at sample T-1 (pad reads)
   int lastaux;         // recorded source at sample T-1
   float padadj;        // adjoint accumulated for sample T-1
+  unsigned long long padfx;   // hard backward: the same as a 64-bit fixed-point sum
   float ga, gb;        // smooth-mask bound-gradient accumulators
   float *tab;          // smooth-mask tables: m_i, dm_i/da, dm_i/db for i in [ia, ib]
   int band_a, band_b;  // bound gradients use offsets [ia, band_a] and [band_b, ib]
@@ -100,6 +103,7 @@ struct LaunchArgs {
   long long n_traces;
   int n_formulas;
   long long T_max;              // longest trace the table was prepared for
+  int n_buckets;                // programs per formula: planned for T_max >> 0, 1, ...
   int gwords;                   // global buffer words per CTA (max over formulas)
   int ut_len;
   long long ut_off;

@@ -375,7 +375,62 @@ struct Cta {
   int t0, t1;          // current root step [t0, t1)
   int root;
   float *out_row;      // forward: out + b*T
+  float fx1, fx2;      // hard backward: fixed-point scale 2^k = fx1 * fx2 of this work item
+  float ifx1, ifx2;    // and its inverse
 };
+
+// Hard-mode adjoints are summed in 64-bit fixed point, so that the result depends neither on
+// the order in which warps deposit nor on the launch shape (integer addition is associative;
+// float addition is not).  Per trace, k is chosen from the largest root gradient M of the
+// whole trace: M * 2^k < 2^30, so a sum of up to 2^30 deposits (T <= 2^30) stays below 2^61,
+// and the resolution 2^-k is below 2^-29 M.  Each root gradient is scaled by 2^k (exact: two
+// powers of two, each representable) and rounded to an integer before any addition; a read
+// converts the integer sum to float once and scales it back (exact).  The gradient is thus
+// the float rounding of sum_q round(g_q 2^k) 2^-k, bit-identical for every tile, CTA size,
+// segmentation and deposit order.
+__device__ __forceinline__ void set_fix_scale(Cta &C, float M) {
+  const int k = M > 0.f ? 29 - ilogbf(M) : 0;
+  const int k1 = k / 2, k2 = k - k1;
+  C.fx1 = ldexpf(1.f, k1);
+  C.fx2 = ldexpf(1.f, k2);
+  C.ifx1 = ldexpf(1.f, -k1);
+  C.ifx2 = ldexpf(1.f, -k2);
+}
+__device__ __forceinline__ long long to_fix(const Cta &C, float v) { return __float2ll_rn((v * C.fx1) * C.fx2); }
+__device__ __forceinline__ float from_fix(float ifx1, float ifx2, unsigned long long a) {
+  return (__ll2float_rn((long long)a) * ifx1) * ifx2;
+}
+// largest |g| over a trace's root gradients (float4 loads, several in flight per thread),
+// kept in L2 with an evict-last hint: the selection walk reads them again step by step
+__device__ __forceinline__ float trace_gmax(const float *g, int T) {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  const int NT = blockDim.x;
+  const int head = min((int)(((16 - (reinterpret_cast<uintptr_t>(g) & 15)) & 15) >> 2), T);
+  float m = 0.f;
+  for (int q = threadIdx.x; q < head; q += NT) m = fmaxf(m, fabsf(g[q]));
+  const float4 *g4 = reinterpret_cast<const float4 *>(g + head);
+  const int nv = (T - head) >> 2;
+#pragma unroll 4
+  for (int i = threadIdx.x; i < nv; i += NT) {
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(g4 + i), "l"(pol));
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+  for (int q = head + 4 * nv + threadIdx.x; q < T; q += NT) m = fmaxf(m, fabsf(g[q]));
+  return m;
+}
+
+__device__ __forceinline__ void fix_add(unsigned long long *p, long long v) {
+  if (__isShared(p)) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+  } else {
+    atomicAdd(p, (unsigned long long)v);
+  }
+}
 
 __device__ __forceinline__ int frontier(const Cta &C, int n) {
   const int e = C.t1 + C.rt[n].hi;
@@ -1782,6 +1837,7 @@ __device__ void setup_geometry(Cta &C, const float *bounds, float *ws_cta, char 
       r.lastval = 0.f;
       r.lastaux = -1;
       r.padadj = 0.f;
+      r.padfx = 0ull;
       r.ga = r.gb = 0.f;
       r.base = 0;
       r.op = nd.op;
@@ -1848,7 +1904,7 @@ __device__ __forceinline__ void move_down(float *p, int src, int len) {
 }
 
 // end of a step: keep the live samples [t1 + lo, t1 + hi) at the front of every buffer
-template <bool BWD>
+template <bool BWD, int AW>   // AW: adjoint words per sample (2: hard fixed point)
 __device__ void shift_buffers(const Cta &C, int tile) {
   const KProgram &P = *C.P;
   int max_span = 0;
@@ -1862,7 +1918,10 @@ __device__ void shift_buffers(const Cta &C, int tile) {
       const int len = min(tile, span - c0);
       move_down(r.val + c0, tile, len);
       if (BWD) {
-        if (r.adj) move_down(r.adj + c0, tile, len);
+        if (r.adj) {
+          if (AW == 1) move_down(r.adj + c0, tile, len);
+          else move_down(r.adj + AW * c0, AW * tile, AW * len);
+        }
         if (r.aux) move_down(reinterpret_cast<float *>(r.aux) + c0, tile, len);
       }
     }
@@ -1872,7 +1931,7 @@ __device__ void shift_buffers(const Cta &C, int tile) {
     // the next step's new samples start with a zero adjoint
     for (int n = 0; n < P.n; ++n) {
       const NodeRt &r = C.rt[n];
-      if (r.adj) zero_words(r.adj, r.hi - r.lo, r.cap);
+      if (r.adj) zero_words(r.adj, AW * (r.hi - r.lo), AW * r.cap);
     }
     __syncthreads();
   }
@@ -1881,19 +1940,24 @@ __device__ void shift_buffers(const Cta &C, int tile) {
 // ------------------------------------------------------------------ hard-mode selection walk
 // In hard semantics the gradient of a root sample flows to exactly one predicate sample (or
 // nowhere): follow the recorded selections down the tree and deposit the root gradient
-// there.  One pass over the root samples of the step, with no barrier between levels;
-// internal nodes keep no adjoint at all.
+// there (64-bit fixed point: the sums do not depend on the order of the deposits).  One pass
+// over the root samples of the step, with no barrier between levels; internal nodes keep no
+// adjoint at all.
 __device__ void hard_walk(const Cta &C, const float *__restrict__ gout_row, int t0, int t1) {
   const NodeRt *rt = C.rt;
   const int T = C.T;
   const int lane = threadIdx.x & 31;
   const int NT = blockDim.x;
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
   for (int qb0 = t0; qb0 < t1; qb0 += NT * BATCH) {
     float gb[BATCH];
 #pragma unroll
     for (int k = 0; k < BATCH; ++k) {
       const int q = qb0 + k * NT + threadIdx.x;
-      gb[k] = q < t1 ? __ldg(gout_row + q) : 0.f;
+      gb[k] = 0.f;
+      if (q < t1)   // last use of the root gradient (it was kept in L2 for this read)
+        asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(gb[k]) : "l"(gout_row + q), "l"(pol));
     }
 #pragma unroll 1
     for (int k = 0; k < BATCH; ++k) {
@@ -1926,24 +1990,25 @@ __device__ void hard_walk(const Cta &C, const float *__restrict__ gout_row, int 
           else { n = r.c0; j = key; }
         }
       }
-      // runs of consecutive lanes ending on the same predicate sample add once
+      // runs of consecutive lanes ending on the same predicate sample add once (integer sums:
+      // exact, so the result does not depend on how samples fall into warps)
+      long long v = pk >= 0 ? to_fix(C, g) : 0;
       const int pj = __shfl_up_sync(FULL, j, 1), pp = __shfl_up_sync(FULL, pk, 1);
       const bool head = lane == 0 || pj != j || pp != pk;
       const unsigned heads = __ballot_sync(FULL, head);
-      float s = g;
       if (heads != FULL) {   // some lanes share a target: segmented sum over the runs
         const int rid = __popc(heads & (0xffffffffu >> (31 - lane)));
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-          const float sv = __shfl_down_sync(FULL, s, off);
+          const long long sv = __shfl_down_sync(FULL, v, off);
           const int rv = __shfl_down_sync(FULL, rid, off);
-          if (lane + off < 32 && rv == rid) s += sv;
+          if (lane + off < 32 && rv == rid) v += sv;
         }
       }
-      if (head && pk >= 0 && s != 0.f) {
+      if (head && pk >= 0 && v != 0) {
         const NodeRt &r = rt[C.P->pred[pk]];
-        if (j >= T - 1) buf_add(const_cast<float *>(&r.padadj), s);
-        else buf_add(&r.adj[j - (C.t0 + r.lo)], s);
+        if (j >= T - 1) fix_add(const_cast<unsigned long long *>(&r.padfx), v);
+        else fix_add(reinterpret_cast<unsigned long long *>(r.adj) + (j - (C.t0 + r.lo)), v);
       }
     }
   }
@@ -1974,9 +2039,16 @@ __device__ __forceinline__ float norm_grad_dim(const KProgram &P, int k, const f
   return q > 0.f ? (nd.op == OP_NGT ? a : -a) * rsqrtf(q) * sg[d] * ud : 0.f;
 }
 
-template <int DD>
+// predicate adjoint k at sample j: a float (smooth) or a fixed-point sum (hard)
+template <bool FX>
+__device__ __forceinline__ float padj_at(float *const *padj, int k, int idx, float i1, float i2) {
+  if constexpr (FX) return from_fix(i1, i2, reinterpret_cast<const unsigned long long *>(padj[k])[idx]);
+  else return padj[k][idx];
+}
+
+template <int DD, bool FX>
 __device__ __forceinline__ void signal_gradient_d(const KProgram &P, float *const *padj, const float *xs, float *gs,
-                                                  int pst, int j0, int j1) {
+                                                  int pst, int j0, int j1, float i1, float i2) {
   constexpr int SB = 4;   // samples per thread per iteration (independent loads in flight)
   const int NT = blockDim.x;
   for (int base = j0 + threadIdx.x; base < j1; base += NT * SB) {
@@ -1986,14 +2058,13 @@ __device__ __forceinline__ void signal_gradient_d(const KProgram &P, float *cons
 #pragma unroll
       for (int d = 0; d < DD; ++d) acc[s][d] = 0.f;
     for (int k = 0; k < P.npred; ++k) {
-      const float *pa = padj[k] - pst;
       float w[DD], a[SB];
 #pragma unroll
       for (int d = 0; d < DD; ++d) w[d] = P.pw[k * STL_MAX_D + d];
 #pragma unroll
       for (int s = 0; s < SB; ++s) {
         const int j = base + s * NT;
-        a[s] = j < j1 ? pa[j] : 0.f;
+        a[s] = j < j1 ? padj_at<FX>(padj, k, j - pst, i1, i2) : 0.f;
       }
 #pragma unroll
       for (int s = 0; s < SB; ++s)
@@ -2006,7 +2077,7 @@ __device__ __forceinline__ void signal_gradient_d(const KProgram &P, float *cons
       for (int s = 0; s < SB; ++s) {
         const int j = base + s * NT;
         if (j >= j1) continue;
-        const float a = padj[k][j - pst];
+        const float a = padj_at<FX>(padj, k, j - pst, i1, i2);
         if (a == 0.f) continue;
 #pragma unroll
         for (int d = 0; d < DD; ++d) acc[s][d] += norm_grad_dim(P, k, xs + (size_t)j * DD, DD, d, a);
@@ -2023,6 +2094,7 @@ __device__ __forceinline__ void signal_gradient_d(const KProgram &P, float *cons
   }
 }
 
+template <bool FX>
 __device__ void signal_gradient(const Cta &C, float *gs, int pst, int j0, int j1) {
   const KProgram &P = *C.P;
   float **padj = reinterpret_cast<float **>(C.scratch);   // free between node evaluations
@@ -2030,19 +2102,20 @@ __device__ void signal_gradient(const Cta &C, float *gs, int pst, int j0, int j1
   __syncthreads();
   const int D = P.D;
   const float *xs = C.sig + C.row0 * D;
+  const float i1 = C.ifx1, i2 = C.ifx2;
   switch (D) {
-    case 1: signal_gradient_d<1>(P, padj, xs, gs, pst, j0, j1); break;
-    case 2: signal_gradient_d<2>(P, padj, xs, gs, pst, j0, j1); break;
-    case 3: signal_gradient_d<3>(P, padj, xs, gs, pst, j0, j1); break;
-    case 4: signal_gradient_d<4>(P, padj, xs, gs, pst, j0, j1); break;
+    case 1: signal_gradient_d<1, FX>(P, padj, xs, gs, pst, j0, j1, i1, i2); break;
+    case 2: signal_gradient_d<2, FX>(P, padj, xs, gs, pst, j0, j1, i1, i2); break;
+    case 3: signal_gradient_d<3, FX>(P, padj, xs, gs, pst, j0, j1, i1, i2); break;
+    case 4: signal_gradient_d<4, FX>(P, padj, xs, gs, pst, j0, j1, i1, i2); break;
     default: {
       for (int idx = threadIdx.x; idx < (j1 - j0) * D; idx += blockDim.x) {
         const int j = j0 + idx / D, d = idx - (idx / D) * D;
         float acc = 0.f;
-        for (int k = 0; k < P.npred; ++k) acc = fmaf(P.pw[k * STL_MAX_D + d], padj[k][j - pst], acc);
+        for (int k = 0; k < P.npred; ++k) acc = fmaf(P.pw[k * STL_MAX_D + d], padj_at<FX>(padj, k, j - pst, i1, i2), acc);
         for (unsigned m = P.norm_mask; m; m &= m - 1) {
           const int k = __ffs(m) - 1;
-          const float a = padj[k][j - pst];
+          const float a = padj_at<FX>(padj, k, j - pst, i1, i2);
           if (a != 0.f) acc += norm_grad_dim(P, k, xs + (size_t)j * D, D, d, a);
         }
         gs[(size_t)j * D + d] = acc;
@@ -2069,6 +2142,7 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
   extern __shared__ float4 smem4[];
   char *smem = reinterpret_cast<char *>(smem4);
   __shared__ long long s_item;
+  __shared__ unsigned s_gmax;
   constexpr bool ragged = RAGGED;
   constexpr bool kLean = !BWD && !SMOOTH && NT == 512;
   Cta C;
@@ -2111,7 +2185,10 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
         continue;
       }
       if (len <= 0) continue;
-      C.P = A.table + k;
+      // the plan of the smallest length bucket (T_max >> bk) that holds this trace
+      int bk = 0;
+      while (bk + 1 < A.n_buckets && (A.T_max >> (bk + 1)) >= len) ++bk;
+      C.P = A.table + (size_t)k * A.n_buckets + bk;
       C.b = b;
       C.row0 = r0;
       C.T = (int)len;
@@ -2133,12 +2210,25 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
     }
     C.out_row = BWD ? nullptr : A.out + C.row0;
     setup_geometry(C, A.bounds, ws_cta, smem, A.status);
+    constexpr int AW = (BWD && !SMOOTH) ? 2 : 1;   // adjoint words per sample
     if (BWD) {
       for (int n = 0; n < P.n; ++n)
-        if (C.rt[n].adj) zero_words(C.rt[n].adj, 0, C.rt[n].cap);
+        if (C.rt[n].adj) zero_words(C.rt[n].adj, 0, AW * C.rt[n].cap);
       __syncthreads();
     }
     const int R0 = BWD ? (s0 - P.hmax > 0 ? s0 - P.hmax : 0) : s0;
+    if constexpr (BWD && !SMOOTH) {
+      // fixed-point scale from the largest root gradient of the whole trace (not only of this
+      // item's samples: every segmentation of a trace then rounds the same way)
+      if (threadIdx.x == 0) s_gmax = 0u;
+      __syncthreads();
+      float m = trace_gmax(A.gout + C.row0, T);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, off));
+      if ((threadIdx.x & 31) == 0) atomicMax(&s_gmax, __float_as_uint(m));   // m >= 0: bits order as values
+      __syncthreads();
+      set_fix_scale(C, __uint_as_float(s_gmax));
+    }
     for (int t0 = R0; t0 < s1; t0 += P.tile) {
       const int t1 = (t0 + P.tile < s1) ? t0 + P.tile : s1;
       C.t0 = t0;
@@ -2234,10 +2324,10 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
           for (int idx = threadIdx.x; idx < (z1 - s0) * D; idx += NT)
             A.gsig[(C.row0 + s0) * D + idx] = 0.f;
         }
-        signal_gradient(C, A.gsig + C.row0 * D, t0 + P.lp, j0, j1);
+        signal_gradient<!SMOOTH>(C, A.gsig + C.row0 * D, t0 + P.lp, j0, j1);
         __syncthreads();
       }
-      if (t1 < s1) shift_buffers<BWD>(C, P.tile);
+      if (t1 < s1) shift_buffers<BWD, AW>(C, P.tile);
     }
     if constexpr (BWD) {
       if (s1 == T) {
@@ -2255,11 +2345,15 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
         const int D = P.D;
         const float *xl = C.sig + (C.row0 + (T - 1)) * D;
         for (int d = threadIdx.x; d < D; d += NT) {
+          auto pad_of = [&](int k) {
+            const NodeRt &pr = C.rt[P.pred[k]];
+            return SMOOTH ? pr.padadj : from_fix(C.ifx1, C.ifx2, pr.padfx);
+          };
           float acc = 0.f;
-          for (int k = 0; k < P.npred; ++k) acc = fmaf(P.pw[k * STL_MAX_D + d], C.rt[P.pred[k]].padadj, acc);
+          for (int k = 0; k < P.npred; ++k) acc = fmaf(P.pw[k * STL_MAX_D + d], pad_of(k), acc);
           for (unsigned m = P.norm_mask; m; m &= m - 1) {
             const int k = __ffs(m) - 1;
-            const float a = C.rt[P.pred[k]].padadj;
+            const float a = pad_of(k);
             if (a != 0.f) acc += norm_grad_dim(P, k, xl, D, d, a);
           }
           A.gsig[(C.row0 + (T - 1)) * D + d] = acc;

@@ -65,9 +65,43 @@ __global__ void __launch_bounds__(UT) mining_update_kernel(float *theta, const f
   }
 }
 
+// per-trace descent: every trace n owns its interval (a_n, b_n) in steps
+__global__ void mining_update_traces_kernel(float *__restrict__ bounds, const float *__restrict__ gb, long long N,
+                                            int n_slots, int slot, float lr, float gamma, float scale, float a_cap,
+                                            float b_cap, float min_width) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float *bp = bounds + (n * n_slots + slot) * 2;
+  const float *g = gb + (n * n_slots + slot) * 2;
+  float a = bp[0] - lr * (scale * g[0] + gamma);
+  float b = bp[1] - lr * (scale * g[1] - gamma);
+  a = fminf(fmaxf(a, 0.f), a_cap);
+  b = fminf(fmaxf(b, a + min_width), b_cap);
+  a = fminf(a, b - min_width);
+  a = fmaxf(a, 0.f);
+  bp[0] = a;
+  bp[1] = b;
+}
+
 }  // namespace
 
 extern "C" {
+
+stl_status stl_mining_update_traces(float *bounds, const float *gbounds, int64_t N, int32_t n_slots, int32_t slot,
+                                    float lr, float gamma, float scale, float a_cap, float b_cap, float min_width,
+                                    void *stream) {
+  if (N < 0 || n_slots < 1 || slot < 0 || slot >= n_slots)
+    return stl_internal_fail(STL_ERR_INVALID_ARG, "need N >= 0 and 0 <= slot < n_slots");
+  if (!(a_cap >= 0.f) || !(b_cap >= min_width) || !(min_width > 0.f))
+    return stl_internal_fail(STL_ERR_INVALID_ARG, "need a_cap >= 0, min_width > 0 and b_cap >= min_width");
+  if (N == 0) return STL_OK;
+  if (!bounds || !gbounds) return stl_internal_fail(STL_ERR_INVALID_ARG, "NULL argument");
+  mining_update_traces_kernel<<<(unsigned)((N + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      bounds, gbounds, N, n_slots, slot, lr, gamma, scale, a_cap, b_cap, min_width);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? STL_OK : stl_internal_fail(STL_ERR_CUDA, "mining update launch failed");
+}
+
 
 stl_status stl_mining_seed(const float *rho, int64_t N, int32_t T, float *grad_out, float *loss, void *stream) {
   if (N < 0 || T < 1) return stl_internal_fail(STL_ERR_INVALID_ARG, "need N >= 0 and T >= 1");

@@ -1,6 +1,6 @@
 // stl_plan.cu -- trajectory-optimisation helpers (include/stl_plan.h): the rollout of the
 // saturated single integrator and its adjoint fused with Adam, the solved/active bookkeeping,
-// and the BF16 tensor-core matrix products and elementwise steps of the warm-start MLP.
+// and the elementwise steps of the warm-start MLP (its matrix products: stl_gemm.cu).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -215,95 +215,6 @@ __global__ void trajopt_step_kernel(float *__restrict__ u, float *__restrict__ m
   }
 }
 
-// ------------------------------------------------------------------ BF16 GEMM (mma.sync)
-// C[M,N] = op(A) op(B): 64 x 64 tiles, 4 warps of 32 x 32, K in steps of 16.  Tiles are staged
-// in shared memory as As[m][k] and Bs[n][k] (both K-contiguous), the layouts of the row / col
-// operands of mma.m16n8k16.
-constexpr int GT = 64, GK = 16, GPAD = 8;
-
-__device__ __forceinline__ unsigned pack2(const __nv_bfloat16 *p) {
-  return *reinterpret_cast<const unsigned *>(p);
-}
-
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *__restrict__ A, int lda, int ta,
-                                                        const __nv_bfloat16 *__restrict__ Bm, int ldb, int tb, int M,
-                                                        int N, int K, const float *__restrict__ bias, int relu,
-                                                        float *__restrict__ Cf, __nv_bfloat16 *__restrict__ Cb,
-                                                        int ldc) {
-  __shared__ __align__(16) __nv_bfloat16 As[GT][GK + GPAD];
-  __shared__ __align__(16) __nv_bfloat16 Bs[GT][GK + GPAD];
-  const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
-  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int g = lane >> 2, t = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-  for (int k0 = 0; k0 < K; k0 += GK) {
-    // stage op(A)[m0.., k0..] and op(B)[k0.., n0..]: 1024 entries each, 8 per thread
-#pragma unroll
-    for (int e = 0; e < (GT * GK) / 128; ++e) {
-      const int idx = tid + e * 128;
-      const int r = idx / GK, kk = idx % GK;
-      const int gm = m0 + r, gk = k0 + kk;
-      __nv_bfloat16 va = zero;
-      if (gm < M && gk < K) va = ta ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
-      As[r][kk] = va;
-      const int gn = n0 + r;
-      __nv_bfloat16 vb = zero;
-      if (gn < N && gk < K) vb = tb ? Bm[(long long)gn * ldb + gk] : Bm[(long long)gk * ldb + gn];
-      Bs[r][kk] = vb;
-    }
-    __syncthreads();
-    unsigned af[2][4], bf[4][2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int r = wm + i * 16;
-      af[i][0] = pack2(&As[r + g][2 * t]);
-      af[i][1] = pack2(&As[r + g + 8][2 * t]);
-      af[i][2] = pack2(&As[r + g][2 * t + 8]);
-      af[i][3] = pack2(&As[r + g + 8][2 * t + 8]);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = wn + j * 8;
-      bf[j][0] = pack2(&Bs[c + g][2 * t]);
-      bf[j][1] = pack2(&Bs[c + g][2 * t + 8]);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-            "{%0,%1,%2,%3};\n"
-            : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-            : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bf[j][0]), "r"(bf[j][1]));
-    __syncthreads();
-  }
-  // epilogue: c0, c1 at (row g, cols 2t, 2t+1), c2, c3 at (row g + 8, same cols)
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int gm = m0 + wm + i * 16 + g + (r >= 2 ? 8 : 0);
-        const int gn = n0 + wn + j * 8 + 2 * t + (r & 1);
-        if (gm >= M || gn >= N) continue;
-        float val = acc[i][j][r];
-        if (bias) val += bias[gn];
-        if (relu) val = fmaxf(val, 0.f);
-        if (Cf) Cf[(long long)gm * ldc + gn] = val;
-        if (Cb) Cb[(long long)gm * ldc + gn] = __float2bfloat16_rn(val);
-      }
-}
-
 __global__ void mse_grad_kernel(const float *__restrict__ z, const float *__restrict__ y, long long n, float scale,
                                 __nv_bfloat16 *__restrict__ dz, float *loss) {
   float s = 0.f;
@@ -440,22 +351,6 @@ stl_status stl_trajopt_step(float *u, float *mu, float *vu, float *theta, float 
       u, mu, vu, theta, mth, vth, xbar, gbounds, gam, B, T, n_slots, slot, dt, start_x, start_y, u_max, i_nom, lr_u,
       lr_theta, b1, b2, 1e-8f, c1, c2, x, bounds);
   return cuda_status(cudaGetLastError(), "trajopt step launch failed");
-}
-
-stl_status stl_gemm_bf16(const uint16_t *a, int32_t lda, int32_t trans_a, const uint16_t *b, int32_t ldb,
-                         int32_t trans_b, int32_t M, int32_t N, int32_t K, const float *bias, int32_t relu, float *c_f32,
-                         uint16_t *c_bf16, int32_t ldc, void *stream) {
-  const int lim = 1 << 20;
-  if (M < 1 || N < 1 || K < 1 || M > lim || N > lim || K > lim)
-    return stl_internal_fail(STL_ERR_INVALID_ARG, "M, N, K must be in [1, 2^20]");
-  if (!a || !b || (!c_f32 && !c_bf16)) return stl_internal_fail(STL_ERR_INVALID_ARG, "NULL argument");
-  if (lda < (trans_a ? M : K) || ldb < (trans_b ? K : N) || ldc < N)
-    return stl_internal_fail(STL_ERR_INVALID_ARG, "leading dimension too small");
-  dim3 grid((unsigned)((N + GT - 1) / GT), (unsigned)((M + GT - 1) / GT));
-  gemm_bf16_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(
-      reinterpret_cast<const __nv_bfloat16 *>(a), lda, trans_a ? 1 : 0, reinterpret_cast<const __nv_bfloat16 *>(b), ldb,
-      trans_b ? 1 : 0, M, N, K, bias, relu ? 1 : 0, c_f32, reinterpret_cast<__nv_bfloat16 *>(c_bf16), ldc);
-  return cuda_status(cudaGetLastError(), "gemm launch failed");
 }
 
 stl_status stl_mse_grad(const float *z, const float *y, int64_t n, float scale, uint16_t *dz, float *loss,

@@ -31,6 +31,8 @@ def _lib():
         lib.stl_mining_seed.restype = i32
         lib.stl_mining_update.argtypes = [vp, vp, i64, i32, i32, i32, f32, f32, vp, vp]
         lib.stl_mining_update.restype = i32
+        lib.stl_mining_update_traces.argtypes = [vp, vp, i64, i32, i32, f32, f32, f32, f32, f32, f32, vp]
+        lib.stl_mining_update_traces.restype = i32
         lib._mining_ready = True
     return lib
 
@@ -114,3 +116,55 @@ def mine_interval(signals: np.ndarray, steps: int = 5000, lr: float = 1e-2, gamm
     th = theta.cpu().numpy()
     a, b = 1 / (1 + np.exp(-th))
     return {"a": float(a), "b": float(b), "history": hist, "us_per_step": 1e3 * e0.elapsed_time(e1) / steps}
+
+
+def per_trace_descent(signals: np.ndarray, bounds: np.ndarray, steps: int = 200, lr: float = 2.0,
+                      gamma: float = 0.01, c: float = 5.0, eps: float = 1e-3, tau: float = 10.0,
+                      a_cap: float = 100.0, b_cap: float = 400.0, formula=None, device="cuda"):
+    """The parameter-mining descent of config 2: each trace n has its own learnable interval
+    (a_n, b_n) (in steps) of Eventually over the sigmoid-masked window of s > 0.8, and takes
+    ``steps`` gradient steps on max(-rho_n(0), 0) - gamma (b_n - a_n).  One step is four
+    launches: robustness, loss seed, backward with the bound gradients, per-trace update.
+    Returns dict(bounds [N, 1, 2] numpy, loss0, loss, ms_per_step, steps)."""
+    N, T = int(signals.shape[0]), int(signals.shape[1])
+    dev = torch.device(device)
+    lib = _lib()
+    st = torch.cuda.current_stream(dev).cuda_stream
+    tree = formula or ("eventually_sm", (a_cap, b_cap, 0, None), ("pred", ">", (1.0,), 0.8))
+    f = Formula(tree, D=1, n_slots=1)
+    p = params("smooth", tau=tau, mask_c=c, mask_eps=eps)
+    x = torch.from_numpy(np.ascontiguousarray(signals, dtype=np.float32)).to(dev)
+    bd = torch.from_numpy(np.ascontiguousarray(bounds, dtype=np.float32)).to(dev)
+    rho = torch.empty((N, T), dtype=torch.float32, device=dev)
+    gout = torch.zeros((N, T), dtype=torch.float32, device=dev)
+    gsig = torch.empty((N, T, 1), dtype=torch.float32, device=dev)
+    gb = torch.empty((N, 1, 2), dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    n_ws = max(f.workspace_size(N, T, p, False), f.workspace_size(N, T, p, True))
+    ws = torch.empty(n_ws // 4 + 1, dtype=torch.float32, device=dev)
+
+    def step(rec=False):
+        robustness_raw(f, x.data_ptr(), N, T, bd.data_ptr(), p, rho.data_ptr(), ws.data_ptr(), n_ws, st)
+        check(lib.stl_mining_seed(rho.data_ptr(), N, T, gout.data_ptr(), loss.data_ptr() if rec else None, st))
+        robustness_backward_raw(f, x.data_ptr(), N, T, bd.data_ptr(), p, gout.data_ptr(), gsig.data_ptr(),
+                                gb.data_ptr(), ws.data_ptr(), n_ws, st)
+        check(lib.stl_mining_update_traces(bd.data_ptr(), gb.data_ptr(), N, 1, 0, lr, gamma, float(N), a_cap, b_cap,
+                                           1.0, st))
+
+    def total_loss():
+        loss.zero_()
+        robustness_raw(f, x.data_ptr(), N, T, bd.data_ptr(), p, rho.data_ptr(), ws.data_ptr(), n_ws, st)
+        check(lib.stl_mining_seed(rho.data_ptr(), N, T, gout.data_ptr(), loss.data_ptr(), st))
+        w = (bd[:, 0, 1] - bd[:, 0, 0]).mean()
+        return float(loss.item()) - gamma * float(w.item())
+
+    loss0 = total_loss()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    return {"bounds": bd.cpu().numpy(), "loss0": loss0, "loss": total_loss(), "ms_per_step": ms / steps,
+            "steps": steps}

@@ -162,7 +162,7 @@ class RaggedBatch:
     allocate nothing, so both can be captured in a CUDA graph (see capture())."""
 
     def __init__(self, fset: FormulaSet, sig, offsets, formula_id, bounds=None, p: StlParams | None = None,
-                 order=None, device="cuda"):
+                 order=None, device="cuda", tune=False):
         self.fset, self.p = fset, p or make_params()
         self.sig = sig.to(device=device, dtype=torch.float32).contiguous()
         self.offsets = offsets.to(device=device, dtype=torch.int64).contiguous()
@@ -180,8 +180,22 @@ class RaggedBatch:
         self.out = torch.empty(total, dtype=torch.float32, device=device)
         self.gsig = torch.empty((total, fset.D), dtype=torch.float32, device=device)
         self.gbounds = torch.empty((self.n, fset.n_slots, 2), device=device) if fset.n_slots else None
-        nf = fset.prepare(max(1, self.n), self.T_max, self.p, False)
-        nb = fset.prepare(max(1, self.n), self.T_max, self.p, True)
+        self.shapes = None
+        if tune and self.n:
+            # stl_set_autotune per direction on this batch (a random upstream gradient for the
+            # backward); the set is left prepared with the winners
+            st = torch.cuda.current_stream(self.sig.device).cuda_stream
+            g = torch.randn(total, device=device)
+            args = (self.sig.data_ptr(), self.offsets.data_ptr(), self.fid.data_ptr(), self._ptr(self.order),
+                    self._ptr(self.bounds))
+            nf, shf, msf = fset.autotune(self.n, self.T_max, self.p, False, *args, None, self.out.data_ptr(), None, st)
+            nb, shb, msb = fset.autotune(self.n, self.T_max, self.p, True, *args, g.data_ptr(), self.gsig.data_ptr(),
+                                         self._ptr(self.gbounds), st)
+            self.shapes = {"forward": {"threads": shf[0], "tile": shf[1], "ms": msf},
+                           "backward": {"threads": shb[0], "tile": shb[1], "ms": msb}}
+        else:
+            nf = fset.prepare(max(1, self.n), self.T_max, self.p, False)
+            nb = fset.prepare(max(1, self.n), self.T_max, self.p, True)
         self.ws_f = torch.empty(nf // 4 + 1, dtype=torch.float32, device=device)
         self.ws_b = torch.empty(nb // 4 + 1, dtype=torch.float32, device=device)
         self.nf, self.nb = nf, nb

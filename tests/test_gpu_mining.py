@@ -81,3 +81,34 @@ def test_mine_interval_recovers_the_interval(mining):
     res = mining.mine_interval(sig, steps=5000, lr=1e-2, gamma=0.1, record_every=500)
     assert 0.2 <= res["a"] <= 0.32 and 0.52 <= res["b"] <= 0.62, res
     assert res["history"][-1][3] < res["history"][0][3]
+
+
+def test_per_trace_descent_step_follows_the_oracle_gradient(mining):
+    # config-2 shape at a size the oracle finishes quickly: one step of the per-trace descent moves
+    # each (a_n, b_n) by -lr (N dL/dbounds + (gamma, -gamma)), with the bound gradient of the
+    # loss seed -1/N [rho_n(0) < 0] taken from the FP64 oracle, then the clamps
+    N, T = 64, 600
+    sig, bounds = W.config2_inputs(B=N, T=T, seed=4)
+    tree = W.config2_formula()
+    kw = dict(mode=oracle.SMOOTH, tau=10.0, mask_c=5.0, mask_eps=1e-3)
+    rho = oracle.robustness(tree, sig, bounds=bounds, **kw)
+    g = np.zeros((N, T))
+    g[:, 0] = np.where(rho[:, 0].astype(np.float32) < 0, -1.0 / N, 0.0)
+    _, gb = oracle.robustness_grad(tree, sig, g, bounds=bounds, **kw)
+    lr, gamma = 2.0, 0.01
+    a = np.clip(bounds[:, 0, 0] - lr * (N * gb[:, 0, 0] + gamma), 0.0, 100.0)
+    b = np.clip(bounds[:, 0, 1] - lr * (N * gb[:, 0, 1] - gamma), a + 1.0, 400.0)
+    r = mining.per_trace_descent(sig, bounds, steps=1, lr=lr, gamma=gamma)
+    got = r["bounds"][:, 0, :]
+    sure = np.abs(rho[:, 0]) > 1e-3   # traces whose seed sign cannot differ by rounding
+    assert sure.sum() > N // 2
+    np.testing.assert_allclose(got[sure, 0], a[sure], rtol=1e-4, atol=1e-3)
+    np.testing.assert_allclose(got[sure, 1], b[sure], rtol=1e-4, atol=1e-3)
+
+
+def test_per_trace_descent_lowers_the_loss(mining):
+    sig, bounds = W.config2_inputs(B=512, T=2000, seed=6)
+    r = mining.per_trace_descent(sig, bounds, steps=200)
+    assert r["loss"] < r["loss0"]
+    bd = r["bounds"][:, 0, :]
+    assert np.all(bd[:, 0] >= 0) and np.all(bd[:, 1] <= 400.0) and np.all(bd[:, 1] - bd[:, 0] >= 1.0 - 1e-4)

@@ -41,7 +41,10 @@ def test_host_pipeline_matches_device_calls(stl, mode):
     else:
         assert float((out - rho_ref).abs().max() / rho_ref.abs().max()) < 1e-6
     gs_ref = gs_ref.cpu()
-    assert float((gs - gs_ref).abs().max() / gs_ref.abs().max()) < 1e-5
+    if mode == "hard":
+        assert torch.equal(gs, gs_ref)   # chunks change the launch shape, not the hard gradient
+    else:
+        assert float((gs - gs_ref).abs().max() / gs_ref.abs().max()) < 1e-5
 
 
 def test_host_pipeline_bounds_and_forward_only(stl):
