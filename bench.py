@@ -394,6 +394,84 @@ def plan_measurement(W, args):
     return res
 
 
+def _timed(torch, call, warmup):
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    call()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_single_ragged(args):
+    """The first --ragged-traces traces of the config-3 batch (the bench's seed), longest first,
+    one ragged launch per call (the set prepared with the planner's default shapes)."""
+    import torch
+    import paper_2501_04194_gb300 as stl
+    import workloads as W
+    wl = W.config3_workload()
+    n = min(args.ragged_traces, len(wl["formula_id"]))
+    offs = wl["offsets"][: n + 1]
+    fs = [stl.Formula(t, D=4, n_slots=wl["n_slots"]) for t in wl["formulas"]]
+    order = torch.from_numpy(np.argsort(-np.diff(offs), kind="stable").astype(np.int32))
+    rb = stl.RaggedBatch(stl.FormulaSet(fs), torch.from_numpy(wl["signal"][: offs[-1]]), torch.from_numpy(offs),
+                         torch.from_numpy(wl["formula_id"][:n]), bounds=torch.from_numpy(wl["bounds"][:n]),
+                         p=stl.params(args.mode, tau=args.tau), order=order)
+    g = torch.from_numpy(np.random.default_rng(1).normal(size=int(offs[-1])).astype(np.float32)).cuda()
+    call = rb.forward if args.single == "ragged-fwd" else (lambda: rb.backward(g))
+    ms = _timed(torch, call, args.warmup)
+    print(f"single {args.single} mode={args.mode} traces={n} trace_steps={int(offs[-1])} ms={ms:.4f}")
+
+
+def run_single_gemm(args):
+    """C = relu(A B + bias) with A [4096, 256], B [256, 256] BF16 (the MLP's hidden layer)."""
+    import torch
+    from paper_2501_04194_gb300.binding import plan_call
+    M, N, K = 4096, 256, 256
+    a = torch.randn(M, K, device="cuda").to(torch.bfloat16).view(torch.int16)
+    b = torch.randn(K, N, device="cuda").to(torch.bfloat16).view(torch.int16)
+    bias = torch.randn(N, device="cuda")
+    c = torch.empty(M, N, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    call = lambda: plan_call("stl_gemm_bf16", a.data_ptr(), K, 0, b.data_ptr(), N, 0, M, N, K,  # noqa: E731
+                             bias.data_ptr(), 1, c.data_ptr(), None, N, st)
+    ms = _timed(torch, call, args.warmup)
+    print(f"single gemm M={M} N={N} K={K} ms={ms:.4f} tflops={2 * M * N * K / ms / 1e9:.2f}")
+
+
+def run_single(args):
+    """One call shape, for profilers: `ncu -k regex:stl_main -s <warmup> -c 1` captures the timed
+    call (each warm-up call is one launch of the same direction)."""
+    import torch
+    import paper_2501_04194_gb300 as stl
+    import workloads as W
+    if args.single.startswith("ragged"):
+        return run_single_ragged(args)
+    if args.single == "gemm":
+        return run_single_gemm(args)
+    f = stl.Formula(W.config1_formula(), D=3)
+    if args.tile or args.threads:
+        f.set_launch(tile=args.tile, threads=args.threads)
+    p = stl.params(args.mode, tau=args.tau)
+    x = torch.from_numpy(W.random_walk(args.B, args.T, 3, seed=0)).cuda()
+    g = torch.from_numpy(np.random.default_rng(1).normal(size=(args.B, args.T)).astype(np.float32)).cuda()
+    call = (lambda: stl.robustness(f, x, p=p)) if args.single == "fwd" else \
+        (lambda: stl.robustness_backward(f, x, g, p=p))
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    call()
+    e1.record()
+    torch.cuda.synchronize()
+    print(f"single {args.single} mode={args.mode} B={args.B} T={args.T} ms={e0.elapsed_time(e1):.4f} "
+          f"launch={f.get_launch(args.B, args.T, p, args.single == 'bwd')}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -402,7 +480,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--T", type=int, default=T_DEFAULT)
     ap.add_argument("--B", type=int, default=B_DEFAULT)
-    ap.add_argument("--mode", default="hard", choices=["hard", "smooth"])
+    ap.add_argument("--mode", default="hard", choices=["hard", "smooth", "softmax"])
     ap.add_argument("--tau", type=float, default=10.0)
     ap.add_argument("--ref-traces", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -411,10 +489,20 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the smooth, ragged and planning side measurements")
     ap.add_argument("--no-plan", action="store_true", help="skip the warm-start planning side measurement")
     ap.add_argument("--plan-train", type=int, default=100000, help="training problems of the warm-start MLP")
+    ap.add_argument("--single", choices=["fwd", "bwd", "ragged-fwd", "ragged-bwd", "gemm"], default=None,
+                    help="profiling mode: --warmup calls, then one timed call; prints its time, no JSON line. "
+                         "fwd/bwd: one direction of the config-1 formula (B, T, --mode, --tile, --threads); "
+                         "ragged-fwd/bwd: the config-3 batch (--ragged-traces traces, --mode); gemm: the "
+                         "warm-start MLP's largest product (4096 x 256 x 256, BF16)")
+    ap.add_argument("--ragged-traces", type=int, default=500)
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
+    if args.single:
+        return run_single(args)
 
     import torch
     import torch.distributed as dist

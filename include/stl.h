@@ -174,13 +174,15 @@ STL_API stl_status stl_robustness(stl_handle h, const float *sig, int64_t B, int
  *   grad_sig     [B, T, D] float32 device, overwritten
  *   grad_bounds  [B, n_slots, 2] float32 device or NULL, overwritten (nonzero only for the
  *                sigmoid-masked operators in smooth mode)
- * Determinism.  STL_HARD: each root gradient is rounded to a 64-bit fixed-point integer
- * (resolution 2^-29 of the trace's largest |grad_out|) before any addition, so grad_sig is
- * bit-identical across calls, launch shapes (stl_set_launch, autotuning), segmentations,
- * stl_robustness_and_backward, the host pipeline and the ragged path.  STL_SMOOTH /
- * STL_SOFTMAX: adjoints are float sums whose order follows warp scheduling, so two calls may
- * differ in the last bits (within float32 summation error; grad_bounds likewise, summed
- * over the segments of a trace). */
+ * Determinism.  STL_HARD and STL_SMOOTH accumulate adjoints in 64-bit fixed point: every
+ * contribution is rounded to a multiple of 2^-k (2^-k below 2^-29 of the trace's largest
+ * |grad_out|) before any addition, so the sums do not depend on the order of the additions.
+ * STL_HARD: grad_sig is bit-identical across calls, launch shapes (stl_set_launch, autotuning),
+ * segmentations, stl_robustness_and_backward, the host pipeline and the ragged path.
+ * STL_SMOOTH: grad_sig is bit-identical across calls with the same launch shape (other shapes
+ * evaluate the window sums in another order).  STL_SOFTMAX, and grad_bounds in the smooth
+ * modes: float sums whose order follows warp scheduling, so two calls may differ in the last
+ * bits (within float32 summation error). */
 STL_API stl_status stl_robustness_backward(stl_handle h, const float *sig, int64_t B, int64_t T,
                                    const float *bounds, const stl_params *p,
                                    const float *grad_out, float *grad_sig, float *grad_bounds,
@@ -291,6 +293,10 @@ STL_API stl_status stl_robustness_ragged_backward(stl_set_handle s, const float 
                                                   const stl_params *p, const float *grad_out, float *grad_sig,
                                                   float *grad_bounds, void *workspace, size_t workspace_bytes,
                                                   void *stream);
+
+/* Launch shape of a formula set for one direction (threads 64 / 256 / 512 and tile, a multiple
+ * of 32; zero fields: the planner's choice), used from the next stl_set_prepare on. */
+STL_API stl_status stl_set_set_launch(stl_set_handle s, int32_t backward, const stl_launch *launch);
 
 /* Autotuner of a formula set (the paper's static-graph batching, Sec. IV-E, over uneven
  * traces): times candidate launch shapes -- CTA size 64 / 256 / 512 (64 only for T_max <= 8192)

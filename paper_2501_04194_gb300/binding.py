@@ -309,6 +309,8 @@ class FormulaSet:
                                          vp, vp, ctypes.POINTER(StlLaunch), ctypes.POINTER(ctypes.c_float),
                                          ctypes.POINTER(sz)]
         lib.stl_set_autotune.restype = i32
+        lib.stl_set_set_launch.argtypes = [vp, i32, ctypes.POINTER(StlLaunch)]
+        lib.stl_set_set_launch.restype = i32
         lib._set_ready = True
 
     @property
@@ -319,6 +321,10 @@ class FormulaSet:
         n = ctypes.c_size_t()
         check(load().stl_set_prepare(self._h, n_traces, T_max, ctypes.byref(p), int(backward), ctypes.byref(n)))
         return int(n.value)
+
+    def set_launch(self, backward, tile=0, threads=0):
+        """stl_set_set_launch: fix the launch shape of one direction (zeros: the planner's)."""
+        check(load().stl_set_set_launch(self._h, int(backward), ctypes.byref(StlLaunch(tile, threads, 0, 0))))
 
     def autotune(self, n_traces, T_max, p: StlParams, backward, sig_ptr, off_ptr, fid_ptr, order_ptr, bounds_ptr,
                  gout_ptr, out_ptr, gb_ptr, stream):

@@ -231,10 +231,10 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
       int nrings = 1;
       if (bwd) {
         // hard backward: only predicates keep an adjoint (selection walk; 64-bit fixed-point
-        // sums, two words per sample), temporal nodes keep their selected samples; smooth
-        // backward: every node keeps a float adjoint
-        if (soft_mode(p.mode)) nrings += 1;
-        else if (is_pred(nd.op)) nrings += 2;
+        // sums, two words per sample), temporal nodes keep their selected samples; logsumexp
+        // backward: every node keeps a fixed-point adjoint; softmax-weighted: a float one
+        if (p.mode == STL_SOFTMAX) nrings += 1;
+        else if (p.mode == STL_SMOOTH || is_pred(nd.op)) nrings += 2;
         if (p.mode == STL_HARD && is_temporal(nd.op)) nrings += 1;
         // softmax windows keep each output's log-normaliser for their adjoint
         if (p.mode == STL_SOFTMAX && is_window(nd.op)) nrings += 1;
@@ -311,8 +311,8 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
     k.adj_off = -1;
     k.aux_off = -1;
     if (bwd) {
-      if (soft_mode(p.mode)) { k.adj_off = off; off += pw; }
-      else if (is_pred(nd.op)) { k.adj_off = off; off += 2 * pw; }   // 64-bit fixed point
+      if (p.mode == STL_SOFTMAX) { k.adj_off = off; off += pw; }
+      else if (p.mode == STL_SMOOTH || is_pred(nd.op)) { k.adj_off = off; off += 2 * pw; }   // 64-bit fixed point
       if ((p.mode == STL_HARD && is_temporal(nd.op)) || (p.mode == STL_SOFTMAX && is_window(nd.op))) {
         k.aux_off = off;
         off += pw;
@@ -382,8 +382,10 @@ stl_status make_plan(const stl_program *hp, long long B, long long T, const stl_
     int ut = 0;
     for (int i = 0; i < n; ++i)
       if (is_until(h->nodes[i].op)) ut = std::max(ut, window_hi(h->nodes[i], T, p) + 1);
+    // per thread: logsumexp, two words per checkpoint (every 8th tap); softmax-weighted, P_k,
+    // z_k and log S_k per tap (its double-precision prefix reduction is too costly to recompute)
+    if (p.mode == STL_SMOOTH) ut = ut / 8 + 2;
     P.ut_len = ut;
-    // per tap and thread: P_k and z_k (logsumexp); P_k, z_k and log S_k (softmax-weighted)
     ws_words += (size_t)until_arrays(p.mode) * ut * pl.grid * threads;
   }
   pl.ws_bytes = ws_words * 4;
@@ -1142,6 +1144,15 @@ std::string set_tune_key(const stl_program_set *s, long long n, long long T_max,
 }  // namespace
 
 extern "C" {
+
+stl_status stl_set_set_launch(stl_set_handle s, int32_t backward, const stl_launch *launch) {
+  if (!s || !launch) return fail(STL_ERR_INVALID_ARG, "NULL argument");
+  if (launch->threads != 0 && launch->threads != 64 && launch->threads != 256 && launch->threads != 512)
+    return fail(STL_ERR_INVALID_ARG, "threads must be 0, 64, 256 or 512");
+  if (launch->tile < 0 || launch->tile % 32 != 0) return fail(STL_ERR_INVALID_ARG, "tile must be a multiple of 32");
+  s->st[backward ? 1 : 0].shape = *launch;
+  return STL_OK;
+}
 
 stl_status stl_set_autotune(stl_set_handle s, int64_t n_traces, int64_t T_max, const stl_params *p, int32_t backward,
                             const float *sig, const int64_t *offsets, const int32_t *formula_id, const int32_t *order,

@@ -80,6 +80,8 @@ struct NodeRt {
   float ga, gb;        // smooth-mask bound-gradient accumulators
   float *tab;          // smooth-mask tables: m_i, dm_i/da, dm_i/db for i in [ia, ib]
   int band_a, band_b;  // bound gradients use offsets [ia, band_a] and [band_b, ib]
+  int ja, jb;          // smooth mask: the plateau offsets whose weight is exactly fl(1 - eps)
+                       // (ja > jb: none); the rest of [ia, ib] are the two edge bands
   int op, c0, c1;      // copies of the node's operator and children (selection walk)
   int pred_k;          // index in the predicate list, or -1
 };

@@ -130,6 +130,22 @@ struct LseM {
   }
 };
 
+// the same pair with the scaled sum in double: the transposed (adjoint) windows sum upstream
+// gradients of both signs over up to thousands of outputs, where a float sum loses digits to
+// cancellation
+struct LSd { float m; double s; };
+struct LsdM {
+  using T = LSd;
+  static __device__ __forceinline__ T comb(T a, T b) {
+    if (b.m == -INFINITY) return a;
+    if (a.m == -INFINITY) return b;
+    T o;
+    if (b.m > a.m) { o.m = b.m; o.s = fma(a.s, (double)__expf(a.m - b.m), b.s); }
+    else { o.m = a.m; o.s = fma(b.s, (double)__expf(b.m - a.m), a.s); }
+    return o;
+  }
+};
+
 // softmax-weighted reduction (Sec. III-C "soft" max / min): (m, s, n) = (largest exponent
 // z = sgn tau v seen, sum e^{z - m}, sum v e^{z - m}); the value is n / s.  An entry with
 // z = +inf dominates (kept with s = 1, n = its value), z = -inf carries no weight.
@@ -235,7 +251,8 @@ struct Lse2M {
 
 // The host sizes the window scratch for entries of 16 bytes (24 in softmax-weighted backward
 // launches, the only users of LS2).
-static_assert(sizeof(VI) <= 16 && sizeof(C2) <= 16 && sizeof(CC) <= 16 && sizeof(LS) <= 16 && sizeof(SW) <= 16,
+static_assert(sizeof(VI) <= 16 && sizeof(C2) <= 16 && sizeof(CC) <= 16 && sizeof(LS) <= 16 && sizeof(SW) <= 16 &&
+                  sizeof(LSd) <= 16,
               "window aggregates must fit the 16-byte scratch entries");
 static_assert(sizeof(LS2) <= 24, "softmax adjoint aggregates must fit the 24-byte scratch entries");
 
@@ -375,7 +392,8 @@ struct Cta {
   int t0, t1;          // current root step [t0, t1)
   int root;
   float *out_row;      // forward: out + b*T
-  float fx1, fx2;      // hard backward: fixed-point scale 2^k = fx1 * fx2 of this work item
+  bool fx;             // adjoint buffers hold 64-bit fixed point (hard and logsumexp backward)
+  float fx1, fx2;      // fixed-point scale 2^k = fx1 * fx2 of this work item
   float ifx1, ifx2;    // and its inverse
 };
 
@@ -487,9 +505,18 @@ struct OwnView {
   int start, T;
   float lastval, padadj;
   int lastaux;
+  bool fx;                    // adjoint in 64-bit fixed point, scale 1 / (i1 * i2)
+  float i1, i2;
+  unsigned long long padfx;
   __device__ __forceinline__ float val(int q) const { return q >= T - 1 ? lastval : v[q - start]; }
   __device__ __forceinline__ int src(int q) const { return q >= T - 1 ? lastaux : aux[q - start]; }
-  __device__ __forceinline__ float g(int q) const { return q >= T - 1 ? padadj : adj[q - start]; }
+  __device__ __forceinline__ float g(int q) const {
+    if (fx) {
+      const unsigned long long a = q >= T - 1 ? padfx : reinterpret_cast<const unsigned long long *>(adj)[q - start];
+      return from_fix(i1, i2, a);
+    }
+    return q >= T - 1 ? padadj : adj[q - start];
+  }
 };
 
 __device__ __forceinline__ OwnView own_view(const Cta &C, int n) {
@@ -503,6 +530,10 @@ __device__ __forceinline__ OwnView own_view(const Cta &C, int n) {
   o.lastval = r.lastval;
   o.lastaux = r.lastaux;
   o.padadj = r.padadj;
+  o.fx = C.fx;
+  o.i1 = C.ifx1;
+  o.i2 = C.ifx2;
+  o.padfx = r.padfx;
   return o;
 }
 
@@ -539,17 +570,35 @@ __device__ __forceinline__ NodeOut node_out(const Cta &C, int n) {
 }
 
 // a parent's write access to a child's adjoint (sample T-1 and pads go to the per-node cell)
+// With fx, every contribution is rounded to the fixed-point grid before it is added (integer
+// sums: exact and order-independent).
 struct ChildAdj {
   float *a;
   float *padadj;
+  unsigned long long *padfx;
   int start, T;
+  bool fx;
+  float f1, f2;               // fixed-point scale 2^k = f1 * f2
+  __device__ __forceinline__ long long fix(float g) const { return __float2ll_rn((g * f1) * f2); }
   __device__ __forceinline__ void add_atomic(int j, float g) const {
     if (j < 0 || g == 0.f) return;
+    if (fx) {
+      const long long v = fix(g);
+      if (j >= T - 1) fix_add(padfx, v);
+      else fix_add(reinterpret_cast<unsigned long long *>(a) + (j - start), v);
+      return;
+    }
     if (j >= T - 1) buf_add(padadj, g);
     else buf_add(&a[j - start], g);
   }
   __device__ __forceinline__ void add_owned(int j, float g) const {
     if (j < 0) return;
+    if (fx) {
+      const long long v = fix(g);
+      if (j >= T - 1) { if (v != 0) fix_add(padfx, v); }
+      else reinterpret_cast<unsigned long long *>(a)[j - start] += (unsigned long long)v;
+      return;
+    }
     if (j >= T - 1) { if (g != 0.f) buf_add(padadj, g); }
     else a[j - start] += g;
   }
@@ -560,8 +609,12 @@ __device__ __forceinline__ ChildAdj child_adj(const Cta &C, int c) {
   ChildAdj o;
   o.a = r.adj;
   o.padadj = &r.padadj;
+  o.padfx = &r.padfx;
   o.start = C.t0 + r.lo;
   o.T = C.T;
+  o.fx = C.fx;
+  o.f1 = C.fx1;
+  o.f2 = C.fx2;
   return o;
 }
 
@@ -1310,6 +1363,28 @@ __device__ void eval_smooth_mask(const Cta &C, int n, int F, int E) {
     }
     return;
   }
+  const int ja = me.ja, jb = me.jb, ib = me.ib;
+  if (jb - ja + 1 >= 2 * RUN) {
+    // O(1) per sample: the plateau [ja, jb] (every weight exactly w0 = fl(1 - eps)) is a sliding
+    // logsumexp window scaled by w0; the two edge bands [ia, ja) and (jb, ib] are added tap by tap
+    const float w0 = w[ja - ia];
+    auto elem = [&](int j) { LS r; r.m = st * cv.get(j); r.s = 1.f; return r; };
+    auto out = [&](int q, LS r) {
+      float M = r.m, S = r.m == -INFINITY ? 0.f : r.s * w0;
+      auto add = [&](int i) {
+        const float m = w[i - ia];
+        const float z = st * cv.get(q + i);
+        if (z == -INFINITY || m <= 0.f) return;
+        if (z > M) { S = fmaf(S, __expf(M - z), m); M = z; }
+        else S = fmaf(m, __expf(z - M), S);
+      };
+      for (int i = ia; i < ja; ++i) add(i);
+      for (int i = jb + 1; i <= ib; ++i) add(i);
+      o.put(q, M == -INFINITY ? sgn * -INFINITY : sgn * (M + __logf(S)) * P.inv_tau);
+    };
+    window_any<LseM>(jb - ja + 1, F, E, ja, jb, elem, out, C.scratch);
+    return;
+  }
   for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
     float M = -INFINITY, S = 0.f;
     for (int i = 0; i < len; ++i) {
@@ -1534,19 +1609,50 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
         accumulate_shared_d(&rt.gb, gbv);
         return;
       }
-      for (int j = A0 + ia + threadIdx.x; j < A1 + ib; j += NT) {
-        int src;
-        const float x = cv.get(j, src);
-        if (src < 0) continue;
-        const int ilo = max(ia, j - (A1 - 1)), ihi = min(ib, j - A0);
-        float acc = 0.f;
-        const float sx = st * x;
-        for (int i = ilo; i <= ihi; ++i) {
-          const int q = j - i;
-          const float g = me.g(q);
-          acc = fmaf(g * w[i - ia], __expf(sx - st * me.val(q)), acc);
+      const int ja = rt.ja, jb = rt.jb;
+      if (jb - ja + 1 >= 2 * RUN) {
+        // plateau offsets: the transposed logsumexp window over the parent samples scaled by
+        // w0, x̄_j += w0 e^{st x_j} sum_{q in [j-jb, j-ja]} g_q e^{-st y_q}; edge offsets tap by tap
+        const float w0 = w[ja - ia];
+        auto elem = [&](int q) {
+          LSd r;
+          if (q < A0 || q >= A1) { r.m = -INFINITY; r.s = 0.0; return r; }
+          r.m = -st * me.val(q);
+          r.s = me.g(q);
+          return r;
+        };
+        auto out = [&](int j, LSd r) {
+          int src;
+          const float x = cv.get(j, src);
+          if (src < 0) return;
+          const float sx = st * x;
+          float acc = (r.m == -INFINITY || r.s == 0.0) ? 0.f : w0 * (float)(r.s * (double)__expf(sx + r.m));
+          auto edge = [&](int i) {
+            const int q = j - i;
+            if (q < A0 || q >= A1) return;
+            const float g = me.g(q);
+            acc = fmaf(g * w[i - ia], __expf(sx - st * me.val(q)), acc);
+          };
+          for (int i = ia; i < ja; ++i) edge(i);
+          for (int i = jb + 1; i <= ib; ++i) edge(i);
+          a0.add_owned(src, acc);
+        };
+        window_any<LsdM>(jb - ja + 1, A0 + ia, A1 + ib, -jb, -ja, elem, out, C.scratch);
+      } else {
+        for (int j = A0 + ia + threadIdx.x; j < A1 + ib; j += NT) {
+          int src;
+          const float x = cv.get(j, src);
+          if (src < 0) continue;
+          const int ilo = max(ia, j - (A1 - 1)), ihi = min(ib, j - A0);
+          float acc = 0.f;
+          const float sx = st * x;
+          for (int i = ilo; i <= ihi; ++i) {
+            const int q = j - i;
+            const float g = me.g(q);
+            acc = fmaf(g * w[i - ia], __expf(sx - st * me.val(q)), acc);
+          }
+          a0.add_owned(src, acc);
         }
-        a0.add_owned(src, acc);
       }
       float ga = 0.f, gbv = 0.f;
       for (int q = A0 + threadIdx.x; q < A1; q += NT) {
@@ -1599,31 +1705,43 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
       return;
     }
     auto elem = [&](int q) {
-      LS r;
-      if (q < A0 || q >= A1) { r.m = -INFINITY; r.s = 0.f; return r; }
+      LSd r;
+      if (q < A0 || q >= A1) { r.m = -INFINITY; r.s = 0.0; return r; }
       r.m = -st * me.val(q);
       r.s = me.g(q);
       return r;
     };
-    auto out = [&](int j, LS r) {
-      if (r.m == -INFINITY || r.s == 0.f) return;
+    auto out = [&](int j, LSd r) {
+      if (r.m == -INFINITY || r.s == 0.0) return;
       int src;
       const float x = cv.get(j, src);
       if (src < 0) return;
-      a0.add_owned(src, r.s * __expf(st * x + r.m));
+      a0.add_owned(src, (float)(r.s * (double)__expf(st * x + r.m)));
     };
-    window_any<LseM>(ib - ia + 1, A0 + ia, A1 + ib, -ib, -ia, elem, out, C.scratch);
+    window_any<LsdM>(ib - ia + 1, A0 + ia, A1 + ib, -ib, -ia, elem, out, C.scratch);
   }
 }
 
-// Smooth Until adjoint.  With L_i = log(S_i + Q_i) = -tau z_i and tau U = log sum_i e^{-L_i}:
-//   dU/dpsi_{q+i} = e^{tau(z_i - U)} e^{tau(z_i - psi_i)}
-//   dU/dphi_{q+k} = e^{tau(P_k - phi_k)} D_k,  D_k = [k>=a] e^{tau(2 z_k - U - P_k)} + e^{tau(P_{k+1}-P_k)} D_{k+1}
-// where P_k = -(1/tau) log S_k.  A forward pass over the taps stores P_k and z_k in the
-// per-thread workspace arrays (2 (b+1) floats), a backward pass runs the D recursion; every
-// exponent above is <= 0, so nothing overflows.  Masked-interval Until: the terms of offset i
-// carry the weight m_i (the node's table), and the bound gradients add
+// Smooth Until adjoint.  With S_k = sum_{j<=k} e^{-tau phi_{q+j}}, Q_i = e^{-tau psi_{q+i}},
+// L_i = log(S_i + Q_i) = -tau z_i and tau U = log W, W = sum_{i in [a,b]} e^{-L_i}:
+//   dU/dpsi_{q+i} = e^{-2 L_i - tau U} Q_i
+//   dU/dphi_{q+k} = e^{-tau phi_{q+k}} R_k,   R_k = sum_{i >= max(k, a)} e^{-2 L_i - tau U}
+// (differentiate log W through S_i = ... + e^{-tau phi_k} for every i >= k).  R_k is a suffix sum
+// of positive terms, accumulated from k = b down to 0 with the running maximum m_k of the
+// exponents of S_k as scale, R'_k = e^{m_k} R_k = e^{m_k - m_{k+1}} R'_{k+1} + [k>=a] e^{-2 L_k - tau U + m_k},
+// and dU/dphi_{q+k} = e^{-tau phi_{q+k} - m_k} R'_k: every exponent is <= 0, and the factor
+// e^{m_k - m_{k+1}} is exactly 1 except where the maximum moves (products of rounded ratios of
+// S would lose a few ulps per tap over windows of thousands of taps).  The recursion needs m_k
+// and L_k from k = b down to 0, which a running sum cannot give without cancellation.  So a first
+// pass over the taps keeps only the accumulator of S at every UCK-th tap (two floats per
+// checkpoint in the per-thread workspace arrays), and a second pass walks the chunks from the
+// last to the first: it restarts S from the chunk's checkpoint, recomputes m_k and L_k for the
+// chunk's UCK taps into registers (depositing the psi adjoint and the bound gradients on the
+// way), then runs the recursion over the chunk backwards.  Masked-interval Until: the terms of
+// offset i carry the weight m_i (the node's table), and the bound gradients add
 // g m'_i e^{tau (z_i - U)} / tau over the owned samples [own0, own1).
+constexpr int UCK = 8;   // taps per checkpoint of the smooth Until adjoint
+
 __device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, int own0, int own1, float *Pk,
                                      long long pstride) {
   const KProgram &P = *C.P;
@@ -1637,45 +1755,70 @@ __device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, int ow
   const bool masked = nd.op == OP_UNTSM;
   const int len = ib - ia + 1;
   const float *w = masked ? rt.tab : nullptr, *wa = masked ? rt.tab + len : nullptr, *wb = masked ? rt.tab + 2 * len : nullptr;
-  float *Zk = Pk + (long long)P.ut_len * pstride;
+  float *Cm = Pk, *Cs = Pk + (long long)P.ut_len * pstride;   // checkpoints: max and scaled sum of S
   double ga = 0.0, gbv = 0.0;
   for (int q = A0 + threadIdx.x; q < A1; q += blockDim.x) {
     const float g = me.g(q);
     if (g == 0.f) continue;
     const float tU = tau * me.val(q);
     const bool own = masked && q >= own0 && q < own1;
-    LseAcc S;
-    for (int k = 0; k <= ib; ++k) {
-      S.add(-tau * cp.get(q + k));
-      const float ls = S.log();
-      Pk[k * pstride] = ls == -INFINITY ? INFINITY : -ls * itau;
-      if (k >= ia) {
-        int sq;
-        const float zq = -tau * cq.get(q + k, sq);
-        const float L = log_s_plus_q(S, zq);
-        Zk[k * pstride] = -L * itau;
-        const float m = w ? w[k - ia] : 1.f;
-        if (zq != -INFINITY && L != -INFINITY) aq.add_atomic(sq, g * m * __expf(-L - tU + zq - L));
-        if (own && L != -INFINITY) {
-          const double e = (double)__expf(-L - tU) * (double)itau * (double)g;
-          ga = fma(e, (double)wa[k - ia], ga);
-          gbv = fma(e, (double)wb[k - ia], gbv);
+    {
+      LseAcc S;
+      for (int k = 0; k <= ib; ++k) {
+        if ((k & (UCK - 1)) == 0) {
+          Cm[(k / UCK) * pstride] = S.m;
+          Cs[(k / UCK) * pstride] = S.s;
         }
+        S.add(-tau * cp.get(q + k));
       }
     }
-    float Dn = 0.f, Pnext = 0.f;
-    for (int k = ib; k >= 0; --k) {
-      const float Pv = Pk[k * pstride];
-      float Dk = (k < ib && !isinf(Pv)) ? __expf(tau * (Pnext - Pv)) * Dn : 0.f;
-      if (k >= ia && !isinf(Pv)) {
-        const float tz = tau * Zk[k * pstride];
-        Dk += (w ? w[k - ia] : 1.f) * __expf(2.f * tz - tU - tau * Pv);
+    float Rn = 0.f, mnext = -INFINITY;   // R'_{k+1} and m_{k+1}
+    for (int c0 = (ib / UCK) * UCK; c0 >= 0; c0 -= UCK) {
+      LseAcc S;
+      S.m = Cm[(c0 / UCK) * pstride];
+      S.s = Cs[(c0 / UCK) * pstride];
+      float Mc[UCK], Lc[UCK], Zc[UCK];
+      int Sc[UCK];
+#pragma unroll
+      for (int j = 0; j < UCK; ++j) {
+        const int k = c0 + j;
+        Mc[j] = -INFINITY;
+        Lc[j] = -INFINITY;
+        Zc[j] = -INFINITY;
+        Sc[j] = -1;
+        if (k <= ib) {
+          Zc[j] = -tau * cp.get(q + k, Sc[j]);
+          S.add(Zc[j]);
+          Mc[j] = S.m;
+          if (k >= ia) {
+            int sq;
+            const float zq = -tau * cq.get(q + k, sq);
+            const float L = log_s_plus_q(S, zq);
+            Lc[j] = L;
+            const float m = w ? w[k - ia] : 1.f;
+            if (zq != -INFINITY && L != -INFINITY) aq.add_atomic(sq, g * m * __expf(-L - tU + zq - L));
+            if (own && L != -INFINITY) {
+              const double e = (double)__expf(-L - tU) * (double)itau * (double)g;
+              ga = fma(e, (double)wa[k - ia], ga);
+              gbv = fma(e, (double)wb[k - ia], gbv);
+            }
+          }
+        }
       }
-      int sp;
-      const float pv = cp.get(q + k, sp);
-      if (!isinf(pv) && !isinf(Pv)) ap.add_atomic(sp, g * __expf(tau * (Pv - pv)) * Dk);
-      Dn = Dk;
-      Pnext = Pv;
+#pragma unroll
+      for (int j = UCK - 1; j >= 0; --j) {
+        const int k = c0 + j;
+        if (k > ib) continue;
+        const float mk = Mc[j];
+        float R = 0.f;
+        if (mk != -INFINITY) {
+          if (k < ib) R = (mk == mnext ? 1.f : __expf(mk - mnext)) * Rn;
+          if (k >= ia && Lc[j] != -INFINITY) R += (w ? w[k - ia] : 1.f) * __expf(-2.f * Lc[j] - tU + mk);
+          if (!isinf(Zc[j])) ap.add_atomic(Sc[j], g * __expf(Zc[j] - mk) * R);
+        }
+        Rn = R;
+        mnext = mk;
+      }
     }
   }
   if (masked) {
@@ -1877,6 +2020,27 @@ __device__ void setup_geometry(Cta &C, const float *bounds, float *ws_cta, char 
     }
   }
   __syncthreads();
+  // plateau of each mask: the offsets whose float weight is exactly 1 - eps (the sigmoid at a has
+  // rounded to 1 and the one at b is below half an ulp of 1); they form one interval
+  if (threadIdx.x == 0) {
+    for (int n = 0; n < P.n; ++n) {
+      NodeRt &r = C.rt[n];
+      r.ja = 1;
+      r.jb = 0;
+      if (!r.tab) continue;
+      const float w0 = 1.f - P.mask_eps;
+      const int len = r.ib - r.ia + 1;
+      int lo = 0;
+      while (lo < len && r.tab[lo] != w0) ++lo;
+      int hi = lo;
+      while (hi + 1 < len && r.tab[hi + 1] == w0) ++hi;
+      if (lo < len) {
+        r.ja = r.ia + lo;
+        r.jb = r.ia + hi;
+      }
+    }
+  }
+  __syncthreads();
 }
 
 // zero words [w0, w1) of a buffer (16-byte aligned base; vector stores for the bulk)
@@ -1904,8 +2068,8 @@ __device__ __forceinline__ void move_down(float *p, int src, int len) {
 }
 
 // end of a step: keep the live samples [t1 + lo, t1 + hi) at the front of every buffer
-template <bool BWD, int AW>   // AW: adjoint words per sample (2: hard fixed point)
-__device__ void shift_buffers(const Cta &C, int tile) {
+template <bool BWD>   // AW: adjoint words per sample (2: fixed point)
+__device__ void shift_buffers(const Cta &C, int tile, int AW) {
   const KProgram &P = *C.P;
   int max_span = 0;
   for (int n = 0; n < P.n; ++n) max_span = max(max_span, C.rt[n].hi - C.rt[n].lo);
@@ -2210,14 +2374,20 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
     }
     C.out_row = BWD ? nullptr : A.out + C.row0;
     setup_geometry(C, A.bounds, ws_cta, smem, A.status);
-    constexpr int AW = (BWD && !SMOOTH) ? 2 : 1;   // adjoint words per sample
+    // hard and logsumexp backward launches keep their adjoints in 64-bit fixed point (two words
+    // per sample): every weight of those adjoints is in [0, 1] (selections, softmax weights of
+    // logsumexp reductions), so no adjoint exceeds the sum of |grad_out| over a trace and the
+    // scale below cannot overflow; softmax-weighted launches keep float adjoints
+    C.fx = BWD && (!SMOOTH || P.mode == 1);
+    const int AW = C.fx ? 2 : 1;   // adjoint words per sample
     if (BWD) {
       for (int n = 0; n < P.n; ++n)
         if (C.rt[n].adj) zero_words(C.rt[n].adj, 0, AW * C.rt[n].cap);
       __syncthreads();
     }
     const int R0 = BWD ? (s0 - P.hmax > 0 ? s0 - P.hmax : 0) : s0;
-    if constexpr (BWD && !SMOOTH) {
+    C.fx1 = C.fx2 = C.ifx1 = C.ifx2 = 1.f;
+    if (C.fx) {
       // fixed-point scale from the largest root gradient of the whole trace (not only of this
       // item's samples: every segmentation of a trace then rounds the same way)
       if (threadIdx.x == 0) s_gmax = 0u;
@@ -2290,8 +2460,14 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
           const float *g = A.gout + C.row0;
           for (int q = t0 + threadIdx.x; q < t1; q += NT) {
             const float v = __ldg(g + q);
-            if (q == T - 1) r.padadj += v;
-            else ra[q - st] = v;
+            if (C.fx) {
+              const unsigned long long f = (unsigned long long)to_fix(C, v);
+              if (q == T - 1) r.padfx += f;
+              else reinterpret_cast<unsigned long long *>(ra)[q - st] = f;
+            } else {
+              if (q == T - 1) r.padadj += v;
+              else ra[q - st] = v;
+            }
           }
         }
         __syncthreads();
@@ -2324,10 +2500,11 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
           for (int idx = threadIdx.x; idx < (z1 - s0) * D; idx += NT)
             A.gsig[(C.row0 + s0) * D + idx] = 0.f;
         }
-        signal_gradient<!SMOOTH>(C, A.gsig + C.row0 * D, t0 + P.lp, j0, j1);
+        if (C.fx) signal_gradient<true>(C, A.gsig + C.row0 * D, t0 + P.lp, j0, j1);
+        else signal_gradient<false>(C, A.gsig + C.row0 * D, t0 + P.lp, j0, j1);
         __syncthreads();
       }
-      if (t1 < s1) shift_buffers<BWD, AW>(C, P.tile);
+      if (t1 < s1) shift_buffers<BWD>(C, P.tile, AW);
     }
     if constexpr (BWD) {
       if (s1 == T) {
@@ -2347,7 +2524,7 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 8 : NT == 256 ? ((SMOOTH && !B
         for (int d = threadIdx.x; d < D; d += NT) {
           auto pad_of = [&](int k) {
             const NodeRt &pr = C.rt[P.pred[k]];
-            return SMOOTH ? pr.padadj : from_fix(C.ifx1, C.ifx2, pr.padfx);
+            return C.fx ? from_fix(C.ifx1, C.ifx2, pr.padfx) : pr.padadj;
           };
           float acc = 0.f;
           for (int k = 0; k < P.npred; ++k) acc = fmaf(P.pw[k * STL_MAX_D + d], pad_of(k), acc);

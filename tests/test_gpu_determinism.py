@@ -3,8 +3,10 @@
 Hard mode: every root gradient is rounded to a 64-bit fixed-point integer (scale from the
 trace's largest root gradient) before any addition, so the signal gradient is bit-identical
 across repeated launches, CTA sizes, tiles, segmentations, the one-launch robustness-and-
-gradient call and the ragged path.  The smooth modes add floats in an order set by the
-scheduling of warps; there two launches may differ, within float32 summation error.
+gradient call and the ragged path.  Logsumexp mode: adjoints are fixed-point sums as well, so
+repeated launches of one shape agree bit for bit.  The softmax-weighted mode adds floats in an
+order set by the scheduling of warps; there two launches may differ, within float32
+summation error.
 """
 import numpy as np
 import pytest
@@ -71,10 +73,20 @@ def test_hard_gradient_with_large_and_tiny_upstream_gradients(stl):
         assert torch.equal(got[b], base[0] * scale[b, 0])
 
 
-@pytest.mark.parametrize("mode", ["smooth", "softmax"])
-def test_smooth_gradient_differs_at_most_by_summation_error(stl, mode):
+def test_logsumexp_gradient_is_bitwise_repeatable(stl):
+    # the logsumexp adjoints are fixed-point sums too: the same launch shape gives the same bits
     f = stl.Formula(W.config1_formula(), D=3)
-    p = stl.params(mode, tau=10.0)
+    p = stl.params("smooth", tau=10.0)
+    x, g = _inputs(16, 3000, 3, 34)
+    ref, _ = stl.robustness_backward(f, x, g, p=p)
+    for _ in range(3):
+        got, _ = stl.robustness_backward(f, x, g, p=p)
+        assert torch.equal(got, ref)
+
+
+def test_softmax_gradient_differs_at_most_by_summation_error(stl):
+    f = stl.Formula(W.config1_formula(), D=3)
+    p = stl.params("softmax", tau=10.0)
     x, g = _inputs(16, 3000, 3, 34)
     ref, _ = stl.robustness_backward(f, x, g, p=p)
     scale = ref.abs().amax(dim=(1, 2), keepdim=True).clamp_min(1e-30)

@@ -119,6 +119,19 @@ def test_config2_smooth_mask(stl):
     check(stl, W.config2_formula(), sig, bounds=bounds, mode="hard", mask_c=5.0, mask_eps=1e-3)
 
 
+@pytest.mark.parametrize("c,eps", [(0.7, 1e-3), (1.5, 1e-2), (5.0, 1e-3)])
+@pytest.mark.parametrize("op", ["eventually", "always"])
+def test_smooth_mask_plateau_and_edge_bands(stl, c, eps, op):
+    # logsumexp mode: offsets whose float weight is exactly 1 - eps go through a sliding window,
+    # the two edge bands tap by tap; per-trace widths b - a in [20, 300] give plateaus from none
+    # (short windows at c = 0.7) to most of the support, one and several steps per trace
+    sig, bounds = W.config2_inputs(B=24, T=1500, seed=11)
+    ctor = W.EventuallySm if op == "eventually" else W.AlwaysSm
+    tree = ctor(100, 400, W.gt([1.0], 0.8), slot=0)
+    for launch in (None, dict(tile=256)):
+        check(stl, tree, sig, bounds=bounds, mode="smooth", tau=10.0, mask_c=c, mask_eps=eps, launch=launch)
+
+
 @pytest.mark.parametrize("mode", ["hard", "smooth"])
 def test_always_sm_small_sharpness(stl, mode):
     rng = np.random.default_rng(7)

@@ -90,13 +90,17 @@ def test_noalloc_empty_batch(stl):
 
 
 def test_noalloc_rejects_scratch_beyond_its_array(stl):
-    # Until over [0, 70000]: two floats per tap and thread need 35.8 MB even for one 64-thread
-    # CTA, more than the 32 MiB array
+    # twelve nested Always_[0,60000] over traces of 800,000 samples: the node buffers that spill
+    # out of shared memory (value and adjoint, spans 60,000 .. 720,000 samples) need about 37 MB
+    # for one CTA of any size, more than the 32 MiB array; the call is rejected before any launch
     from paper_2501_04194_gb300.binding import StlError
-    f = stl.Formula(W.Until(0, 70000, W.gt([1.0], 0.0), W.lt([1.0], 0.5)), D=1)
+    f = W.gt([1.0], 0.0)
+    for _ in range(12):
+        f = W.Always(0, 60000, f)
+    f = stl.Formula(f, D=1)
     p = stl.params("smooth", tau=5.0)
-    x = torch.zeros((2, 71000, 1), device="cuda")
-    g = torch.zeros((2, 71000), device="cuda")
+    x = torch.zeros((2, 800000, 1), device="cuda")
+    g = torch.zeros((2, 800000), device="cuda")
     with pytest.raises(StlError) as ei:
         noalloc_backward(stl, f, x, g, p)
     assert ei.value.status == -4 and "static scratch" in str(ei.value)
