@@ -452,6 +452,16 @@ def run_single(args):
         return run_single_ragged(args)
     if args.single == "gemm":
         return run_single_gemm(args)
+    if args.single.startswith("cfg2"):
+        sig, bounds = W.config2_inputs(B=4096, T=2000, seed=0)
+        f = stl.Formula(W.config2_formula(), D=1, n_slots=1)
+        p = stl.params(args.mode, tau=args.tau, mask_c=5.0, mask_eps=1e-3)
+        x, bd = torch.from_numpy(sig).cuda(), torch.from_numpy(bounds).cuda()
+        g = torch.from_numpy(np.random.default_rng(1).normal(size=(4096, 2000)).astype(np.float32)).cuda()
+        call = (lambda: stl.robustness(f, x, bounds=bd, p=p)) if args.single == "cfg2-fwd" else \
+            (lambda: stl.robustness_backward(f, x, g, bounds=bd, p=p))
+        print(f"single {args.single} mode={args.mode} B=4096 T=2000 ms={_timed(torch, call, args.warmup):.4f}")
+        return
     f = stl.Formula(W.config1_formula(), D=3)
     if args.tile or args.threads:
         f.set_launch(tile=args.tile, threads=args.threads)
@@ -489,11 +499,13 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the smooth, ragged and planning side measurements")
     ap.add_argument("--no-plan", action="store_true", help="skip the warm-start planning side measurement")
     ap.add_argument("--plan-train", type=int, default=100000, help="training problems of the warm-start MLP")
-    ap.add_argument("--single", choices=["fwd", "bwd", "ragged-fwd", "ragged-bwd", "gemm"], default=None,
+    ap.add_argument("--single", choices=["fwd", "bwd", "ragged-fwd", "ragged-bwd", "gemm", "cfg2-fwd", "cfg2-bwd"],
+                    default=None,
                     help="profiling mode: --warmup calls, then one timed call; prints its time, no JSON line. "
                          "fwd/bwd: one direction of the config-1 formula (B, T, --mode, --tile, --threads); "
                          "ragged-fwd/bwd: the config-3 batch (--ragged-traces traces, --mode); gemm: the "
-                         "warm-start MLP's largest product (4096 x 256 x 256, BF16)")
+                         "warm-start MLP's largest product (4096 x 256 x 256, BF16); cfg2-fwd/bwd: the "
+                         "sigmoid-masked Eventually of config 2 (B = 4096, T = 2000, c = 5, --mode)")
     ap.add_argument("--ragged-traces", type=int, default=500)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)

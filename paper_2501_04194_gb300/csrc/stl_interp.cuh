@@ -1274,11 +1274,23 @@ __device__ void eval_smooth_until(const Cta &C, int n, int F, int E, int ia, int
   const ChildView cq = child_view(C, nd, nd.c1);
   const NodeOut o = node_out(C, n);
   const float tau = P.tau, itau = P.inv_tau;
+  // outputs whose taps all lie below T-1 inside both children's computed ranges read the
+  // buffers directly (no per-tap clamp or end-of-trace select)
+  const int qdirect = min(min(cp.fmax, cq.fmax), C.T - 2) - ib;
   for (int q = F + threadIdx.x; q < E; q += blockDim.x) {
     LseAcc S, Z;   // S: sum_k e^{-tau phi_k};  Z: sum_i m_i e^{tau z_i}
-    for (int i = 0; i <= ib; ++i) {
-      S.add(-tau * cp.get(q + i));
-      if (i >= ia) Z.add(-log_s_plus_q(S, -tau * cq.get(q + i)) + (w ? __logf(w[i - ia]) : 0.f));
+    if (q <= qdirect && q >= cp.start && q >= cq.start) {
+      const float *pp = cp.p + (q - cp.start), *pq = cq.p + (q - cq.start);
+      for (int i = 0; i < ia; ++i) S.add(-tau * pp[i]);
+      for (int i = ia; i <= ib; ++i) {
+        S.add(-tau * pp[i]);
+        Z.add(-log_s_plus_q(S, -tau * pq[i]) + (w ? __logf(w[i - ia]) : 0.f));
+      }
+    } else {
+      for (int i = 0; i <= ib; ++i) {
+        S.add(-tau * cp.get(q + i));
+        if (i >= ia) Z.add(-log_s_plus_q(S, -tau * cq.get(q + i)) + (w ? __logf(w[i - ia]) : 0.f));
+      }
     }
     const float lz = Z.log();
     o.put(q, lz == -INFINITY ? -INFINITY : lz * itau);
@@ -1742,6 +1754,104 @@ __device__ void adjoint_node(const Cta &C, int n, int A0, int A1, int own0, int 
 // g m'_i e^{tau (z_i - U)} / tau over the owned samples [own0, own1).
 constexpr int UCK = 8;   // taps per checkpoint of the smooth Until adjoint
 
+// Reads of an Until's children and deposits into their adjoints for one output q, through the
+// clamped views (any output) or, for outputs whose taps q..q+b all lie below T-1, directly:
+// plain loads of the children's buffers and fixed-point additions at the tap's offset, with
+// no per-tap clamp, end-of-trace select or address-space test.
+struct UntilIOView {
+  const ChildView &cp, &cq;
+  const ChildAdj &ap, &aq;
+  int q;
+  __device__ __forceinline__ float phi(int k, int &src) const { return cp.get(q + k, src); }
+  __device__ __forceinline__ float psi(int k, int &src) const { return cq.get(q + k, src); }
+  __device__ __forceinline__ void dep_phi(int src, float v) const { ap.add_atomic(src, v); }
+  __device__ __forceinline__ void dep_psi(int src, float v) const { aq.add_atomic(src, v); }
+};
+struct UntilIODirect {
+  const float *pp, *pq;              // the children's values at sample q
+  unsigned long long *dp, *dq;       // their fixed-point adjoints at sample q
+  unsigned dps, dqs;                 // the same as shared addresses (when sh)
+  bool sh;                           // both adjoint buffers in shared memory
+  float f1, f2;                      // fixed-point scale
+  __device__ __forceinline__ float phi(int k, int &src) const { src = k; return pp[k]; }
+  __device__ __forceinline__ float psi(int k, int &src) const { src = k; return pq[k]; }
+  __device__ __forceinline__ void dep(unsigned long long *base, unsigned sbase, int k, float v) const {
+    const long long f = __float2ll_rn((v * f1) * f2);
+    if (f == 0) return;
+    if (sh) asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(sbase + 8u * (unsigned)k), "l"(f) : "memory");
+    else atomicAdd(base + k, (unsigned long long)f);
+  }
+  __device__ __forceinline__ void dep_phi(int k, float v) const { dep(dp, dps, k, v); }
+  __device__ __forceinline__ void dep_psi(int k, float v) const { dep(dq, dqs, k, v); }
+};
+
+// the adjoint of one output q (see the derivation above); g its upstream gradient, tU = tau U_q
+template <class IO>
+__device__ __forceinline__ void until_adjoint_one(const IO &io, float g, float tU, int ia, int ib, float tau,
+                                                  float itau, const float *w, const float *wa, const float *wb,
+                                                  bool own, float *Cm, float *Cs, long long pstride, double &ga,
+                                                  double &gbv) {
+  {
+    LseAcc S;
+    for (int k = 0; k <= ib; ++k) {
+      if ((k & (UCK - 1)) == 0) {
+        Cm[(k / UCK) * pstride] = S.m;
+        Cs[(k / UCK) * pstride] = S.s;
+      }
+      int src;
+      S.add(-tau * io.phi(k, src));
+    }
+  }
+  float Rn = 0.f, mnext = -INFINITY;   // R'_{k+1} and m_{k+1}
+  for (int c0 = (ib / UCK) * UCK; c0 >= 0; c0 -= UCK) {
+    LseAcc S;
+    S.m = Cm[(c0 / UCK) * pstride];
+    S.s = Cs[(c0 / UCK) * pstride];
+    float Mc[UCK], Lc[UCK], Zc[UCK];
+    int Sc[UCK];
+#pragma unroll
+    for (int j = 0; j < UCK; ++j) {
+      const int k = c0 + j;
+      Mc[j] = -INFINITY;
+      Lc[j] = -INFINITY;
+      Zc[j] = -INFINITY;
+      Sc[j] = -1;
+      if (k <= ib) {
+        Zc[j] = -tau * io.phi(k, Sc[j]);
+        S.add(Zc[j]);
+        Mc[j] = S.m;
+        if (k >= ia) {
+          int sq;
+          const float zq = -tau * io.psi(k, sq);
+          const float L = log_s_plus_q(S, zq);
+          Lc[j] = L;
+          const float m = w ? w[k - ia] : 1.f;
+          if (zq != -INFINITY && L != -INFINITY) io.dep_psi(sq, g * m * __expf(-L - tU + zq - L));
+          if (own && L != -INFINITY) {
+            const double e = (double)__expf(-L - tU) * (double)itau * (double)g;
+            ga = fma(e, (double)wa[k - ia], ga);
+            gbv = fma(e, (double)wb[k - ia], gbv);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = UCK - 1; j >= 0; --j) {
+      const int k = c0 + j;
+      if (k > ib) continue;
+      const float mk = Mc[j];
+      float R = 0.f;
+      if (mk != -INFINITY) {
+        if (k < ib) R = (mk == mnext ? 1.f : __expf(mk - mnext)) * Rn;
+        if (k >= ia && Lc[j] != -INFINITY) R += (w ? w[k - ia] : 1.f) * __expf(-2.f * Lc[j] - tU + mk);
+        if (!isinf(Zc[j])) io.dep_phi(Sc[j], g * __expf(Zc[j] - mk) * R);
+      }
+      Rn = R;
+      mnext = mk;
+    }
+  }
+}
+
 __device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, int own0, int own1, float *Pk,
                                      long long pstride) {
   const KProgram &P = *C.P;
@@ -1756,69 +1866,32 @@ __device__ void adjoint_smooth_until(const Cta &C, int n, int A0, int A1, int ow
   const int len = ib - ia + 1;
   const float *w = masked ? rt.tab : nullptr, *wa = masked ? rt.tab + len : nullptr, *wb = masked ? rt.tab + 2 * len : nullptr;
   float *Cm = Pk, *Cs = Pk + (long long)P.ut_len * pstride;   // checkpoints: max and scaled sum of S
+  // outputs whose taps all lie below T-1 and inside both children's computed ranges take the
+  // direct path (fixed-point adjoints only)
+  const int qdirect = min(min(cp.fmax, cq.fmax), C.T - 2) - ib;   // last such output
+  const bool can_direct = ap.fx && aq.fx;
+  const bool sh = __isShared(ap.a) && __isShared(aq.a);
   double ga = 0.0, gbv = 0.0;
   for (int q = A0 + threadIdx.x; q < A1; q += blockDim.x) {
     const float g = me.g(q);
     if (g == 0.f) continue;
     const float tU = tau * me.val(q);
     const bool own = masked && q >= own0 && q < own1;
-    {
-      LseAcc S;
-      for (int k = 0; k <= ib; ++k) {
-        if ((k & (UCK - 1)) == 0) {
-          Cm[(k / UCK) * pstride] = S.m;
-          Cs[(k / UCK) * pstride] = S.s;
-        }
-        S.add(-tau * cp.get(q + k));
-      }
-    }
-    float Rn = 0.f, mnext = -INFINITY;   // R'_{k+1} and m_{k+1}
-    for (int c0 = (ib / UCK) * UCK; c0 >= 0; c0 -= UCK) {
-      LseAcc S;
-      S.m = Cm[(c0 / UCK) * pstride];
-      S.s = Cs[(c0 / UCK) * pstride];
-      float Mc[UCK], Lc[UCK], Zc[UCK];
-      int Sc[UCK];
-#pragma unroll
-      for (int j = 0; j < UCK; ++j) {
-        const int k = c0 + j;
-        Mc[j] = -INFINITY;
-        Lc[j] = -INFINITY;
-        Zc[j] = -INFINITY;
-        Sc[j] = -1;
-        if (k <= ib) {
-          Zc[j] = -tau * cp.get(q + k, Sc[j]);
-          S.add(Zc[j]);
-          Mc[j] = S.m;
-          if (k >= ia) {
-            int sq;
-            const float zq = -tau * cq.get(q + k, sq);
-            const float L = log_s_plus_q(S, zq);
-            Lc[j] = L;
-            const float m = w ? w[k - ia] : 1.f;
-            if (zq != -INFINITY && L != -INFINITY) aq.add_atomic(sq, g * m * __expf(-L - tU + zq - L));
-            if (own && L != -INFINITY) {
-              const double e = (double)__expf(-L - tU) * (double)itau * (double)g;
-              ga = fma(e, (double)wa[k - ia], ga);
-              gbv = fma(e, (double)wb[k - ia], gbv);
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int j = UCK - 1; j >= 0; --j) {
-        const int k = c0 + j;
-        if (k > ib) continue;
-        const float mk = Mc[j];
-        float R = 0.f;
-        if (mk != -INFINITY) {
-          if (k < ib) R = (mk == mnext ? 1.f : __expf(mk - mnext)) * Rn;
-          if (k >= ia && Lc[j] != -INFINITY) R += (w ? w[k - ia] : 1.f) * __expf(-2.f * Lc[j] - tU + mk);
-          if (!isinf(Zc[j])) ap.add_atomic(Sc[j], g * __expf(Zc[j] - mk) * R);
-        }
-        Rn = R;
-        mnext = mk;
-      }
+    if (can_direct && q <= qdirect && q >= cp.start && q >= cq.start) {
+      UntilIODirect io;
+      io.pp = cp.p + (q - cp.start);
+      io.pq = cq.p + (q - cq.start);
+      io.dp = reinterpret_cast<unsigned long long *>(ap.a) + (q - ap.start);
+      io.dq = reinterpret_cast<unsigned long long *>(aq.a) + (q - aq.start);
+      io.sh = sh;
+      io.dps = sh ? (unsigned)__cvta_generic_to_shared(io.dp) : 0u;
+      io.dqs = sh ? (unsigned)__cvta_generic_to_shared(io.dq) : 0u;
+      io.f1 = ap.f1;
+      io.f2 = ap.f2;
+      until_adjoint_one(io, g, tU, ia, ib, tau, itau, w, wa, wb, own, Cm, Cs, pstride, ga, gbv);
+    } else {
+      const UntilIOView io{cp, cq, ap, aq, q};
+      until_adjoint_one(io, g, tU, ia, ib, tau, itau, w, wa, wb, own, Cm, Cs, pstride, ga, gbv);
     }
   }
   if (masked) {
