@@ -184,19 +184,18 @@ def side_measurements(stl, W, torch, dev, args):
       one persistent launch each, against one launch per formula over its own traces."""
     out = {}
     B1, T1 = 1024, 10000
-    f = stl.Formula(W.config1_formula(), D=3)
-    p = stl.params("smooth", tau=10.0)
     x = torch.from_numpy(W.random_walk(B1, T1, 3, seed=0)).to(dev)
     g = torch.randn((B1, T1), device=dev)
-    ms_f = time_ms(torch, lambda: stl.robustness(f, x, p=p))
-    ms_b = time_ms(torch, lambda: stl.robustness_backward(f, x, g, p=p))
-    out["smooth_config1_T10000"] = {"value": B1 * T1 / ((ms_f + ms_b) * 1e-3), "unit": UNIT, "fwd_ms": ms_f,
-                                    "bwd_ms": ms_b, "note": "smooth Until is O(b) per sample (compute-bound)"}
-    ps = stl.params("softmax", tau=10.0)
-    ms_f = time_ms(torch, lambda: stl.robustness(f, x, p=ps))
-    ms_b = time_ms(torch, lambda: stl.robustness_backward(f, x, g, p=ps))
-    out["softmax_config1_T10000"] = {"value": B1 * T1 / ((ms_f + ms_b) * 1e-3), "unit": UNIT, "fwd_ms": ms_f,
-                                     "bwd_ms": ms_b, "note": "softmax-weighted min/max, tau = 10"}
+    for mode, key, note in (("smooth", "smooth_config1_T10000", "smooth Until is O(b) per sample (compute-bound)"),
+                            ("softmax", "softmax_config1_T10000", "softmax-weighted min/max, tau = 10")):
+        f = stl.Formula(W.config1_formula(), D=3)
+        p = stl.params(mode, tau=10.0)
+        lf, _ = stl.autotune(f, x, p=p, backward=False)
+        lb, _ = stl.autotune(f, x, p=p, backward=True)
+        ms_f = time_ms(torch, lambda: stl.robustness(f, x, p=p))
+        ms_b = time_ms(torch, lambda: stl.robustness_backward(f, x, g, p=p))
+        out[key] = {"value": B1 * T1 / ((ms_f + ms_b) * 1e-3), "unit": UNIT, "fwd_ms": ms_f, "bwd_ms": ms_b,
+                    "launch": {"forward": lf, "backward": lb}, "note": note}
     wl = W.config3_workload()
     fs = [stl.Formula(t, D=4, n_slots=wl["n_slots"]) for t in wl["formulas"]]
     offs = torch.from_numpy(wl["offsets"])
@@ -281,7 +280,7 @@ def config2_measurement(W):
     B, T = 4096, 2000
     sig, bounds = W.config2_inputs(B=B, T=T, seed=0)
     mining.per_trace_descent(sig, bounds, steps=5)   # warm-up (plans, caches)
-    r = mining.per_trace_descent(sig, bounds, steps=200)
+    r = mining.per_trace_descent(sig, bounds, steps=200, tune=True)
     ms = r["ms_per_step"]
     hbm = peaks()[0]
     gbs = 20.0 * B * T / (ms * 1e-3) / 1e9   # D = 1: forward 4D + 4, backward 8D + 4
@@ -292,7 +291,7 @@ def config2_measurement(W):
                          "bytes_per_trace_step": 20},
             "l2": "working set (signal 33 MB, rho, grad_out, grad 33 MB each) is L2-resident across the 200 "
                   "steps (129 MB L2): the HBM fraction above counts the algorithmic bytes as if from DRAM",
-            "loss_before": r["loss0"], "loss_after": r["loss"], "mean_width_before": width0,
+            "launch": r["launch"], "loss_before": r["loss0"], "loss_after": r["loss"], "mean_width_before": width0,
             "mean_width_after": width}
 
 

@@ -100,10 +100,36 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float *v) {
 
 // Stage rows [row0, row0 + 128) x K block [k0, k0 + 64) of a matrix X read as X(r, k) into a
 // K-major swizzled tile.  kcontig: X(r, k) = X[r * ld + k] (16-byte chunks load as one vector
-// when aligned and in bounds); otherwise X(r, k) = X[k * ld + r].  Out-of-range entries are 0.
+// when aligned and in bounds); otherwise X(r, k) = X[k * ld + r], read as 16-byte vectors along
+// r (16 threads cover 256 contiguous bytes of one k) and transposed on the way into the tile.
+// Out-of-range entries are 0.  vec_ok: ld is a multiple of 8 and X 16-byte aligned.
 __device__ __forceinline__ void stage_tile(uint8_t *tile, const __nv_bfloat16 *__restrict__ X, int ld, bool kcontig,
                                            int row0, int R, int k0, int K, bool vec_ok) {
   const unsigned short *Xs = reinterpret_cast<const unsigned short *>(X);
+  if (!kcontig) {
+#pragma unroll
+    for (int i = 0; i < (TM * TKB / 8) / 128; ++i) {
+      const int idx = threadIdx.x + i * 128;
+      const int c8 = idx & 15, k = idx >> 4;   // rows 8 c8 .. 8 c8 + 7, column k of the block
+      const int gk = k0 + k, gr = row0 + 8 * c8;
+      unsigned short e[8];
+      if (gk < K && vec_ok && gr + 8 <= R) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(Xs + (long long)gk * ld + gr));
+        e[0] = v.x & 0xffffu; e[1] = v.x >> 16; e[2] = v.y & 0xffffu; e[3] = v.y >> 16;
+        e[4] = v.z & 0xffffu; e[5] = v.z >> 16; e[6] = v.w & 0xffffu; e[7] = v.w >> 16;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          e[j] = (gk < K && gr + j < R) ? Xs[(long long)gk * ld + gr + j] : (unsigned short)0;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int r = 8 * c8 + j;
+        *reinterpret_cast<unsigned short *>(tile + r * 128 + ((((k >> 3) ^ (r & 7))) << 4) + (k & 7) * 2) = e[j];
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < (TM * TKB / 8) / 128; ++i) {
     const int idx = threadIdx.x + i * 128;
@@ -111,14 +137,14 @@ __device__ __forceinline__ void stage_tile(uint8_t *tile, const __nv_bfloat16 *_
     const int gr = row0 + r, gk = k0 + 8 * c;
     uint4 v = make_uint4(0u, 0u, 0u, 0u);
     if (gr < R && gk < K) {
-      if (kcontig && vec_ok && gk + 8 <= K) {
+      if (vec_ok && gk + 8 <= K) {
         v = __ldg(reinterpret_cast<const uint4 *>(Xs + (long long)gr * ld + gk));
       } else {
         unsigned short e[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int kk = gk + j;
-          e[j] = kk < K ? (kcontig ? Xs[(long long)gr * ld + kk] : Xs[(long long)kk * ld + gr]) : (unsigned short)0;
+          e[j] = kk < K ? Xs[(long long)gr * ld + kk] : (unsigned short)0;
         }
         v.x = e[0] | ((unsigned)e[1] << 16);
         v.y = e[2] | ((unsigned)e[3] << 16);
@@ -236,9 +262,9 @@ stl_status stl_gemm_bf16(const uint16_t *a, int32_t lda, int32_t trans_a, const 
   if (e) return stl_internal_fail(STL_ERR_CUDA, cudaGetErrorString((cudaError_t)e));
   cudaError_t ce = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (ce != cudaSuccess) return stl_internal_fail(STL_ERR_CUDA, cudaGetErrorString(ce));
-  // 16-byte vector loads of K-contiguous rows need 16-byte aligned rows
-  const int a_vec = !trans_a && (lda % 8 == 0) && ((reinterpret_cast<uintptr_t>(a) & 15) == 0);
-  const int b_vec = trans_b && (ldb % 8 == 0) && ((reinterpret_cast<uintptr_t>(b) & 15) == 0);
+  // 16-byte vector loads (along K or along the rows) need 16-byte aligned rows
+  const int a_vec = (lda % 8 == 0) && ((reinterpret_cast<uintptr_t>(a) & 15) == 0);
+  const int b_vec = (ldb % 8 == 0) && ((reinterpret_cast<uintptr_t>(b) & 15) == 0);
   dim3 grid((unsigned)((N + TN - 1) / TN), (unsigned)((M + TM - 1) / TM));
   gemm_tc_kernel<<<grid, 128, SMEM_BYTES, (cudaStream_t)stream>>>(
       reinterpret_cast<const __nv_bfloat16 *>(a), lda, trans_a ? 1 : 0, reinterpret_cast<const __nv_bfloat16 *>(b), ldb,

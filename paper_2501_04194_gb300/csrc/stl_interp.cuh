@@ -2103,10 +2103,12 @@ __device__ void setup_geometry(Cta &C, const float *bounds, float *ws_cta, char 
       if (!r.tab) continue;
       const float w0 = 1.f - P.mask_eps;
       const int len = r.ib - r.ia + 1;
+      // scanned in from both ends (a few entries each: the edge bands), not across the plateau,
+      // while the other threads wait at the barrier below
       int lo = 0;
       while (lo < len && r.tab[lo] != w0) ++lo;
-      int hi = lo;
-      while (hi + 1 < len && r.tab[hi + 1] == w0) ++hi;
+      int hi = len - 1;
+      while (hi > lo && r.tab[hi] != w0) --hi;
       if (lo < len) {
         r.ja = r.ia + lo;
         r.jb = r.ia + hi;

@@ -120,12 +120,14 @@ def mine_interval(signals: np.ndarray, steps: int = 5000, lr: float = 1e-2, gamm
 
 def per_trace_descent(signals: np.ndarray, bounds: np.ndarray, steps: int = 200, lr: float = 2.0,
                       gamma: float = 0.01, c: float = 5.0, eps: float = 1e-3, tau: float = 10.0,
-                      a_cap: float = 100.0, b_cap: float = 400.0, formula=None, device="cuda"):
+                      a_cap: float = 100.0, b_cap: float = 400.0, formula=None, tune: bool = False,
+                      device="cuda"):
     """The parameter-mining descent of config 2: each trace n has its own learnable interval
     (a_n, b_n) (in steps) of Eventually over the sigmoid-masked window of s > 0.8, and takes
     ``steps`` gradient steps on max(-rho_n(0), 0) - gamma (b_n - a_n).  One step is four
     launches: robustness, loss seed, backward with the bound gradients, per-trace update.
-    Returns dict(bounds [N, 1, 2] numpy, loss0, loss, ms_per_step, steps)."""
+    tune: pick both launch shapes with stl_autotune first.
+    Returns dict(bounds [N, 1, 2] numpy, loss0, loss, ms_per_step, steps, launch)."""
     N, T = int(signals.shape[0]), int(signals.shape[1])
     dev = torch.device(device)
     lib = _lib()
@@ -140,6 +142,10 @@ def per_trace_descent(signals: np.ndarray, bounds: np.ndarray, steps: int = 200,
     gsig = torch.empty((N, T, 1), dtype=torch.float32, device=dev)
     gb = torch.empty((N, 1, 2), dtype=torch.float32, device=dev)
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    if tune:   # launch shapes of both directions from stl_autotune, before any timing
+        from .torch_api import autotune
+        autotune(f, x, bounds=bd, p=p, backward=False)
+        autotune(f, x, bounds=bd, p=p, backward=True)
     n_ws = max(f.workspace_size(N, T, p, False), f.workspace_size(N, T, p, True))
     ws = torch.empty(n_ws // 4 + 1, dtype=torch.float32, device=dev)
 
@@ -167,4 +173,4 @@ def per_trace_descent(signals: np.ndarray, bounds: np.ndarray, steps: int = 200,
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
     return {"bounds": bd.cpu().numpy(), "loss0": loss0, "loss": total_loss(), "ms_per_step": ms / steps,
-            "steps": steps}
+            "steps": steps, "launch": {"forward": f.get_launch(N, T, p, False), "backward": f.get_launch(N, T, p, True)}}

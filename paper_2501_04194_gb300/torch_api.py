@@ -125,7 +125,9 @@ def autotune(f: Formula, sig: torch.Tensor, bounds=None, p: StlParams | None = N
     stream = torch.cuda.current_stream(sig.device).cuda_stream
     ws = torch.empty(max_workspace_bytes // 4, dtype=torch.float32, device=sig.device)
     if backward:
-        g = torch.zeros((B, T), dtype=torch.float32, device=sig.device)
+        # a dense upstream gradient: with zeros the smooth adjoints skip their work and the timing
+        # would not be the real one
+        g = torch.randn((B, T), dtype=torch.float32, device=sig.device)
         out = torch.empty((B, T, D), dtype=torch.float32, device=sig.device)
         gb = torch.empty((B, f.n_slots, 2), dtype=torch.float32, device=sig.device) if f.n_slots else None
         res = f.autotune(sig.data_ptr(), B, T, None if b is None else b.data_ptr(), p, True, g.data_ptr(),

@@ -132,7 +132,7 @@ def bf16(x):
 
 
 @pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0), (0, 1), (1, 1)])
-@pytest.mark.parametrize("M,N,K", [(70, 45, 33), (128, 256, 16), (5, 400, 256)])
+@pytest.mark.parametrize("M,N,K", [(70, 45, 33), (128, 256, 16), (5, 400, 256), (200, 136, 72), (4096, 256, 256)])
 def test_gemm_bf16(stl, ta, tb, M, N, K):
     rng = np.random.default_rng(M + N + K + 2 * ta + tb)
     A = bf16(rng.normal(size=(K, M) if ta else (M, K)))
