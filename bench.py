@@ -176,6 +176,26 @@ def time_ms(torch, fn, steps=3, warmup=2):
     return a.elapsed_time(b) / steps
 
 
+# Special-function (MUFU: exp, log) operations per sample of the config-1 formula in logsumexp
+# mode, counted from the kernels' arithmetic: the smooth Until over [5, 200] walks 201 prefix taps
+# per output (one exp each) and combines 196 of them with psi (log(S + Q): one exp and one log;
+# the outer sum: one exp); the windows and the two-term Or add about a dozen.  The backward
+# recomputes the forward, then runs the Until adjoint: a checkpoint pass (201 exps) and a chunk
+# pass (201 exps, 2 x 196 for log(S + Q), 196 for the psi deposits, 196 for the suffix terms,
+# 201 for the phi deposits).
+MUFU_FWD = 201 + 3 * 196 + 12
+MUFU_BWD = MUFU_FWD + 201 + 201 + 2 * 196 + 196 + 196 + 201 + 12
+SFU_PEAK = 16 * 152 * 2.07e9   # MUFU results per clock per SM x SMs x maximum SM clock
+
+
+def smooth_sfu_roofline(ms_f, ms_b, steps):
+    ops = (MUFU_FWD + MUFU_BWD) * steps
+    achieved = ops / ((ms_f + ms_b) * 1e-3)
+    return {"bound": "sfu", "achieved": achieved / 1e12, "peak": SFU_PEAK / 1e12, "unit": "T MUFU op/s",
+            "frac": achieved / SFU_PEAK, "ops_per_trace_step": MUFU_FWD + MUFU_BWD, "traffic": None,
+            "peak_kind": "derived: 16 MUFU ops/clk/SM x 152 SMs x 2.07 GHz"}
+
+
 def side_measurements(stl, W, torch, dev, args):
     """Secondary numbers reported beside the headline (not the metric):
     - config 1 in the smooth modes (logsumexp and softmax-weighted, tau = 10) at T = 10000,
@@ -196,6 +216,8 @@ def side_measurements(stl, W, torch, dev, args):
         ms_b = time_ms(torch, lambda: stl.robustness_backward(f, x, g, p=p))
         out[key] = {"value": B1 * T1 / ((ms_f + ms_b) * 1e-3), "unit": UNIT, "fwd_ms": ms_f, "bwd_ms": ms_b,
                     "launch": {"forward": lf, "backward": lb}, "note": note}
+        if mode == "smooth":
+            out[key]["roofline"] = smooth_sfu_roofline(ms_f, ms_b, B1 * T1)
     wl = W.config3_workload()
     fs = [stl.Formula(t, D=4, n_slots=wl["n_slots"]) for t in wl["formulas"]]
     offs = torch.from_numpy(wl["offsets"])

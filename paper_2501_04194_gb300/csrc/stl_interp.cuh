@@ -2026,16 +2026,13 @@ __device__ void setup_geometry(Cta &C, const float *bounds, float *ws_cta, char 
       r.fa = a;
       r.fb = b;
       if (nd.op == OP_EVSM || nd.op == OP_ALWSM || nd.op == OP_UNTSM) {
-        // support {i >= 0 : sigma(c(i-a)) - sigma(c(i-b)) > eps} is an interval
+        // support {i >= 0 : sigma(c(i-a)) - sigma(c(i-b)) > eps} is an interval inside
+        // [a - L - 1, b + L + 2], L = log((1-eps)/eps) / c; warp 0 finds its ends below
         const double c = P.mask_c, eps = P.mask_eps;
         const double L = log((1.0 - eps) / eps) / c;
-        int lo = (int)floor((double)a - L) - 1;
-        int hi = (int)ceil((double)b + L) + 2;
-        lo = lo < 0 ? 0 : lo;
-        while (lo <= hi && smask_d(lo, a, b, c, eps) <= 0.0) ++lo;
-        while (hi >= lo && smask_d(hi, a, b, c, eps) <= 0.0) --hi;
-        r.ia = lo;
-        r.ib = hi;
+        const int lo = (int)floor((double)a - L) - 1;
+        r.ia = lo < 0 ? 0 : lo;
+        r.ib = (int)ceil((double)b + L) + 2;
       } else if (nd.op == OP_EV || nd.op == OP_ALW || nd.op == OP_UNTIL) {
         r.ia = (int)a;
         r.ib = isinf(b) ? (int)(C.T - 1) : (int)b;
@@ -2061,19 +2058,50 @@ __device__ void setup_geometry(Cta &C, const float *bounds, float *ws_cta, char 
       r.c1 = nd.c1;
       r.pred_k = -1;
       r.tab = nd.tab_off >= 0 ? reinterpret_cast<float *>(smem) + nd.tab_off : nullptr;
-      if (r.tab) {
-        if (r.ib - r.ia + 1 > nd.tab_len) {   // cannot happen for bounds within the caps
-          if (status) atomicExch(status, 1);
-          r.ib = r.ia + nd.tab_len - 1;
-        }
-        // beyond 22/c from an edge, sigma(c d)(1 - sigma(c d)) < e^-22: the bound gradient
-        // terms there are below float resolution of the sums they join
-        const float band = 22.f / P.mask_c;
-        r.band_a = min(r.ib, (int)ceilf(a + band));
-        r.band_b = max(r.ia, (int)floorf(b - band));
-      }
     }
     for (int k = 0; k < P.npred; ++k) C.rt[P.pred[k]].pred_k = k;
+  }
+  __syncthreads();
+  // smooth-mask supports: the lanes of warp 0 test 32 candidate offsets at a time from each end
+  // (the double-precision mask costs two exponentials per offset), then fix the tables' range
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int n = 0; n < P.n; ++n) {
+      const KNode &nd = P.nd[n];
+      if (!(nd.op == OP_EVSM || nd.op == OP_ALWSM || nd.op == OP_UNTSM)) continue;
+      NodeRt &r = C.rt[n];
+      const double c = P.mask_c, eps = P.mask_eps;
+      const double fa = r.fa, fb = r.fb;
+      const int lo0 = r.ia, hi0 = r.ib;
+      int lo = hi0 + 1;   // first positive offset (none: past the end)
+      for (int base = lo0; base <= hi0; base += 32) {
+        const int i = base + lane;
+        const unsigned m = __ballot_sync(FULL, i <= hi0 && smask_d(i, fa, fb, c, eps) > 0.0);
+        if (m) { lo = base + __ffs(m) - 1; break; }
+      }
+      int hi = hi0;       // last positive offset at or after lo
+      for (int top = hi0; top >= lo; top -= 32) {
+        const int i = top - lane;
+        const unsigned m = __ballot_sync(FULL, i >= lo && smask_d(i, fa, fb, c, eps) > 0.0);
+        if (m) { hi = top - (__ffs(m) - 1); break; }
+      }
+      if (lane == 0) {
+        r.ia = lo;
+        r.ib = hi;
+        if (r.tab) {
+          if (r.ib - r.ia + 1 > nd.tab_len) {   // cannot happen for bounds within the caps
+            if (status) atomicExch(status, 1);
+            r.ib = r.ia + nd.tab_len - 1;
+          }
+          // beyond 22/c from an edge, sigma(c d)(1 - sigma(c d)) < e^-22: the bound gradient
+          // terms there are below float resolution of the sums they join
+          const float band = 22.f / P.mask_c;
+          r.band_a = min(r.ib, (int)ceilf(r.fa + band));
+          r.band_b = max(r.ia, (int)floorf(r.fb - band));
+        }
+      }
+      __syncwarp();
+    }
   }
   __syncthreads();
   // smooth-mask tables m_i, dm_i/da, dm_i/db over the support (Eq. smooth mask)
