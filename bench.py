@@ -53,8 +53,9 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel, B, T):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernels."""
+def recorded_traffic(kernel, B, T, launch=None):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernels
+    (and, when the summary names one, with the same launch shape)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -62,6 +63,8 @@ def recorded_traffic(kernel, B, T):
         d = json.load(open(p))
         e = d.get(kernel)
         if not e or e.get("source_sha") != kernel_source_sha():
+            return None
+        if launch and "tile" in e and (launch.get("tile"), launch.get("threads")) != (e["tile"], e["threads"]):
             return None
         # captured on a smaller case: scale by trace-steps
         return float(e["dram_bytes"]) * (B * T) / float(e["trace_steps"])
@@ -448,10 +451,11 @@ def run_single_ragged(args):
 
 
 def run_single_gemm(args):
-    """C = relu(A B + bias) with A [4096, 256], B [256, 256] BF16 (the MLP's hidden layer)."""
+    """C = relu(A B + bias), A [M, K] and B [K, N] BF16 (default: the MLP's hidden layer for a
+    batch of 4096 problems)."""
     import torch
     from paper_2501_04194_gb300.binding import plan_call
-    M, N, K = 4096, 256, 256
+    M, N, K = (int(v) for v in args.gemm_mnk.split(","))
     a = torch.randn(M, K, device="cuda").to(torch.bfloat16).view(torch.int16)
     b = torch.randn(K, N, device="cuda").to(torch.bfloat16).view(torch.int16)
     bias = torch.randn(N, device="cuda")
@@ -528,6 +532,7 @@ def main():
                          "warm-start MLP's largest product (4096 x 256 x 256, BF16); cfg2-fwd/bwd: the "
                          "sigmoid-masked Eventually of config 2 (B = 4096, T = 2000, c = 5, --mode)")
     ap.add_argument("--ragged-traces", type=int, default=500)
+    ap.add_argument("--gemm-mnk", default="4096,256,256", help="M,N,K of --single gemm")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     args = ap.parse_args()
@@ -689,7 +694,7 @@ def main():
     dom = "backward" if bwd_ms >= fwd_ms else "forward"
     dom_bytes, dom_ms = (bwd_bytes, bwd_ms) if dom == "backward" else (fwd_bytes, fwd_ms)
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(f"stl_main_{dom}", B, T)
+    traffic = recorded_traffic(f"stl_main_{dom}", B, T, (tuned or {}).get(dom))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": f"stl_main ({dom})", "peak_kind": peak_kind,
             "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
