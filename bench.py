@@ -488,8 +488,8 @@ def run_single(args):
         print(f"single {args.single} mode={args.mode} B=4096 T=2000 ms={_timed(torch, call, args.warmup):.4f}")
         return
     f = stl.Formula(W.config1_formula(), D=3)
-    if args.tile or args.threads:
-        f.set_launch(tile=args.tile, threads=args.threads)
+    if args.tile or args.threads or args.kernel != "auto":
+        f.set_launch(tile=args.tile, threads=args.threads, kernel=args.kernel)
     p = stl.params(args.mode, tau=args.tau)
     x = torch.from_numpy(W.random_walk(args.B, args.T, 3, seed=0)).cuda()
     g = torch.from_numpy(np.random.default_rng(1).normal(size=(args.B, args.T)).astype(np.float32)).cuda()
@@ -535,6 +535,8 @@ def main():
     ap.add_argument("--gemm-mnk", default="4096,256,256", help="M,N,K of --single gemm")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--kernel", default="auto", choices=["auto", "interpreter", "compiled"],
+                    help="--single fwd/bwd: which kernel serves the call (stl_launch.kernel)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

@@ -109,13 +109,30 @@ typedef struct {
   float mask_eps;   /* smooth-mask tolerance epsilon, in (0, 1) */
 } stl_params;
 
+/* Which kernel serves a call.
+ *   STL_KERNEL_INTERPRETER  the streaming interpreter: one precompiled kernel family that
+ *                           reads the compiled formula at run time; serves every call.
+ *   STL_KERNEL_COMPILED     a kernel generated for this formula and direction, with every
+ *                           node, interval, buffer offset and predicate weight a compile-time
+ *                           constant, compiled at run time (NVRTC, sm_103a) on first use and
+ *                           kept for the life of the process (first call: about a second).
+ *                           Serves hard semantics (STL_HARD) with static integer intervals
+ *                           (no bound slot, b finite, b <= 16000), affine predicates, True,
+ *                           not / and / or / eventually / always / until, and T at least one
+ *                           more than the largest sum of interval starts along a path.  Values
+ *                           and gradients are bit-identical to the interpreter's.  Needs no
+ *                           workspace and sets no device status.
+ *   STL_KERNEL_AUTO         the compiled kernel where it applies, B*T >= 2^20 samples and
+ *                           tile, threads and segment are all 0; else the interpreter. */
+typedef enum { STL_KERNEL_AUTO = 0, STL_KERNEL_INTERPRETER = 1, STL_KERNEL_COMPILED = 2 } stl_kernel;
+
 /* Launch shape.  Zero fields mean "choose automatically" (the autotuner's cached choice if
  * one was registered with stl_set_launch, else a heuristic). */
 typedef struct {
   int32_t tile;      /* samples advanced per streaming step (multiple of 32) */
-  int32_t threads;   /* CTA size: 64, 256 or 512 */
+  int32_t threads;   /* CTA size: 64, 256 or 512 (compiled kernels: 256 or 512) */
   int32_t segment;   /* samples per work item (a trace is split into segments) */
-  int32_t reserved;
+  int32_t kernel;    /* stl_kernel */
 } stl_launch;
 
 typedef struct stl_program *stl_handle;
@@ -149,9 +166,19 @@ STL_API stl_status stl_autotune(stl_handle h, const float *sig, int64_t B, int64
                                 float *grad_bounds, void *workspace, size_t workspace_bytes, void *stream,
                                 stl_launch *best, float *best_ms);
 
-/* Launch shape the library would use for this call shape (after heuristics/overrides). */
+/* Launch shape the library would use for this call shape (after heuristics/overrides);
+ * out->kernel is STL_KERNEL_INTERPRETER or STL_KERNEL_COMPILED. */
 STL_API stl_status stl_get_launch(stl_handle h, int64_t B, int64_t T, const stl_params *p,
                           int32_t backward, stl_launch *out);
+
+/* Generate and compile (NVRTC, sm_103a) the formula-compiled kernel of this handle for one
+ * direction and launch shape, without launching it; needs no GPU.  launch: threads (0, 256
+ * or 512) and tile (0: the default, else the largest tile up to this one whose buffers fit
+ * in shared memory); tile_out / smem_bytes (either may be NULL) receive the tile and dynamic
+ * shared memory the kernel uses.  Returns STL_ERR_UNSUPPORTED when the formula is outside
+ * what the compiled kernels serve (reason in stl_last_error()) or NVRTC is missing. */
+STL_API stl_status stl_compile_kernel(stl_handle h, int32_t backward, int64_t T, const stl_launch *launch,
+                                      int32_t *tile_out, int32_t *smem_bytes);
 
 /* Bytes of device workspace that stl_robustness (backward = 0) or stl_robustness_backward
  * (backward = 1) needs for B traces of length T; 0 when everything fits on chip. */

@@ -32,6 +32,11 @@ class StlNode(ctypes.Structure):
                 ("pred_offset", ctypes.c_int32), ("pred_c", ctypes.c_float)]
 
 
+KERNEL_AUTO, KERNEL_INTERPRETER, KERNEL_COMPILED = 0, 1, 2
+KERNELS = {"auto": KERNEL_AUTO, "interpreter": KERNEL_INTERPRETER, "compiled": KERNEL_COMPILED}
+KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
+
+
 class StlParams(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tau", ctypes.c_float), ("mask_c", ctypes.c_float),
                 ("mask_eps", ctypes.c_float)]
@@ -39,7 +44,7 @@ class StlParams(ctypes.Structure):
 
 class StlLaunch(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("threads", ctypes.c_int32), ("segment", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32)]
 
 
 class StlError(RuntimeError):
@@ -180,13 +185,29 @@ class Formula:
     def handle(self):
         return self._h
 
-    def set_launch(self, tile=0, threads=0, segment=0):
-        check(load().stl_set_launch(self._h, ctypes.byref(StlLaunch(tile, threads, segment, 0))))
+    def set_launch(self, tile=0, threads=0, segment=0, kernel=KERNEL_AUTO):
+        """stl_set_launch; kernel: "auto", "interpreter" or "compiled" (or the stl_kernel value)."""
+        k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        check(load().stl_set_launch(self._h, ctypes.byref(StlLaunch(tile, threads, segment, k))))
 
     def get_launch(self, B, T, p: StlParams, backward=False):
         out = StlLaunch()
         check(load().stl_get_launch(self._h, B, T, ctypes.byref(p), int(backward), ctypes.byref(out)))
-        return dict(tile=out.tile, threads=out.threads, segment=out.segment, grid=out.reserved)
+        return dict(tile=out.tile, threads=out.threads, segment=out.segment, kernel=KERNEL_NAMES.get(out.kernel))
+
+    def compile_kernel(self, backward=False, T=1 << 20, threads=0, tile=0):
+        """stl_compile_kernel: generate and compile this formula's kernel for one direction
+        (NVRTC; no GPU needed).  Returns (tile, dynamic shared memory bytes)."""
+        lib = load()
+        fn = lib.stl_compile_kernel
+        if fn.argtypes is None:
+            fn.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(StlLaunch),
+                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+            fn.restype = ctypes.c_int32
+        t, sm = ctypes.c_int32(), ctypes.c_int32()
+        check(fn(self._h, int(backward), int(T), ctypes.byref(StlLaunch(tile, threads, 0, KERNEL_COMPILED)),
+                 ctypes.byref(t), ctypes.byref(sm)))
+        return int(t.value), int(sm.value)
 
     def autotune(self, sig_ptr, B, T, bounds_ptr, p: StlParams, backward, grad_out_ptr, out_ptr, gb_ptr, ws_ptr,
                  ws_bytes, stream):
@@ -202,7 +223,8 @@ class Formula:
         best, ms = StlLaunch(), ctypes.c_float()
         check(fn(self._h, sig_ptr, B, T, bounds_ptr, ctypes.byref(p), int(backward), grad_out_ptr, out_ptr, gb_ptr,
                  ws_ptr, ws_bytes, stream, ctypes.byref(best), ctypes.byref(ms)))
-        return dict(tile=best.tile, threads=best.threads, segment=best.segment), float(ms.value)
+        return (dict(tile=best.tile, threads=best.threads, segment=best.segment,
+                     kernel=KERNEL_NAMES.get(best.kernel)), float(ms.value))
 
     def workspace_size(self, B, T, p: StlParams, backward=False) -> int:
         n = ctypes.c_size_t()

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstl.so")
-SOURCES = [f"stl_kern_{nt}_{d}{m}{r}.cu" for nt in (64, 256, 512) for d in "fb" for m in "hs" for r in ("", "_r")] + ["stl_kernels.cu", "stl_capi.cu", "stl_noalloc.cu", "stl_plan.cu", "stl_gemm.cu", "stl_mining.cu"]
+SOURCES = [f"stl_kern_{nt}_{d}{m}{r}.cu" for nt in (64, 256, 512) for d in "fb" for m in "hs" for r in ("", "_r")] + ["stl_kernels.cu", "stl_capi.cu", "stl_noalloc.cu", "stl_plan.cu", "stl_gemm.cu", "stl_mining.cu", "stl_fk.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -27,7 +27,23 @@ def nvcc() -> str:
 
 def _flags(extra=()):
     return [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-            "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr", *extra]
+            "-I", os.path.join(ROOT, "include"), "-I", BUILD, "--expt-relaxed-constexpr", *extra]
+
+
+FK_DEV = os.path.join(CSRC, "stl_fk_dev.cuh")
+FK_INC = os.path.join(BUILD, "stl_fk_src.inc")
+
+
+def _embed_fk_source():
+    """The device building blocks of the formula-compiled kernels, as a C++ raw string (NVRTC
+    compiles them at run time together with the generated code)."""
+    with open(FK_DEV) as fh:
+        src = fh.read()
+    assert ")FKSRC" not in src
+    text = 'R"FKSRC(' + src + ')FKSRC"\n'
+    if not os.path.exists(FK_INC) or open(FK_INC).read() != text:
+        with open(FK_INC, "w") as fh:
+            fh.write(text)
 
 
 def _stale(obj, srcs):
@@ -46,13 +62,18 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         force = True
     with open(stamp, "w") as fh:
         fh.write(arch)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    _embed_fk_source()
+    fk_only = {"stl_fk_dev.cuh", "stl_fk.h"}   # only the compiled-kernel units depend on these
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")) and f not in fk_only]
     headers.append(os.path.join(ROOT, "include", "stl.h"))
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src + ".o")
-        if force or _stale(o, [s, *headers]):
+        deps = [s, *headers]
+        if src in ("stl_fk.cu", "stl_capi.cu"):
+            deps += [os.path.join(CSRC, "stl_fk.h"), FK_INC]
+        if force or _stale(o, deps):
             extra = ["-Xptxas", "-v"] if ptxas_info else []
             jobs.append([nvcc(), *_flags(extra), "-c", s, "-o", o])
     def run(cmd):
@@ -68,7 +89,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     objs = [os.path.join(BUILD, s + ".o") for s in SOURCES]
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
+        run([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

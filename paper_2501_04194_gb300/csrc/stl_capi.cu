@@ -16,6 +16,7 @@
 
 #include "../../include/stl.h"
 #include "stl_internal.cuh"
+#include "stl_fk.h"
 
 namespace {
 
@@ -516,12 +517,60 @@ void stl_destroy(stl_handle h) {
   delete h;
 }
 
+namespace {
+FkFormula fk_formula(const stl_program *h) { return FkFormula{&h->nodes, &h->w, h->D, h->n_slots}; }
+
+// which kernel serves this call: the handle's choice for the direction, or (automatic) the
+// formula-compiled kernel where it applies to a call of at least 2^20 samples
+stl_status resolve_kernel(const stl_program *h, long long B, long long T, const stl_params &p, bool bwd, int *kind) {
+  const int want = h->launch_dir[bwd ? 1 : 0].kernel;
+  std::string why;
+  if (want == STL_KERNEL_INTERPRETER) { *kind = want; return STL_OK; }
+  const bool ok = stl_fk_eligible(fk_formula(h), p, T, &why) && stl_fk_available(&why);
+  if (want == STL_KERNEL_COMPILED) {
+    if (!ok) return fail(STL_ERR_UNSUPPORTED, "compiled kernel not applicable: %s", why.c_str());
+    *kind = want;
+    return STL_OK;
+  }
+  // automatic: the compiled kernel unless a launch shape for the interpreter was set
+  const stl_launch &l = h->launch_dir[bwd ? 1 : 0];
+  const bool shape_set = l.tile || l.threads || l.segment;
+  *kind = (ok && !shape_set && B * T >= (1LL << 20)) ? STL_KERNEL_COMPILED : STL_KERNEL_INTERPRETER;
+  return STL_OK;
+}
+
+stl_status fk_launch(const stl_program *h, bool bwd, long long B, long long T, const float *sig, const float *gout,
+                     float *out, float *gsig, void *stream) {
+  FkCall c;
+  c.bwd = bwd;
+  c.B = B;
+  c.T = T;
+  c.sig = sig;
+  c.gout = gout;
+  c.out = out;
+  c.gsig = gsig;
+  const stl_launch &l = h->launch_dir[bwd ? 1 : 0];
+  c.threads = l.threads;
+  c.tile = l.tile;
+  c.segment = l.segment;
+  c.stream = stream;
+  std::string err;
+  stl_status s = stl_fk_run(fk_formula(h), c, &err);
+  if (s) return fail(s, "%s", err.c_str());
+  return STL_OK;
+}
+}  // namespace
+
 stl_status stl_set_launch(stl_handle h, const stl_launch *launch) {
   if (!h || !launch) return fail(STL_ERR_INVALID_ARG, "NULL argument");
   if (launch->threads && launch->threads != 64 && launch->threads != 256 && launch->threads != 512)
     return fail(STL_ERR_INVALID_ARG, "threads must be 0, 64, 256 or 512");
   if (launch->tile < 0 || (launch->tile && launch->tile % 32) || launch->segment < 0)
     return fail(STL_ERR_INVALID_ARG, "tile must be a non-negative multiple of 32; segment >= 0");
+  if (launch->kernel < STL_KERNEL_AUTO || launch->kernel > STL_KERNEL_COMPILED)
+    return fail(STL_ERR_INVALID_ARG, "kernel must be STL_KERNEL_AUTO, _INTERPRETER or _COMPILED");
+  if (launch->kernel == STL_KERNEL_COMPILED && launch->threads == 64)
+    return fail(STL_ERR_INVALID_ARG, "compiled kernels run 256 or 512 threads");
   h->launch_dir[0] = h->launch_dir[1] = *launch;
   return STL_OK;
 }
@@ -531,13 +580,47 @@ stl_status stl_get_launch(stl_handle h, int64_t B, int64_t T, const stl_params *
   if (!out) return fail(STL_ERR_INVALID_ARG, "out is NULL");
   stl_status s = check_call(h, (const float *)1, B, T, (const float *)1, p);
   if (s) return s;
+  int kind = 0;
+  s = resolve_kernel(h, B, T, *p, backward != 0, &kind);
+  if (s) return s;
+  if (kind == STL_KERNEL_COMPILED) {
+    const stl_launch &l = h->launch_dir[backward ? 1 : 0];
+    int tile = 0;
+    std::string err;
+    s = stl_fk_plan_shape(fk_formula(h), backward != 0, l.threads, l.tile, &tile, nullptr, &err);
+    if (s) return fail(s, "%s", err.c_str());
+    out->tile = tile;
+    out->threads = l.threads ? l.threads : 512;
+    out->segment = l.segment;
+    out->kernel = STL_KERNEL_COMPILED;
+    return STL_OK;
+  }
   Plan pl;
   s = make_plan(h, B, T, *p, backward != 0, pl);
   if (s) return s;
   out->tile = pl.P.tile;
   out->threads = pl.threads;
   out->segment = pl.P.seg;
-  out->reserved = pl.grid;
+  out->kernel = STL_KERNEL_INTERPRETER;
+  return STL_OK;
+}
+
+stl_status stl_compile_kernel(stl_handle h, int32_t backward, int64_t T, const stl_launch *launch, int32_t *tile_out,
+                              int32_t *smem_bytes) {
+  if (!h) return fail(STL_ERR_INVALID_ARG, "handle is NULL");
+  if (T < 1 || T > (1LL << 30)) return fail(STL_ERR_INVALID_ARG, "T must be in [1, 2^30]");
+  stl_params hp{};
+  hp.mode = STL_HARD;
+  std::string why;
+  if (!stl_fk_eligible(fk_formula(h), hp, T, &why)) return fail(STL_ERR_UNSUPPORTED, "%s", why.c_str());
+  const int nt = launch ? launch->threads : 0, tile = launch ? launch->tile : 0;
+  if (tile < 0 || tile % 32) return fail(STL_ERR_INVALID_ARG, "tile must be a non-negative multiple of 32");
+  int to = 0, sm = 0;
+  std::string err;
+  stl_status s = stl_fk_compile_only(fk_formula(h), backward != 0, T, nt, tile, &to, &sm, nullptr, &err);
+  if (s) return fail(s, "%s", err.c_str());
+  if (tile_out) *tile_out = to;
+  if (smem_bytes) *smem_bytes = sm;
   return STL_OK;
 }
 
@@ -548,6 +631,10 @@ stl_status stl_workspace_size(stl_handle h, int64_t B, int64_t T, const stl_para
   stl_status s = check_call(h, (const float *)1, B, T, (const float *)1, p);
   if (s) return s;
   if (B == 0) return STL_OK;
+  int kind = 0;
+  s = resolve_kernel(h, B, T, *p, backward != 0, &kind);
+  if (s) return s;
+  if (kind == STL_KERNEL_COMPILED) return STL_OK;   // everything on chip
   Plan pl;
   s = make_plan(h, B, T, *p, backward != 0, pl);
   if (s) return s;
@@ -562,6 +649,10 @@ stl_status stl_robustness(stl_handle h, const float *sig, int64_t B, int64_t T, 
   if (s) return s;
   if (B > 0 && !out) return fail(STL_ERR_INVALID_ARG, "out is NULL");
   if (B == 0) return STL_OK;
+  int kind = 0;
+  s = resolve_kernel(h, B, T, *p, false, &kind);
+  if (s) return s;
+  if (kind == STL_KERNEL_COMPILED) return fk_launch(h, false, B, T, sig, nullptr, out, nullptr, stream);
   Plan pl;
   s = make_plan(h, B, T, *p, false, pl);
   if (s) return s;
@@ -592,6 +683,10 @@ stl_status backward_launch(stl_handle h, const float *sig, int64_t B, int64_t T,
   if (s) return s;
   if (B > 0 && (!grad_out || !grad_sig)) return fail(STL_ERR_INVALID_ARG, "grad_out / grad_sig is NULL");
   if (B == 0) return STL_OK;
+  int kind = 0;
+  s = resolve_kernel(h, B, T, *p, true, &kind);
+  if (s) return s;
+  if (kind == STL_KERNEL_COMPILED) return fk_launch(h, true, B, T, sig, grad_out, out, grad_sig, stream);
   Plan pl;
   s = make_plan(h, B, T, *p, true, pl);
   if (s) return s;
@@ -1044,14 +1139,20 @@ bool cache_lookup(const char *path, const std::string &key, stl_launch *out) {
     std::string k;
     stl_launch l{};
     double ms;
-    if (is >> k >> l.tile >> l.threads >> l.segment >> ms && k == key) { *out = l; found = true; }
+    // line: key tile threads segment ms [kernel]
+    if (is >> k >> l.tile >> l.threads >> l.segment >> ms && k == key) {
+      int kind = 0;
+      if (is >> kind) l.kernel = kind;
+      *out = l;
+      found = true;
+    }
   }
   return found;
 }
 
 void cache_store(const char *path, const std::string &key, const stl_launch &l, double ms) {
   std::ofstream f(path, std::ios::app);
-  if (f) f << key << " " << l.tile << " " << l.threads << " " << l.segment << " " << ms << "\n";
+  if (f) f << key << " " << l.tile << " " << l.threads << " " << l.segment << " " << ms << " " << l.kernel << "\n";
 }
 
 }  // namespace
@@ -1084,8 +1185,22 @@ stl_status stl_autotune(stl_handle h, const float *sig, int64_t B, int64_t T, co
       stl_launch l{};
       l.threads = nt;
       l.tile = std::max(256, (nt * mult / 32) * 32);
+      l.kernel = STL_KERNEL_INTERPRETER;
       cands.push_back(l);
     }
+  // formula-compiled kernels (CTA size x tile), where they apply
+  {
+    std::string why;
+    if (stl_fk_eligible(fk_formula(h), *p, T, &why) && stl_fk_available(&why))
+      for (int nt : {512, 256})
+        for (int mult : bwd ? std::vector<int>{7, 5} : std::vector<int>{15, 11, 7}) {
+          stl_launch l{};
+          l.threads = nt;
+          l.tile = nt * mult;
+          l.kernel = STL_KERNEL_COMPILED;
+          cands.push_back(l);
+        }
+  }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(STL_ERR_CUDA, "cudaEventCreate failed");
@@ -1182,6 +1297,7 @@ stl_status stl_set_autotune(stl_set_handle s, int64_t n_traces, int64_t T_max, c
       stl_launch l{};
       l.threads = nt;
       l.tile = std::max(256, (nt * mult / 32) * 32);
+      l.kernel = STL_KERNEL_INTERPRETER;
       cands.push_back(l);
     }
   cudaEvent_t e0, e1;

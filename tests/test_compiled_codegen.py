@@ -1,0 +1,59 @@
+"""CPU checks of the formula-compiled kernels' code generation: NVRTC compiles the generated
+source for sm_103a without a GPU (stl_compile_kernel), the tile shrinks until the buffers fit
+in shared memory, and formulas outside the compiled set are refused on the host."""
+import math
+
+import pytest
+
+import workloads as W
+
+
+@pytest.fixture(scope="module")
+def stl():
+    import paper_2501_04194_gb300 as m
+    try:
+        m.load()
+    except ImportError as e:   # the library is built by __graft_entry__.build()
+        pytest.skip(str(e))
+    return m
+
+
+CASES = [
+    ("config1", W.config1_formula(), 3),
+    ("config0", W.config0_formula(), 2),
+    ("table3_phi6", W.table3_formulas(D=2, I=(2, 37))[5], 2),
+    ("pads", W.Always(0, 50, W.Or(W.Eventually(10, 30, W.gt([1, 0], 0.2), pad=0.0),
+                                  W.Not(W.Until(0, 20, W.gt([0, 1], -0.1), W.lt([1, 0], 0.0))))), 2),
+    ("long_until", W.Until(300, 4000, W.gt([1], -0.5), W.lt([1], 0.5)), 1),
+]
+
+
+@pytest.mark.parametrize("name,tree,D", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("backward", [False, True])
+def test_generated_kernels_compile(stl, name, tree, D, backward):
+    f = stl.Formula(tree, D=D)
+    tile, smem = f.compile_kernel(backward=backward, T=50000)
+    assert tile % 32 == 0 and 512 <= tile <= (7680 if not backward else 3584)
+    assert 0 < smem <= 227 * 1024
+
+
+def test_tile_shrinks_to_fit_shared_memory(stl):
+    f = stl.Formula(W.config1_formula(), D=3)
+    t_fwd, s_fwd = f.compile_kernel(backward=False, T=50000)
+    t_bwd, s_bwd = f.compile_kernel(backward=True, T=50000)
+    assert t_fwd == 7680            # 512 threads x runs of 15
+    assert t_bwd < 3584             # the 64-bit adjoint rings do not fit at 512 x 7
+    t_small, s_small = f.compile_kernel(backward=True, T=50000, threads=256, tile=1024)
+    assert t_small == 1024 and s_small < s_bwd
+
+
+@pytest.mark.parametrize("tree,D", [
+    (W.Eventually(0, math.inf, W.gt([1], 0.0)), 1),                       # unbounded interval
+    (W.Eventually(0, 10, W.gt([1], 0.0), slot=0), 1),                     # per-trace bounds
+    (W.And(W.norm_lt([1.0, 1.0], [0.0, 0.0], 1.0), W.gt([1, 0], 0.0)), 2),   # norm predicate
+    (W.Always(0, 20000, W.gt([1], 0.0)), 1),                              # interval past 16000
+])
+def test_outside_the_compiled_set_is_refused(stl, tree, D):
+    f = stl.Formula(tree, D=D, n_slots=1)
+    with pytest.raises(stl.StlError):
+        f.compile_kernel(backward=False)

@@ -135,7 +135,8 @@ def test_autotune_keeps_parity_and_uses_the_cache(stl, tmp_path, monkeypatch):
 def test_ragged_autotuned_set_matches_the_default_plan(stl, mode):
     # stl_set_autotune picks a launch shape per direction; the results are those of the default
     # plan (hard: bit for bit, values and fixed-point gradients; smooth: within tolerance)
-    wl = W.config3_workload(n_traces=48, t_lo=50, t_hi=6000, seed=9)
+    # (smooth: shorter traces, the FP64 oracle's literal smooth-Until adjoint is O(b^2) per sample)
+    wl = W.config3_workload(n_traces=48, t_lo=50, t_hi=6000 if mode == "hard" else 1500, seed=9)
     lengths = np.diff(wl["offsets"])
     order = np.argsort(-lengths, kind="stable").astype(np.int32)
     rb0, fs, _ = make_batch(stl, wl, mode, order=order)
