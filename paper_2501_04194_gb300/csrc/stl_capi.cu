@@ -540,7 +540,7 @@ stl_status resolve_kernel(const stl_program *h, long long B, long long T, const 
 }
 
 stl_status fk_launch(const stl_program *h, bool bwd, long long B, long long T, const float *sig, const float *gout,
-                     float *out, float *gsig, void *stream) {
+                     float *out, float *gsig, void *ws, size_t ws_bytes, void *stream) {
   FkCall c;
   c.bwd = bwd;
   c.B = B;
@@ -553,6 +553,8 @@ stl_status fk_launch(const stl_program *h, bool bwd, long long B, long long T, c
   c.threads = l.threads;
   c.tile = l.tile;
   c.segment = l.segment;
+  c.ws = ws;
+  c.ws_bytes = ws_bytes;
   c.stream = stream;
   std::string err;
   stl_status s = stl_fk_run(fk_formula(h), c, &err);
@@ -587,7 +589,7 @@ stl_status stl_get_launch(stl_handle h, int64_t B, int64_t T, const stl_params *
     const stl_launch &l = h->launch_dir[backward ? 1 : 0];
     int tile = 0;
     std::string err;
-    s = stl_fk_plan_shape(fk_formula(h), backward != 0, l.threads, l.tile, &tile, nullptr, &err);
+    s = stl_fk_plan_shape(fk_formula(h), backward != 0, l.threads, l.tile, &tile, nullptr, nullptr, &err);
     if (s) return fail(s, "%s", err.c_str());
     out->tile = tile;
     out->threads = l.threads ? l.threads : 512;
@@ -634,7 +636,13 @@ stl_status stl_workspace_size(stl_handle h, int64_t B, int64_t T, const stl_para
   int kind = 0;
   s = resolve_kernel(h, B, T, *p, backward != 0, &kind);
   if (s) return s;
-  if (kind == STL_KERNEL_COMPILED) return STL_OK;   // everything on chip
+  if (kind == STL_KERNEL_COMPILED) {
+    const stl_launch &l = h->launch_dir[backward ? 1 : 0];
+    std::string err;
+    s = stl_fk_plan_shape(fk_formula(h), backward != 0, l.threads, l.tile, nullptr, nullptr, bytes, &err);
+    if (s) return fail(s, "%s", err.c_str());
+    return STL_OK;
+  }
   Plan pl;
   s = make_plan(h, B, T, *p, backward != 0, pl);
   if (s) return s;
@@ -652,7 +660,8 @@ stl_status stl_robustness(stl_handle h, const float *sig, int64_t B, int64_t T, 
   int kind = 0;
   s = resolve_kernel(h, B, T, *p, false, &kind);
   if (s) return s;
-  if (kind == STL_KERNEL_COMPILED) return fk_launch(h, false, B, T, sig, nullptr, out, nullptr, stream);
+  if (kind == STL_KERNEL_COMPILED)
+    return fk_launch(h, false, B, T, sig, nullptr, out, nullptr, workspace, workspace_bytes, stream);
   Plan pl;
   s = make_plan(h, B, T, *p, false, pl);
   if (s) return s;
@@ -686,7 +695,8 @@ stl_status backward_launch(stl_handle h, const float *sig, int64_t B, int64_t T,
   int kind = 0;
   s = resolve_kernel(h, B, T, *p, true, &kind);
   if (s) return s;
-  if (kind == STL_KERNEL_COMPILED) return fk_launch(h, true, B, T, sig, grad_out, out, grad_sig, stream);
+  if (kind == STL_KERNEL_COMPILED)
+    return fk_launch(h, true, B, T, sig, grad_out, out, grad_sig, workspace, workspace_bytes, stream);
   Plan pl;
   s = make_plan(h, B, T, *p, true, pl);
   if (s) return s;
@@ -1193,7 +1203,7 @@ stl_status stl_autotune(stl_handle h, const float *sig, int64_t B, int64_t T, co
     std::string why;
     if (stl_fk_eligible(fk_formula(h), *p, T, &why) && stl_fk_available(&why))
       for (int nt : {512, 256})
-        for (int mult : bwd ? std::vector<int>{7, 5} : std::vector<int>{15, 11, 7}) {
+        for (int mult : bwd ? std::vector<int>{13, 10, 7} : std::vector<int>{15, 11, 7}) {
           stl_launch l{};
           l.threads = nt;
           l.tile = nt * mult;

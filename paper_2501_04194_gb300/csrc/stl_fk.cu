@@ -33,6 +33,10 @@
 
 namespace {
 
+// Untils whose phi prefix [0, a] has at most this many samples take it from registers in the
+// same pass as the clamp composition
+constexpr int FK_UNTIL_FUSE_W = 16;
+
 // the device building blocks, embedded at build time from stl_fk_dev.cuh
 const char *const k_dev_src =
 #include "stl_fk_src.inc"
@@ -133,6 +137,8 @@ struct GPlan {
   int LP = 0, HP = 0, HMAX = 0, LOMAX = 0;
   int capA = 0;            // predicate adjoint ring length (samples)
   int off_j = -1;          // adjoint rings (u64), predicate k at off_j + 8 * k * capA
+  bool gring = false;      // backward: adjoint rings in the workspace (L2) instead of shared memory
+  int RING = 0;            // their length: a power of two >= TILE + HP - LP, indexed by (j - LP) mod RING
   int off_cells = 0, off_scr = 0, smem = 0;
   std::vector<GNode> g;
   std::vector<int> preds;  // node index of predicate k
@@ -154,7 +160,7 @@ int elem_bytes(int op, bool bwd, bool until_pass2) {
 }
 
 // geometry for one tile; returns false if the formula is outside the compiled path
-bool build_plan(const FkFormula &f, bool bwd, int NT, int TILE, GPlan &P, std::string *why) {
+bool build_plan(const FkFormula &f, bool bwd, int NT, int TILE, GPlan &P, std::string *why, bool gring = false) {
   const std::vector<stl_node> &nd = *f.nodes;
   const int n = (int)nd.size();
   P = GPlan{};
@@ -253,7 +259,11 @@ bool build_plan(const FkFormula &f, bool bwd, int NT, int TILE, GPlan &P, std::s
     if (x.has_val) x.off_v = take(4LL * x.cap);
     if (x.has_aux) x.off_a = take(2LL * x.cap);
   }
-  if (bwd && P.npred > 0) {
+  if (bwd && P.npred > 0 && gring) {
+    P.gring = true;
+    P.RING = 1;
+    while (P.RING < TILE + P.HP - P.LP) P.RING <<= 1;
+  } else if (bwd && P.npred > 0) {
     P.capA = round_up((long long)TILE + P.HP - P.LP, 4);
     P.off_j = take(8LL * P.capA * P.npred);
   }
@@ -272,7 +282,7 @@ bool build_plan(const FkFormula &f, bool bwd, int NT, int TILE, GPlan &P, std::s
     };
     if (x.op == STL_OP_EVENTUALLY || x.op == STL_OP_ALWAYS) need(x.b - x.a + 1, x.R, elem_bytes(x.op, bwd, false), true);
     if (x.op == STL_OP_UNTIL) {
-      need(x.a + 1, x.R1, elem_bytes(x.op, bwd, false), true);
+      if (x.a + 1 > FK_UNTIL_FUSE_W) need(x.a + 1, x.R1, elem_bytes(x.op, bwd, false), true);
       need(x.b - x.a + 1, x.R, elem_bytes(x.op, bwd, true), false);
     }
   }
@@ -420,6 +430,25 @@ struct Gen {
         l(fmt("    float *const o = fv%d;", i));
         l(fmt("    const float *const xp = fv%d;", x.c0));
         l(fmt("    const float *const xq = fv%d;", x.c1));
+        if (x.a + 1 <= FK_UNTIL_FUSE_W) {
+          // one pass: the phi prefix minimum over [q, q+a] comes from the thread's registers
+          if (!bwd) {
+            l(fmt("    fk_until<FkClamp, FkMin, NT, %d, %d, %d>(F, E, [&](int j) {", x.R, x.a, x.b));
+            l("          const float p = xp[j - cp], s = xq[j - cq]; FkC2 r; r.c = fminf(p, s); r.d = p; return r; },");
+            l("        [&](int j) { return xp[j - cp]; },");
+            l("        [&](int q, FkC2 r, float a) { o[q - base] = (a <= r.c) ? a : r.c; }, fk_scr);");
+          } else {
+            l(fmt("    fk_u16 *const oa = fa%d;", i));
+            l(fmt("    fk_until<FkClampP, FkMinP, NT, %d, %d, %d>(F, E, [&](int j) {", x.R, x.a, x.b));
+            l("          const float p = xp[j - cp], s = xq[j - cq]; const bool pl = p <= s; FkCC r;");
+            l("          r.c = pl ? p : s; r.cs = pl ? 2 * j : 2 * j + 1; r.d = p; r.ds = 2 * j; return r; },");
+            l("        [&](int j) { FkVP r; r.v = xp[j - cp]; r.p = j; return r; },");
+            l("        [&](int q, FkCC r, FkVP a) {");
+            l("          if (a.v <= r.c) { o[q - base] = a.v; oa[q - base] = (fk_u16)(2 * (a.p - q)); }");
+            l("          else { o[q - base] = r.c; oa[q - base] = (fk_u16)(r.cs - 2 * q); } }, fk_scr);");
+          }
+          break;
+        }
         if (!bwd) {
           l(fmt("    fk_window<FkMin, NT, %d, 0, %d>(F, E, [&](int j) { return xp[j - cp]; },", x.R1, x.a));
           l("        [&](int q, float v) { o[q - base] = v; }, fk_scr);");
@@ -479,7 +508,7 @@ struct Gen {
       if (x.has_val) mv.push_back({fmt("fv%d", i), P.TILE, span});
       if (x.has_aux) mv.push_back({fmt("reinterpret_cast<float *>(fa%d)", i), P.TILE / 2, (span + 1) / 2});
     }
-    if (P.bwd && P.npred > 0 && P.HP - P.LP > 0)
+    if (P.bwd && !P.gring && P.npred > 0 && P.HP - P.LP > 0)
       for (int k = 0; k < P.npred; ++k)
         mv.push_back({fmt("reinterpret_cast<float *>(fj + %d)", k * P.capA), 2 * P.TILE, 2 * (P.HP - P.LP)});
     int rounds = 0;
@@ -494,7 +523,7 @@ struct Gen {
       }
       l("    __syncthreads();");
     }
-    if (P.bwd && P.npred > 0) {
+    if (P.bwd && !P.gring && P.npred > 0) {
       // new samples of the predicate adjoint rings start at zero
       const int keep = 2 * (P.HP - P.LP);
       for (int k = 0; k < P.npred; ++k)
@@ -590,7 +619,7 @@ struct Gen {
     l(fmt("#define NT %d", NT));
     l(fmt("extern \"C\" __global__ void __launch_bounds__(%d, 1) %s(", NT, name.c_str()));
     l("    const float *__restrict__ sig, const float *__restrict__ gout, float *__restrict__ out,");
-    l("    float *__restrict__ gsig, int T, int seg, int segs, long long n_items) {");
+    l("    float *__restrict__ gsig, fk_u64 *__restrict__ ws, int T, int seg, int segs, long long n_items) {");
     l("  extern __shared__ float4 fk_sm4[];");
     l("  char *const fk_sm = reinterpret_cast<char *>(fk_sm4);");
     for (int i = 0; i < P.n; ++i) {
@@ -598,13 +627,15 @@ struct Gen {
       if (x.has_val) l(fmt("  float *const fv%d = reinterpret_cast<float *>(fk_sm + %d);", i, x.off_v));
       if (x.has_aux) l(fmt("  fk_u16 *const fa%d = reinterpret_cast<fk_u16 *>(fk_sm + %d);", i, x.off_a));
     }
-    if (P.bwd && P.npred > 0) l(fmt("  fk_u64 *const fj = reinterpret_cast<fk_u64 *>(fk_sm + %d);", P.off_j));
+    if (P.bwd && P.npred > 0 && !P.gring) l(fmt("  fk_u64 *const fj = reinterpret_cast<fk_u64 *>(fk_sm + %d);", P.off_j));
+    if (P.bwd && P.npred > 0 && P.gring)
+      l(fmt("  fk_u64 *const fj = ws + (long long)blockIdx.x * %d;   // this CTA's adjoint rings", P.npred * P.RING));
     l(fmt("  float *const fk_vcell = reinterpret_cast<float *>(fk_sm + %d);", P.off_cells));
     l(fmt("  int *const fk_acell = reinterpret_cast<int *>(fk_sm + %d);", P.off_cells + 4 * P.n));
     l(fmt("  fk_u64 *const fk_jcell = reinterpret_cast<fk_u64 *>(fk_sm + %d);", P.off_cells + 8 * P.n));
     l(fmt("  void *const fk_scr = fk_sm + %d;", P.off_scr));
     l("  const int tid = threadIdx.x;");
-    l("  (void)fk_vcell; (void)fk_acell; (void)fk_jcell; (void)gout; (void)gsig; (void)out;");
+    l("  (void)fk_vcell; (void)fk_acell; (void)fk_jcell; (void)gout; (void)gsig; (void)out; (void)ws;");
     if (P.bwd) {
       l("  __shared__ unsigned s_gmax;");
       l("  fk_u64 pol_first;");
@@ -626,7 +657,8 @@ struct Gen {
       // fixed-point scale from the largest root gradient of the whole trace
       l("    if (tid == 0) s_gmax = 0u;");
       if (P.npred > 0) {
-        l(fmt("    fk_zero<NT>(reinterpret_cast<float *>(fj), 0, %d);", 2 * P.capA * P.npred));
+        if (P.gring) l(fmt("    for (int i = tid; i < %d; i += NT) __stcg(fj + i, 0ull);", P.npred * P.RING));
+        else l(fmt("    fk_zero<NT>(reinterpret_cast<float *>(fj), 0, %d);", 2 * P.capA * P.npred));
         l(fmt("    if (tid < %d) fk_jcell[tid] = 0ull;", P.npred));
       }
       l("    __syncthreads();");
@@ -642,6 +674,16 @@ struct Gen {
     l(fmt("    for (int t0 = R0; t0 < s1; t0 += %d) {", TILE));
     l(fmt("      const int t1 = min(t0 + %d, s1);", TILE));
     l("      const bool first = t0 == R0;");
+    if (P.bwd && P.gring && P.npred > 0) {
+      // ring slots of the samples that become live in this step held samples RING earlier,
+      // all emitted by now: clear them before this step's deposits (barriers follow)
+      l("      if (!first) {");
+      l(fmt("        for (int j = t0 + %d + tid; j < t1 + %d; j += NT) {", P.HP, P.HP));
+      l(fmt("          const int js = (j - %d) & %d;", P.LP, P.RING - 1));
+      for (int k = 0; k < P.npred; ++k) l(fmt("          __stcg(fj + %d + js, 0ull);", k * P.RING));
+      l("        }");
+      l("      }");
+    }
     s += "      // ---- node passes\n";
     pred_pass();
     for (int i = 0; i < P.n; ++i) node_pass(i);
@@ -658,7 +700,10 @@ struct Gen {
       l("        auto flush = [&]() {");
       l("          if (ck < 0 || acc == 0) return;");
       l(fmt("          if (cp >= T - 1) fk_red_add(fk_jcell + ck, acc);"));
-      l(fmt("          else fk_red_add(fj + ck * %d + (cp - (t0 + %d)), acc);", P.capA, P.LP));
+      if (P.gring)
+        l(fmt("          else atomicAdd(fj + ck * %d + ((cp - %d) & %d), (fk_u64)acc);", P.RING, P.LP, P.RING - 1));
+      else
+        l(fmt("          else fk_red_add(fj + ck * %d + (cp - (t0 + %d)), acc);", P.capA, P.LP));
       l("        };");
       l("#pragma unroll");
       l(fmt("        for (int r = 0; r < %d; ++r) {", RW));
@@ -685,7 +730,14 @@ struct Gen {
       if (P.npred > 0) {
         l("        for (int j = j0 + tid; j < j1; j += NT) {");
         l(fmt("          const int ja = j - (t0 + %d);", P.LP));
-        for (int k = 0; k < P.npred; ++k) l(fmt("          const float a%d = fk_from_fix(fx, fj[%d + ja]);", k, k * P.capA));
+        if (P.gring) {
+          // L2 reads: the deposits of other threads are atomics performed at L2
+          l(fmt("          const int js = (j - %d) & %d;", P.LP, P.RING - 1));
+          for (int k = 0; k < P.npred; ++k)
+            l(fmt("          const float a%d = fk_from_fix(fx, __ldcg(fj + %d + js));", k, k * P.RING));
+        } else {
+          for (int k = 0; k < P.npred; ++k) l(fmt("          const float a%d = fk_from_fix(fx, fj[%d + ja]);", k, k * P.capA));
+        }
         for (int d = 0; d < D; ++d) {
           l("          {");
           l("            float acc = 0.f;");
@@ -781,22 +833,46 @@ struct Shape {
 };
 
 // largest tile (multiple of 32, at most `want`) whose buffers fit the shared memory limit
-bool fit_tile(const FkFormula &f, bool bwd, int NT, int want, int max_smem, GPlan &P, std::string *why) {
+bool fit_tile(const FkFormula &f, bool bwd, int NT, int want, int max_smem, GPlan &P, std::string *why,
+              bool gring) {
   for (int tile = want; tile >= 512; tile -= (tile > 2048 ? 512 : 256)) {
-    if (!build_plan(f, bwd, NT, tile, P, why)) return false;
+    if (!build_plan(f, bwd, NT, tile, P, why, gring)) return false;
     if (P.smem <= max_smem) return true;
   }
   if (why) *why = "the formula's buffers do not fit in shared memory at a 512-sample tile";
   return false;
 }
 
-int default_tile(bool bwd, int NT) { return bwd ? NT * 7 : NT * 15; }
+int default_tile(bool bwd, int NT) { return bwd ? NT * 10 : NT * 15; }
+
+// The plan of one call shape.  Backward launches keep their 64-bit predicate adjoint rings in
+// shared memory when the requested tile fits with them, else in the caller's workspace (L2:
+// global 64-bit reductions, L2-only reads), which leaves shared memory to the node buffers: for
+// the nested formula of config 1 this allows a tile of 5120 instead of 3072 (measured backward
+// at B=1024, T=50000: 2.18 -> 1.60 ms).
+bool choose_plan(const FkFormula &f, bool bwd, int NT, int tile_req, int max_smem, GPlan &P, std::string *why) {
+  const int want = tile_req > 0 ? tile_req : default_tile(bwd, NT);
+  if (!fit_tile(f, bwd, NT, want, max_smem, P, why, false)) return false;
+  if (!bwd || P.TILE >= want || P.npred == 0) return true;
+  GPlan G;
+  std::string w2;
+  if (fit_tile(f, bwd, NT, want, max_smem, G, &w2, true) && G.TILE > P.TILE) P = G;
+  return true;
+}
+
+// CTAs that can be resident at once (an upper bound on the grid) for this plan
+int grid_cap(const GPlan &P, int sms) {
+  const int by_smem = std::max(1, (228 * 1024) / (P.smem + 1024));
+  return sms * std::max(1, std::min(2048 / P.NT, by_smem));
+}
+size_t ws_bytes_for(const GPlan &P, int sms) {
+  return P.gring ? (size_t)grid_cap(P, sms) * P.npred * P.RING * 8 : 0;
+}
 
 stl_status get_kernel(const FkFormula &f, bool bwd, int NT, int tile_req, int max_smem, GPlan &P,
                       std::shared_ptr<Compiled> &out, std::string *err, std::string *src_out, bool load) {
   std::string why;
-  const int want = tile_req > 0 ? tile_req : default_tile(bwd, NT);
-  if (!fit_tile(f, bwd, NT, want, max_smem, P, &why)) {
+  if (!choose_plan(f, bwd, NT, tile_req, max_smem, P, &why)) {
     *err = why;
     return STL_ERR_UNSUPPORTED;
   }
@@ -885,7 +961,7 @@ stl_status device_limits(std::string *err) {
 }  // namespace
 
 stl_status stl_fk_plan_shape(const FkFormula &f, bool bwd, int threads, int tile, int *tile_out, int *smem_out,
-                             std::string *err) {
+                             size_t *ws_out, std::string *err) {
   const int NT = threads ? threads : 512;
   if (NT != 256 && NT != 512) { *err = "threads must be 256 or 512"; return STL_ERR_INVALID_ARG; }
   int max_smem = 232448;
@@ -895,12 +971,20 @@ stl_status stl_fk_plan_shape(const FkFormula &f, bool bwd, int threads, int tile
   }
   GPlan P;
   std::string why;
-  if (!fit_tile(f, bwd, NT, tile > 0 ? tile : default_tile(bwd, NT), max_smem - 1024, P, &why)) {
+  if (!choose_plan(f, bwd, NT, tile, max_smem - 1024, P, &why)) {
     *err = why;
     return STL_ERR_UNSUPPORTED;
   }
   if (tile_out) *tile_out = P.TILE;
   if (smem_out) *smem_out = P.smem;
+  if (ws_out) {
+    int sms = 152;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    *ws_out = ws_bytes_for(P, sms);
+  }
   return STL_OK;
 }
 
@@ -961,13 +1045,21 @@ stl_status stl_fk_run(const FkFormula &f, const FkCall &c, std::string *err) {
     seg = (T + segs - 2) / (segs - 1);   // one segment fewer
   }
   const long long n_items = B * segs;
-  const int grid = (int)std::max(1LL, std::min(n_items, slots));
+  const int grid = (int)std::max(1LL, std::min(n_items, std::min(slots, (long long)grid_cap(P, g_sms))));
+  if (P.gring) {
+    const size_t need = (size_t)grid * P.npred * P.RING * 8;
+    if (!c.ws || c.ws_bytes < need) {
+      *err = fmt("workspace of %zu bytes needed (adjoint rings)", need);
+      return STL_ERR_WORKSPACE;
+    }
+  }
+  void *ws = c.ws;
   int Ti = (int)T, segi = (int)seg, segsi = (int)segs;
   long long items = n_items;
   const float *sig = c.sig, *gout = c.gout;
   float *out = c.out, *gsig = c.gsig;
-  void *args[] = {(void *)&sig, (void *)&gout, (void *)&out, (void *)&gsig, (void *)&Ti, (void *)&segi, (void *)&segsi,
-                  (void *)&items};
+  void *args[] = {(void *)&sig, (void *)&gout, (void *)&out, (void *)&gsig, (void *)&ws, (void *)&Ti, (void *)&segi,
+                  (void *)&segsi, (void *)&items};
   e = cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, (size_t)P.smem, (cudaStream_t)c.stream);
   if (e != cudaSuccess) { *err = std::string("compiled kernel launch: ") + cudaGetErrorString(e); return STL_ERR_CUDA; }
   return STL_OK;

@@ -29,6 +29,8 @@ struct FkCall {
   float *out = nullptr;          // robustness [B, T] (forward; optional in backward launches)
   float *gsig = nullptr;         // backward: signal gradient [B, T, D]
   int threads = 0, tile = 0, segment = 0;   // 0: automatic
+  void *ws = nullptr;            // workspace (backward with adjoint rings in L2)
+  size_t ws_bytes = 0;
   void *stream = nullptr;
 };
 
@@ -36,9 +38,10 @@ struct FkCall {
 // failure returns a status and sets *err.
 stl_status stl_fk_run(const FkFormula &f, const FkCall &c, std::string *err);
 
-// The tile and shared memory the compiled kernel of this shape would use (no code generation).
+// The tile, shared memory and workspace bytes the compiled kernel of this shape would use (no
+// code generation).
 stl_status stl_fk_plan_shape(const FkFormula &f, bool bwd, int threads, int tile, int *tile_out, int *smem_out,
-                             std::string *err);
+                             size_t *ws_out, std::string *err);
 
 // Plan and compile without launching (no GPU needed): the launch shape the call would use and,
 // if src is non-NULL, the generated source.

@@ -193,25 +193,130 @@ __device__ __forceinline__ void fk_window(int q0, int q1, const Elem &elem, cons
 #pragma unroll
           for (int i = 2; i <= NF; ++i) mid = M::comb(mid, ra[tid + i]);
         }
+        // ma = middle (+) the trailing prefix of output u+k, extended by one sample per output
         const int gs = u + IA + (NF + 1) * R;
-        T acc;
-        if constexpr (RHO > 0) {
-          acc = elem(gs);
+        T ma = mid;
 #pragma unroll
-          for (int e = 1; e < RHO; ++e) acc = M::comb(acc, elem(gs + e));
-        }
+        for (int e = 0; e < RHO; ++e) ma = M::comb(ma, elem(gs + e));
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-          if (k > 0 || RHO > 0) {
-            if (u + k < q1) out(u + k, M::comb(M::comb(hv[k], mid), acc));
+          if (u + k < q1) out(u + k, M::comb(hv[k], ma));
+          if (k + 1 < R) ma = M::comb(ma, elem(gs + RHO + k));
+        }
+      }
+      if (p0 + NT * R < q1) __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------------ hard Until in one pass
+// rho_q = min(A_q, X_q): A_q = min of phi over [q, q+IA] (MA, with its sample in backward
+// launches), X_q = the clamp composition over offsets [IA, IB] (MC).  A thread's outputs
+// u..u+R-1 take A from a sliding minimum over its own phi samples u..u+R+IA-1 held in
+// registers (van Herk blocks of W = IA+1: suffix within the block of q, prefix within the
+// next), so A needs no pass, buffer or barrier of its own.  out(q, X, A).
+template <class M, int R, int W>
+__device__ __forceinline__ void fk_slide_regs(const typename M::T (&e)[R + W - 1], typename M::T (&a)[R]) {
+  typedef typename M::T T;
+  constexpr int N = R + W - 1;
+  T suf[N], pre[N];
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) suf[i] = (i % W == W - 1 || i == N - 1) ? e[i] : M::comb(e[i], suf[i + 1]);
+#pragma unroll
+  for (int i = 0; i < N; ++i) pre[i] = (i % W == 0) ? e[i] : M::comb(pre[i - 1], e[i]);
+#pragma unroll
+  for (int k = 0; k < R; ++k) a[k] = (k % W == 0) ? suf[k] : M::comb(suf[k], pre[k + W - 1]);
+}
+
+template <class MC, class MA, int NT, int R, int IA, int IB, class ElemC, class ElemA, class Out>
+__device__ __forceinline__ void fk_until(int q0, int q1, const ElemC &elemc, const ElemA &elema, const Out &out,
+                                         void *scratch) {
+  typedef typename MC::T T;
+  typedef typename MA::T TA;
+  constexpr int K = IB - IA + 1;
+  constexpr int W = IA + 1;
+  const int tid = threadIdx.x;
+  if (q1 <= q0) return;
+  if constexpr (K < 2 * R) {
+    for (int q = q0 + tid; q < q1; q += NT) {
+      TA a = elema(q);
+#pragma unroll
+      for (int i = 1; i <= IA; ++i) a = MA::comb(a, elema(q + i));
+      T acc = elemc(q + IA);
+#pragma unroll
+      for (int i = IA + 1; i <= IB; ++i) acc = MC::comb(acc, elemc(q + i));
+      out(q, acc, a);
+    }
+  } else {
+    constexpr int NF = K / R - 1;
+    constexpr int RHO = K - (NF + 1) * R;
+    constexpr int L2 = 8;
+    constexpr bool TWO = NF >= 3 * L2;
+    T *ra = reinterpret_cast<T *>(scratch);
+    T *a2 = ra + NT + NF + 8;
+    for (int p0 = q0; p0 < q1; p0 += NT * R) {
+      const int u = p0 + tid * R;
+      const int nv = min(NT, (q1 - p0 + R - 1) / R);
+      const int nr = nv + NF;
+      T hv[R];
+      if (tid < nr) {
+        hv[R - 1] = elemc(u + IA + R - 1);
+#pragma unroll
+        for (int k = R - 2; k >= 0; --k) hv[k] = MC::comb(elemc(u + IA + k), hv[k + 1]);
+        ra[tid] = hv[0];
+      }
+      for (int e = NT + tid; e < nr; e += NT) {
+        const int s = p0 + IA + e * R;
+        T acc = elemc(s);
+#pragma unroll
+        for (int k = 1; k < R; ++k) acc = MC::comb(acc, elemc(s + k));
+        ra[e] = acc;
+      }
+      __syncthreads();
+      if constexpr (TWO) {
+        for (int m = tid; (m + 1) * L2 <= nr; m += NT) {
+          T acc = ra[m * L2];
+#pragma unroll
+          for (int k = 1; k < L2; ++k) acc = MC::comb(acc, ra[m * L2 + k]);
+          a2[m] = acc;
+        }
+        __syncthreads();
+      }
+      if (tid < nv) {
+        TA av[R];
+        {
+          TA ev[R + IA];
+#pragma unroll
+          for (int i = 0; i < R + IA; ++i) ev[i] = elema(u + i);
+          fk_slide_regs<MA, R, W>(ev, av);
+        }
+        T mid;
+        if constexpr (TWO) {
+          const int l = tid + 1, r = tid + NF;
+          const int ml = (l + L2 - 1) / L2, mr = (r + 1) / L2 - 1;
+          int j = l;
+          if (j < ml * L2) {
+            mid = ra[j++];
+            for (; j < ml * L2; ++j) mid = MC::comb(mid, ra[j]);
+            mid = MC::comb(mid, a2[ml]);
           } else {
-            if (u + k < q1) out(u + k, M::comb(hv[k], mid));
+            mid = a2[ml];
           }
-          if (k + 1 < R) {
-            const T e = elem(gs + RHO + k);
-            if (k == 0 && RHO == 0) acc = e;
-            else acc = M::comb(acc, e);
-          }
+          for (int m = ml + 1; m <= mr; ++m) mid = MC::comb(mid, a2[m]);
+          for (j = (mr + 1) * L2; j <= r; ++j) mid = MC::comb(mid, ra[j]);
+        } else {
+          mid = ra[tid + 1];
+#pragma unroll
+          for (int i = 2; i <= NF; ++i) mid = MC::comb(mid, ra[tid + i]);
+        }
+        const int gs = u + IA + (NF + 1) * R;
+        T ma = mid;
+#pragma unroll
+        for (int e = 0; e < RHO; ++e) ma = MC::comb(ma, elemc(gs + e));
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          if (u + k < q1) out(u + k, MC::comb(hv[k], ma), av[k]);
+          if (k + 1 < R) ma = MC::comb(ma, elemc(gs + RHO + k));
         }
       }
       if (p0 + NT * R < q1) __syncthreads();
