@@ -753,15 +753,14 @@ constexpr int kPipeSlots = 3;   // chunk k: copies in, kernels, copies out on sl
 stl_status staging_layout(const stl_program *h, long long chunk, long long T, const stl_params &p, bool bwd,
                           Staging &L) {
   const size_t c = (size_t)chunk, t = (size_t)T, D = (size_t)h->D, S = (size_t)h->n_slots;
-  size_t ws = 0;
-  Plan pl;
-  stl_status e = make_plan(h, chunk, T, p, false, pl);
+  // workspace of whichever kernel serves a chunk (interpreter or formula-compiled)
+  size_t ws = 0, wb = 0;
+  stl_status e = stl_workspace_size(const_cast<stl_program *>(h), chunk, T, &p, 0, &ws);
   if (e) return e;
-  ws = pl.ws_bytes;
   if (bwd) {
-    e = make_plan(h, chunk, T, p, true, pl);
+    e = stl_workspace_size(const_cast<stl_program *>(h), chunk, T, &p, 1, &wb);
     if (e) return e;
-    ws = std::max(ws, pl.ws_bytes);
+    ws = std::max(ws, wb);
   }
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off += align256(bytes); return o; };

@@ -684,6 +684,14 @@ struct Gen {
       l("        }");
       l("      }");
     }
+    if (P.npred > 0) {
+      // the signal rows the next step's predicate pass reads, fetched into L2 in the background
+      l("      if (tid == 0 && t1 < s1) {");
+      l(fmt("        const long long r0 = min((long long)t1 + %d, (long long)T), r1 = min((long long)t1 + %d, (long long)T);",
+            P.HP, P.TILE + P.HP));
+      l(fmt("        fk_prefetch_l2(xs + r0 * %d, xs + r1 * %d, sig, sig + (long long)T * %d * (b + 1));", D, D, D));
+      l("      }");
+    }
     s += "      // ---- node passes\n";
     pred_pass();
     for (int i = 0; i < P.n; ++i) node_pass(i);
@@ -705,11 +713,16 @@ struct Gen {
       else
         l(fmt("          else fk_red_add(fj + ck * %d + (cp - (t0 + %d)), acc);", P.capA, P.LP));
       l("        };");
+      // the root gradients of the thread's samples, loaded together (the trace was kept in L2
+      // by the scale pre-pass; this is its last use)
+      l(fmt("        float gq[%d];", RW));
+      l("#pragma unroll");
+      l(fmt("        for (int r = 0; r < %d; ++r) gq[r] = qa + r < qb ? fk_ldg_first(grow + qa + r, pol_first) : 0.f;", RW));
       l("#pragma unroll");
       l(fmt("        for (int r = 0; r < %d; ++r) {", RW));
       l("          const int q = qa + r;");
       l("          if (q >= qb) break;");
-      l("          float g = fk_ldg_first(grow + q, pol_first);");
+      l("          float g = gq[r];");
       l("          int pos = q, leaf = -1;");
       walk(P.root, 10);
       l("          if (leaf >= 0) {");
@@ -728,24 +741,37 @@ struct Gen {
       l(fmt("        if (first && s0 < j0) for (int i = s0 * %d + tid; i < min(j0, T - 1) * %d; i += NT) gs[i] = 0.f;", D,
             D));
       if (P.npred > 0) {
-        l("        for (int j = j0 + tid; j < j1; j += NT) {");
-        l(fmt("          const int ja = j - (t0 + %d);", P.LP));
+        // EB samples per thread per iteration: their adjoint loads are issued together
+        const int EB = P.gring ? 4 : 2;
+        l(fmt("        for (int jb = j0 + tid; jb < j1; jb += NT * %d) {", EB));
+        l(fmt("          fk_u64 av[%d][%d];", EB, P.npred));
+        l("#pragma unroll");
+        l(fmt("          for (int e = 0; e < %d; ++e) {", EB));
+        l("            const int j = jb + e * NT;");
         if (P.gring) {
           // L2 reads: the deposits of other threads are atomics performed at L2
-          l(fmt("          const int js = (j - %d) & %d;", P.LP, P.RING - 1));
+          l(fmt("            const int js = (j - %d) & %d;", P.LP, P.RING - 1));
           for (int k = 0; k < P.npred; ++k)
-            l(fmt("          const float a%d = fk_from_fix(fx, __ldcg(fj + %d + js));", k, k * P.RING));
+            l(fmt("            av[e][%d] = j < j1 ? __ldcg(fj + %d + js) : 0ull;", k, k * P.RING));
         } else {
-          for (int k = 0; k < P.npred; ++k) l(fmt("          const float a%d = fk_from_fix(fx, fj[%d + ja]);", k, k * P.capA));
+          l(fmt("            const int ja = j - (t0 + %d);", P.LP));
+          for (int k = 0; k < P.npred; ++k) l(fmt("            av[e][%d] = j < j1 ? fj[%d + ja] : 0ull;", k, k * P.capA));
         }
+        l("          }");
+        l("#pragma unroll");
+        l(fmt("          for (int e = 0; e < %d; ++e) {", EB));
+        l("            const int j = jb + e * NT;");
+        l("            if (j >= j1) break;");
+        for (int k = 0; k < P.npred; ++k) l(fmt("            const float a%d = fk_from_fix(fx, av[e][%d]);", k, k));
         for (int d = 0; d < D; ++d) {
-          l("          {");
-          l("            float acc = 0.f;");
+          l("            {");
+          l("              float acc = 0.f;");
           for (int k = 0; k < P.npred; ++k)
-            l(fmt("            acc = fmaf(%s, a%d, acc);", flit(P.pw[(size_t)k * D + d]).c_str(), k));
-          l(fmt("            gs[(long long)j * %d + %d] = acc;", D, d));
-          l("          }");
+            l(fmt("              acc = fmaf(%s, a%d, acc);", flit(P.pw[(size_t)k * D + d]).c_str(), k));
+          l(fmt("              gs[(long long)j * %d + %d] = acc;", D, d));
+          l("            }");
         }
+        l("          }");
         l("        }");
       } else {
         l(fmt("        for (int i = j0 * %d + tid; i < j1 * %d; i += NT) gs[i] = 0.f;", D, D));

@@ -416,6 +416,21 @@ __device__ __forceinline__ float fk_trace_gmax(const float *g, int T) {
   return m;
 }
 
+// Asynchronous L2 prefetch of the 16-byte aligned part of [p0, p1), kept inside [lo, hi) (the
+// allocation); one thread issues it.
+__device__ __forceinline__ void fk_prefetch_l2(const float *p0, const float *p1, const float *lo, const float *hi) {
+  unsigned long long a = reinterpret_cast<unsigned long long>(p0), e = reinterpret_cast<unsigned long long>(p1);
+  const unsigned long long l = (reinterpret_cast<unsigned long long>(lo) + 15) & ~15ull;
+  const unsigned long long h = reinterpret_cast<unsigned long long>(hi) & ~15ull;
+  a = (a + 15) & ~15ull;
+  e &= ~15ull;
+  if (a < l) a = l;
+  if (e > h) e = h;
+  if (e <= a) return;
+  const unsigned n = (unsigned)min(e - a, 1ull << 20);
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
+}
+
 __device__ __forceinline__ float fk_ldg_first(const float *p, fk_u64 pol) {
   float v;
   asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
