@@ -565,8 +565,9 @@ stl_status fk_launch(const stl_program *h, bool bwd, long long B, long long T, c
 
 stl_status stl_set_launch(stl_handle h, const stl_launch *launch) {
   if (!h || !launch) return fail(STL_ERR_INVALID_ARG, "NULL argument");
-  if (launch->threads && launch->threads != 64 && launch->threads != 256 && launch->threads != 512)
-    return fail(STL_ERR_INVALID_ARG, "threads must be 0, 64, 256 or 512");
+  if (launch->threads && launch->threads != 64 && launch->threads != 256 && launch->threads != 512 &&
+      !(launch->kernel == STL_KERNEL_COMPILED && (launch->threads == 768 || launch->threads == 1024)))
+    return fail(STL_ERR_INVALID_ARG, "threads must be 0, 64, 256 or 512 (compiled kernels: 256, 512, 768, 1024)");
   if (launch->tile < 0 || (launch->tile && launch->tile % 32) || launch->segment < 0)
     return fail(STL_ERR_INVALID_ARG, "tile must be a non-negative multiple of 32; segment >= 0");
   if (launch->kernel < STL_KERNEL_AUTO || launch->kernel > STL_KERNEL_COMPILED)

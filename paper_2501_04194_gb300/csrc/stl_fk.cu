@@ -321,16 +321,18 @@ struct Gen {
     l("  {  // predicates (Sec. III-B): float32, left-to-right sums, no contraction");
     l(fmt("    const int base = t0 + %d;", P.LP));
     l(fmt("    const int F = min(first ? base : t0 + %d, T), E = min(t1 + %d, T);", P.HP, P.HP));
-    l("    for (int j0 = F + tid; j0 < E; j0 += NT * 4) {");
-    l(fmt("      float x[4][%d];", D));
+    // PB samples per thread per iteration: their loads are in flight together
+    const int PB = D <= 4 ? 8 : 4;
+    l(fmt("    for (int j0 = F + tid; j0 < E; j0 += NT * %d) {", PB));
+    l(fmt("      float x[%d][%d];", PB, D));
     l("#pragma unroll");
-    l("      for (int u = 0; u < 4; ++u) {");
+    l(fmt("      for (int u = 0; u < %d; ++u) {", PB));
     l("        const int j = j0 + u * NT;");
     l("#pragma unroll");
     l(fmt("        for (int d = 0; d < %d; ++d) x[u][d] = j < E ? __ldg(xs + (long long)j * %d + d) : 0.f;", D, D));
     l("      }");
     l("#pragma unroll");
-    l("      for (int u = 0; u < 4; ++u) {");
+    l(fmt("      for (int u = 0; u < %d; ++u) {", PB));
     l("        const int j = j0 + u * NT;");
     l("        if (j >= E) continue;");
     l("        float s;");
@@ -718,18 +720,27 @@ struct Gen {
       l(fmt("        float gq[%d];", RW));
       l("#pragma unroll");
       l(fmt("        for (int r = 0; r < %d; ++r) gq[r] = qa + r < qb ? fk_ldg_first(grow + qa + r, pol_first) : 0.f;", RW));
+      // first every sample's walk (independent: their loads overlap), then the runs of equal
+      // targets and their deposits
+      l(fmt("        int wl[%d], wp[%d];", RW, RW));
       l("#pragma unroll");
       l(fmt("        for (int r = 0; r < %d; ++r) {", RW));
       l("          const int q = qa + r;");
-      l("          if (q >= qb) break;");
       l("          float g = gq[r];");
       l("          int pos = q, leaf = -1;");
-      walk(P.root, 10);
-      l("          if (leaf >= 0) {");
-      l("            const fk_i64 v = fk_to_fix(fx, g);");
-      l("            if (leaf == ck && pos == cp) acc += v;");
-      l("            else { flush(); ck = leaf; cp = pos; acc = v; }");
+      l("          if (q < qb) {");
+      walk(P.root, 12);
       l("          }");
+      l("          wl[r] = leaf;");
+      l("          wp[r] = pos;");
+      l("          gq[r] = g;");
+      l("        }");
+      l("#pragma unroll");
+      l(fmt("        for (int r = 0; r < %d; ++r) {", RW));
+      l("          if (wl[r] < 0) continue;");
+      l("          const fk_i64 v = fk_to_fix(fx, gq[r]);");
+      l("          if (wl[r] == ck && wp[r] == cp) acc += v;");
+      l("          else { flush(); ck = wl[r]; cp = wp[r]; acc = v; }");
       l("        }");
       l("        flush();");
       l("      }");
@@ -989,7 +1000,7 @@ stl_status device_limits(std::string *err) {
 stl_status stl_fk_plan_shape(const FkFormula &f, bool bwd, int threads, int tile, int *tile_out, int *smem_out,
                              size_t *ws_out, std::string *err) {
   const int NT = threads ? threads : 512;
-  if (NT != 256 && NT != 512) { *err = "threads must be 256 or 512"; return STL_ERR_INVALID_ARG; }
+  if (NT != 256 && NT != 512 && NT != 768 && NT != 1024) { *err = "threads must be 256, 512, 768 or 1024"; return STL_ERR_INVALID_ARG; }
   int max_smem = 232448;
   if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0) != cudaSuccess) {
     cudaGetLastError();
@@ -1018,7 +1029,7 @@ stl_status stl_fk_compile_only(const FkFormula &f, bool bwd, long long T, int th
                                int *smem_out, std::string *src, std::string *err) {
   (void)T;
   const int NT = threads ? threads : 512;
-  if (NT != 256 && NT != 512) { *err = "threads must be 256 or 512"; return STL_ERR_INVALID_ARG; }
+  if (NT != 256 && NT != 512 && NT != 768 && NT != 1024) { *err = "threads must be 256, 512, 768 or 1024"; return STL_ERR_INVALID_ARG; }
   GPlan P;
   std::shared_ptr<Compiled> c;
   stl_status s = get_kernel(f, bwd, NT, tile, 232448 - 1024, P, c, err, src, false);
@@ -1037,7 +1048,10 @@ stl_status stl_fk_run(const FkFormula &f, const FkCall &c, std::string *err) {
   stl_status s = device_limits(err);
   if (s) return s;
   const int NT = c.threads ? c.threads : 512;
-  if (NT != 256 && NT != 512) { *err = "threads must be 256 or 512 for the compiled kernels"; return STL_ERR_INVALID_ARG; }
+  if (NT != 256 && NT != 512 && NT != 768 && NT != 1024) {
+    *err = "threads must be 256, 512, 768 or 1024 for the compiled kernels";
+    return STL_ERR_INVALID_ARG;
+  }
   GPlan P;
   std::shared_ptr<Compiled> k;
   s = get_kernel(f, c.bwd, NT, c.tile, g_smem_optin - 1024, P, k, err, nullptr, true);
