@@ -31,6 +31,8 @@
 
 #include "stl_fk.h"
 
+int stl_status_ptr(int **ptr);   // the library's sticky device status word (stl_kernels.cu)
+
 namespace {
 
 // Untils whose phi prefix [0, a] has at most this many samples take it from registers in the
@@ -138,6 +140,7 @@ struct GPlan {
   int capA = 0;            // predicate adjoint ring length (samples)
   int off_j = -1;          // adjoint rings (u64), predicate k at off_j + 8 * k * capA
   bool gring = false;      // backward: adjoint rings in the workspace (L2) instead of shared memory
+  bool check = false;      // bounds-checked build (STL_FK_CHECK=1)
   int RING = 0;            // their length: a power of two >= TILE + HP - LP, indexed by (j - LP) mod RING
   int off_cells = 0, off_scr = 0, smem = 0;
   std::vector<GNode> g;
@@ -165,6 +168,10 @@ bool build_plan(const FkFormula &f, bool bwd, int NT, int TILE, GPlan &P, std::s
   const int n = (int)nd.size();
   P = GPlan{};
   P.bwd = bwd;
+  {
+    const char *e = std::getenv("STL_FK_CHECK");
+    P.check = e && *e && std::strcmp(e, "0") != 0;
+  }
   P.D = f.D;
   P.NT = NT;
   P.TILE = TILE;
@@ -371,12 +378,12 @@ struct Gen {
     const GNode &x = P.g[i];
     const GNode &par = P.g[x.parent];
     if (par.padc) {
-      l(fmt("    fk_fill<NT>(fv%d, max(T - base, 0), %d, %s);", i, x.cap, flit(par.padv).c_str()));
+      l(fmt("    fk_fill<NT>(FK_PTR(fv%d), max(T - base, 0), %d, %s);", i, x.cap, flit(par.padv).c_str()));
     } else {
       l("    {");
       l(fmt("      const float pv = inb ? fv%d[T - 1 - base] : fk_vcell[%d];", i, i));
       l(fmt("      if (inb && tid == 0) fk_vcell[%d] = pv;", i));
-      l(fmt("      fk_fill<NT>(fv%d, max(T - base, 0), %d, pv);", i, x.cap));
+      l(fmt("      fk_fill<NT>(FK_PTR(fv%d), max(T - base, 0), %d, pv);", i, x.cap));
       l("    }");
     }
   }
@@ -413,14 +420,14 @@ struct Gen {
       case STL_OP_ALWAYS: {
         const bool mx = x.op == STL_OP_EVENTUALLY;
         l(fmt("    const int cb = %s;", cb(x.c0).c_str()));
-        l(fmt("    float *const o = fv%d;", i));
-        l(fmt("    const float *const xc = fv%d;", x.c0));
+        l(fmt("    const auto o = fv%d;", i));
+        l(fmt("    const auto xc = fv%d;", x.c0));
         if (!bwd) {
           l(fmt("    fk_window<%s, NT, %d, %d, %d>(F, E, [&](int j) { return xc[j - cb]; },", mx ? "FkMax" : "FkMin", x.R,
                 x.a, x.b));
           l("        [&](int q, float v) { o[q - base] = v; }, fk_scr);");
         } else {
-          l(fmt("    fk_u16 *const oa = fa%d;", i));
+          l(fmt("    const auto oa = fa%d;", i));
           l(fmt("    fk_window<%s, NT, %d, %d, %d>(F, E, [&](int j) { FkVP r; r.v = xc[j - cb]; r.p = j; return r; },",
                 mx ? "FkMaxP" : "FkMinP", x.R, x.a, x.b));
           l("        [&](int q, FkVP r) { o[q - base] = r.v; oa[q - base] = (fk_u16)(r.p - q); }, fk_scr);");
@@ -429,9 +436,9 @@ struct Gen {
       }
       case STL_OP_UNTIL: {
         l(fmt("    const int cp = %s, cq = %s;", cb(x.c0).c_str(), cb(x.c1).c_str()));
-        l(fmt("    float *const o = fv%d;", i));
-        l(fmt("    const float *const xp = fv%d;", x.c0));
-        l(fmt("    const float *const xq = fv%d;", x.c1));
+        l(fmt("    const auto o = fv%d;", i));
+        l(fmt("    const auto xp = fv%d;", x.c0));
+        l(fmt("    const auto xq = fv%d;", x.c1));
         if (x.a + 1 <= FK_UNTIL_FUSE_W) {
           // one pass: the phi prefix minimum over [q, q+a] comes from the thread's registers
           if (!bwd) {
@@ -440,7 +447,7 @@ struct Gen {
             l("        [&](int j) { return xp[j - cp]; },");
             l("        [&](int q, FkC2 r, float a) { o[q - base] = (a <= r.c) ? a : r.c; }, fk_scr);");
           } else {
-            l(fmt("    fk_u16 *const oa = fa%d;", i));
+            l(fmt("    const auto oa = fa%d;", i));
             l(fmt("    fk_until<FkClampP, FkMinP, NT, %d, %d, %d>(F, E, [&](int j) {", x.R, x.a, x.b));
             l("          const float p = xp[j - cp], s = xq[j - cq]; const bool pl = p <= s; FkCC r;");
             l("          r.c = pl ? p : s; r.cs = pl ? 2 * j : 2 * j + 1; r.d = p; r.ds = 2 * j; return r; },");
@@ -459,7 +466,7 @@ struct Gen {
           l("          const float p = xp[j - cp], s = xq[j - cq]; FkC2 r; r.c = fminf(p, s); r.d = p; return r; },");
           l("        [&](int q, FkC2 r) { const float a = o[q - base]; if (!(a <= r.c)) o[q - base] = r.c; }, fk_scr);");
         } else {
-          l(fmt("    fk_u16 *const oa = fa%d;", i));
+          l(fmt("    const auto oa = fa%d;", i));
           l(fmt("    fk_window<FkMinP, NT, %d, 0, %d>(F, E, [&](int j) { FkVP r; r.v = xp[j - cp]; r.p = j; return r; },",
                 x.R1, x.a));
           l("        [&](int q, FkVP r) { o[q - base] = r.v; oa[q - base] = (fk_u16)(2 * (r.p - q)); }, fk_scr);");
@@ -507,12 +514,12 @@ struct Gen {
       const GNode &x = P.g[i];
       const int span = x.hi - x.lo;
       if (span <= 0) continue;
-      if (x.has_val) mv.push_back({fmt("fv%d", i), P.TILE, span});
-      if (x.has_aux) mv.push_back({fmt("reinterpret_cast<float *>(fa%d)", i), P.TILE / 2, (span + 1) / 2});
+      if (x.has_val) mv.push_back({fmt("FK_PTR(fv%d)", i), P.TILE, span});
+      if (x.has_aux) mv.push_back({fmt("reinterpret_cast<float *>(FK_PTR(fa%d))", i), P.TILE / 2, (span + 1) / 2});
     }
     if (P.bwd && !P.gring && P.npred > 0 && P.HP - P.LP > 0)
       for (int k = 0; k < P.npred; ++k)
-        mv.push_back({fmt("reinterpret_cast<float *>(fj + %d)", k * P.capA), 2 * P.TILE, 2 * (P.HP - P.LP)});
+        mv.push_back({fmt("reinterpret_cast<float *>(FK_PTR(fj) + %d)", k * P.capA), 2 * P.TILE, 2 * (P.HP - P.LP)});
     int rounds = 0;
     for (auto &m : mv) rounds = std::max(rounds, (m.len + m.src - 1) / m.src);
     for (int r = 0; r < rounds; ++r) {
@@ -529,7 +536,7 @@ struct Gen {
       // new samples of the predicate adjoint rings start at zero
       const int keep = 2 * (P.HP - P.LP);
       for (int k = 0; k < P.npred; ++k)
-        l(fmt("    fk_zero<NT>(reinterpret_cast<float *>(fj + %d), %d, %d);", k * P.capA, keep, 2 * P.capA));
+        l(fmt("    fk_zero<NT>(reinterpret_cast<float *>(FK_PTR(fj) + %d), %d, %d);", k * P.capA, keep, 2 * P.capA));
       l("    __syncthreads();");
     }
   }
@@ -606,7 +613,7 @@ struct Gen {
       l("      const bool inb = T - 1 >= base;");
       l(fmt("      const fk_u16 av = inb ? fa%d[T - 1 - base] : (fk_u16)fk_acell[%d];", i, i));
       l(fmt("      if (inb && tid == 0) fk_acell[%d] = av;", i));
-      l(fmt("      fk_fill16<NT>(fa%d, max(T - base, 0), %d, av);", i, x.cap));
+      l(fmt("      fk_fill16<NT>(FK_PTR(fa%d), max(T - base, 0), %d, av);", i, x.cap));
       l("    }");
     }
     l("    __syncthreads();");
@@ -617,27 +624,33 @@ struct Gen {
     const int D = P.D, NT = P.NT, TILE = P.TILE;
     s.clear();
     l(fmt("// generated: formula of %d nodes, %s, %d threads, tile %d", P.n, P.bwd ? "backward" : "forward", NT, TILE));
+    l(fmt("#define FK_CHECK %d", P.check ? 1 : 0));
     l(k_dev_src);
     l(fmt("#define NT %d", NT));
     l(fmt("extern \"C\" __global__ void __launch_bounds__(%d, 1) %s(", NT, name.c_str()));
     l("    const float *__restrict__ sig, const float *__restrict__ gout, float *__restrict__ out,");
-    l("    float *__restrict__ gsig, fk_u64 *__restrict__ ws, int T, int seg, int segs, long long n_items) {");
+    l("    float *__restrict__ gsig, fk_u64 *__restrict__ ws, int *__restrict__ fk_status, int T, int seg, int segs,");
+    l("    long long n_items) {");
     l("  extern __shared__ float4 fk_sm4[];");
     l("  char *const fk_sm = reinterpret_cast<char *>(fk_sm4);");
     for (int i = 0; i < P.n; ++i) {
       const GNode &x = P.g[i];
-      if (x.has_val) l(fmt("  float *const fv%d = reinterpret_cast<float *>(fk_sm + %d);", i, x.off_v));
-      if (x.has_aux) l(fmt("  fk_u16 *const fa%d = reinterpret_cast<fk_u16 *>(fk_sm + %d);", i, x.off_a));
+      if (x.has_val)
+        l(fmt("  FK_BUF(float) fv%d = FK_MAKE(float, fk_sm + %d, %d, %d);", i, x.off_v, x.cap, i));
+      if (x.has_aux)
+        l(fmt("  FK_BUF(fk_u16) fa%d = FK_MAKE(fk_u16, fk_sm + %d, %d, %d);", i, x.off_a, x.cap, 100 + i));
     }
-    if (P.bwd && P.npred > 0 && !P.gring) l(fmt("  fk_u64 *const fj = reinterpret_cast<fk_u64 *>(fk_sm + %d);", P.off_j));
-    if (P.bwd && P.npred > 0 && P.gring)
-      l(fmt("  fk_u64 *const fj = ws + (long long)blockIdx.x * %d;   // this CTA's adjoint rings", P.npred * P.RING));
+    if (P.bwd && P.npred > 0 && !P.gring)
+      l(fmt("  FK_BUF(fk_u64) fj = FK_MAKE(fk_u64, fk_sm + %d, %d, 200);", P.off_j, P.capA * P.npred));
+    if (P.bwd && P.npred > 0 && P.gring)   // this CTA's adjoint rings
+      l(fmt("  FK_BUF(fk_u64) fj = FK_MAKE(fk_u64, ws + (long long)blockIdx.x * %d, %d, 201);", P.npred * P.RING,
+            P.npred * P.RING));
     l(fmt("  float *const fk_vcell = reinterpret_cast<float *>(fk_sm + %d);", P.off_cells));
     l(fmt("  int *const fk_acell = reinterpret_cast<int *>(fk_sm + %d);", P.off_cells + 4 * P.n));
     l(fmt("  fk_u64 *const fk_jcell = reinterpret_cast<fk_u64 *>(fk_sm + %d);", P.off_cells + 8 * P.n));
     l(fmt("  void *const fk_scr = fk_sm + %d;", P.off_scr));
     l("  const int tid = threadIdx.x;");
-    l("  (void)fk_vcell; (void)fk_acell; (void)fk_jcell; (void)gout; (void)gsig; (void)out; (void)ws;");
+    l("  (void)fk_vcell; (void)fk_acell; (void)fk_jcell; (void)gout; (void)gsig; (void)out; (void)ws; (void)fk_status;");
     if (P.bwd) {
       l("  __shared__ unsigned s_gmax;");
       l("  fk_u64 pol_first;");
@@ -659,8 +672,8 @@ struct Gen {
       // fixed-point scale from the largest root gradient of the whole trace
       l("    if (tid == 0) s_gmax = 0u;");
       if (P.npred > 0) {
-        if (P.gring) l(fmt("    for (int i = tid; i < %d; i += NT) __stcg(fj + i, 0ull);", P.npred * P.RING));
-        else l(fmt("    fk_zero<NT>(reinterpret_cast<float *>(fj), 0, %d);", 2 * P.capA * P.npred));
+        if (P.gring) l(fmt("    for (int i = tid; i < %d; i += NT) __stcg(&fj[i], 0ull);", P.npred * P.RING));
+        else l(fmt("    fk_zero<NT>(reinterpret_cast<float *>(FK_PTR(fj)), 0, %d);", 2 * P.capA * P.npred));
         l(fmt("    if (tid < %d) fk_jcell[tid] = 0ull;", P.npred));
       }
       l("    __syncthreads();");
@@ -682,7 +695,7 @@ struct Gen {
       l("      if (!first) {");
       l(fmt("        for (int j = t0 + %d + tid; j < t1 + %d; j += NT) {", P.HP, P.HP));
       l(fmt("          const int js = (j - %d) & %d;", P.LP, P.RING - 1));
-      for (int k = 0; k < P.npred; ++k) l(fmt("          __stcg(fj + %d + js, 0ull);", k * P.RING));
+      for (int k = 0; k < P.npred; ++k) l(fmt("          __stcg(&fj[%d + js], 0ull);", k * P.RING));
       l("        }");
       l("      }");
     }
@@ -711,9 +724,9 @@ struct Gen {
       l("          if (ck < 0 || acc == 0) return;");
       l(fmt("          if (cp >= T - 1) fk_red_add(fk_jcell + ck, acc);"));
       if (P.gring)
-        l(fmt("          else atomicAdd(fj + ck * %d + ((cp - %d) & %d), (fk_u64)acc);", P.RING, P.LP, P.RING - 1));
+        l(fmt("          else atomicAdd(&fj[ck * %d + ((cp - %d) & %d)], (fk_u64)acc);", P.RING, P.LP, P.RING - 1));
       else
-        l(fmt("          else fk_red_add(fj + ck * %d + (cp - (t0 + %d)), acc);", P.capA, P.LP));
+        l(fmt("          else fk_red_add(&fj[ck * %d + (cp - (t0 + %d))], acc);", P.capA, P.LP));
       l("        };");
       // the root gradients of the thread's samples, loaded together (the trace was kept in L2
       // by the scale pre-pass; this is its last use)
@@ -763,7 +776,7 @@ struct Gen {
           // L2 reads: the deposits of other threads are atomics performed at L2
           l(fmt("            const int js = (j - %d) & %d;", P.LP, P.RING - 1));
           for (int k = 0; k < P.npred; ++k)
-            l(fmt("            av[e][%d] = j < j1 ? __ldcg(fj + %d + js) : 0ull;", k, k * P.RING));
+            l(fmt("            av[e][%d] = j < j1 ? __ldcg(&fj[%d + js]) : 0ull;", k, k * P.RING));
         } else {
           l(fmt("            const int ja = j - (t0 + %d);", P.LP));
           for (int k = 0; k < P.npred; ++k) l(fmt("            av[e][%d] = j < j1 ? fj[%d + ja] : 0ull;", k, k * P.capA));
@@ -1094,12 +1107,14 @@ stl_status stl_fk_run(const FkFormula &f, const FkCall &c, std::string *err) {
     }
   }
   void *ws = c.ws;
+  int *status = nullptr;
+  if (stl_status_ptr(&status) != 0) { cudaGetLastError(); status = nullptr; }
   int Ti = (int)T, segi = (int)seg, segsi = (int)segs;
   long long items = n_items;
   const float *sig = c.sig, *gout = c.gout;
   float *out = c.out, *gsig = c.gsig;
-  void *args[] = {(void *)&sig, (void *)&gout, (void *)&out, (void *)&gsig, (void *)&ws, (void *)&Ti, (void *)&segi,
-                  (void *)&segsi, (void *)&items};
+  void *args[] = {(void *)&sig, (void *)&gout, (void *)&out, (void *)&gsig, (void *)&ws, (void *)&status, (void *)&Ti,
+                  (void *)&segi, (void *)&segsi, (void *)&items};
   e = cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, (size_t)P.smem, (cudaStream_t)c.stream);
   if (e != cudaSuccess) { *err = std::string("compiled kernel launch: ") + cudaGetErrorString(e); return STL_ERR_CUDA; }
   return STL_OK;

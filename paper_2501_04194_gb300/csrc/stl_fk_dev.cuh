@@ -31,6 +31,32 @@ typedef unsigned short fk_u16;
 
 #define FK_FULL 0xffffffffu
 
+// Buffers.  In the bounds-checked build (FK_CHECK 1) every shared-memory buffer is a view that
+// compares each index with the buffer's length; an index outside it is not performed (the
+// access goes to element 0) and sets the library's device status word to -6
+// (STL_ERR_DEVICE_CHECK).  The normal build uses plain pointers.
+template <class T> struct FkChk {
+  T *p;
+  int cap, id;
+  int *st;
+  __device__ __forceinline__ T &operator[](int i) const {
+    if ((unsigned)i >= (unsigned)cap) {
+      if (st) atomicExch(st, -6);
+      return p[0];
+    }
+    return p[i];
+  }
+};
+#if FK_CHECK
+#define FK_BUF(T) const FkChk<T>
+#define FK_MAKE(T, ptr, cap, id) FkChk<T>{reinterpret_cast<T *>(ptr), (cap), (id), fk_status}
+#define FK_PTR(b) ((b).p)
+#else
+#define FK_BUF(T) T *const
+#define FK_MAKE(T, ptr, cap, id) reinterpret_cast<T *>(ptr)
+#define FK_PTR(b) (b)
+#endif
+
 __device__ __forceinline__ float fk_inf() { return __int_as_float(0x7f800000); }
 
 // ------------------------------------------------------------------ combine monoids

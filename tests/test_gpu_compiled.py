@@ -205,3 +205,27 @@ def test_not_applicable_is_an_error(stl):
     check(stl, W.Eventually(10, 20, W.gt([1], 0.0)), W.random_walk(2, 11, 1, seed=1))   # T = a + 1
     with pytest.raises(stl.StlError):   # smooth semantics run in the interpreter only
         stl.robustness(f, torch.zeros((2, 500, 1), device="cuda"), p=stl.params("smooth", tau=2.0))
+
+
+def test_bounds_checked_build(stl, monkeypatch):
+    """STL_FK_CHECK=1 generates the kernels with every shared-memory index compared against the
+    length of its buffer (an index outside is not performed and sets the device status word to
+    STL_ERR_DEVICE_CHECK): a stand-in for compute-sanitizer, which is closed on this machine.  The
+    shapes of the parity tests, both adjoint-ring placements and both pad kinds run clean and
+    give the same results as the unchecked kernels."""
+    from paper_2501_04194_gb300.binding import device_status
+    monkeypatch.setenv("STL_FK_CHECK", "1")
+    device_status()
+    sig1 = W.config1_inputs(B=3, T=3001, seed=4)
+    for launch in ({}, dict(tile=512, segment=900), dict(threads=256, tile=768), dict(threads=256, tile=1024)):
+        check(stl, W.config1_formula(), sig1, launch=launch, fused=True)
+    for name, tree, D, T in EDGE:
+        check(stl, tree, W.random_walk(3, T, D, seed=5), launch=dict(tile=512, segment=300), fused=True)
+    rng = np.random.default_rng(3)
+    ties = rng.integers(-2, 3, size=(3, 3000, 2)).astype(np.float32)
+    for K in (6, 30, 401):
+        check(stl, W.Until(K - 1, 2 * K + 20, W.gt([1, 0], -1.0), W.gt([0, 1], 0.0)), ties, launch=dict(tile=2048))
+        check(stl, W.Eventually(1, K, W.gt([1, 0], 0.0)), ties, launch=dict(tile=1024))
+    check(stl, W.config1_formula(), W.config1_inputs(B=4, T=50000, seed=2), oracle_traces=[0])
+    torch.cuda.synchronize()
+    assert device_status() == 0
