@@ -1203,7 +1203,7 @@ stl_status stl_autotune(stl_handle h, const float *sig, int64_t B, int64_t T, co
     std::string why;
     if (stl_fk_eligible(fk_formula(h), *p, T, &why) && stl_fk_available(&why))
       for (int nt : {512, 256})
-        for (int mult : bwd ? std::vector<int>{13, 10, 7} : std::vector<int>{15, 11, 7}) {
+        for (int mult : bwd ? std::vector<int>{11, 9, 7} : std::vector<int>{15, 11, 7}) {
           stl_launch l{};
           l.threads = nt;
           l.tile = nt * mult;

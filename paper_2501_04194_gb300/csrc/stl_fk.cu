@@ -245,7 +245,7 @@ bool build_plan(const FkFormula &f, bool bwd, int NT, int TILE, GPlan &P, std::s
     if (x.op == STL_OP_EVENTUALLY || x.op == STL_OP_ALWAYS) x.R = pick_r(x.b - x.a + 1, rcap);
     if (x.op == STL_OP_UNTIL) {
       x.R1 = pick_r(x.a + 1, rcap);
-      x.R = pick_r(x.b - x.a + 1, bwd ? std::min(rcap, 7) : rcap);
+      x.R = pick_r(x.b - x.a + 1, rcap);
     }
     maxR = std::max(maxR, std::max(x.R, x.R1));
   }
@@ -893,13 +893,15 @@ bool fit_tile(const FkFormula &f, bool bwd, int NT, int want, int max_smem, GPla
   return false;
 }
 
-int default_tile(bool bwd, int NT) { return bwd ? NT * 10 : NT * 15; }
+// one window pass per step (tile = threads x run length); backward runs of 9 measured best
+// (config 1 at B=1024 T=50000: runs of 7 / 9 / 11 at 512 threads, 1.59 / 1.53 / 1.67 ms)
+int default_tile(bool bwd, int NT) { return bwd ? NT * 9 : NT * 15; }
 
 // The plan of one call shape.  Backward launches keep their 64-bit predicate adjoint rings in
 // shared memory when the requested tile fits with them, else in the caller's workspace (L2:
 // global 64-bit reductions, L2-only reads), which leaves shared memory to the node buffers: for
-// the nested formula of config 1 this allows a tile of 5120 instead of 3072 (measured backward
-// at B=1024, T=50000: 2.18 -> 1.60 ms).
+// the nested formula of config 1 this allows a tile of 4608 instead of 3072 (measured backward
+// at B=1024, T=50000: 2.18 -> 1.53 ms).
 bool choose_plan(const FkFormula &f, bool bwd, int NT, int tile_req, int max_smem, GPlan &P, std::string *why) {
   const int want = tile_req > 0 ? tile_req : default_tile(bwd, NT);
   if (!fit_tile(f, bwd, NT, want, max_smem, P, why, false)) return false;
