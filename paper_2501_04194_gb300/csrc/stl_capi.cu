@@ -532,10 +532,16 @@ stl_status resolve_kernel(const stl_program *h, long long B, long long T, const 
     *kind = want;
     return STL_OK;
   }
-  // automatic: the compiled kernel unless a launch shape for the interpreter was set
+  // automatic: the compiled kernel unless a launch shape for the interpreter was set, or its
+  // buffers would not fit in shared memory even at the smallest tile
   const stl_launch &l = h->launch_dir[bwd ? 1 : 0];
   const bool shape_set = l.tile || l.threads || l.segment;
-  *kind = (ok && !shape_set && B * T >= (1LL << 20)) ? STL_KERNEL_COMPILED : STL_KERNEL_INTERPRETER;
+  bool use = ok && !shape_set && B * T >= (1LL << 20);
+  if (use) {
+    std::string err;
+    use = stl_fk_plan_shape(fk_formula(h), bwd, 0, 0, nullptr, nullptr, nullptr, &err) == STL_OK;
+  }
+  *kind = use ? STL_KERNEL_COMPILED : STL_KERNEL_INTERPRETER;
   return STL_OK;
 }
 

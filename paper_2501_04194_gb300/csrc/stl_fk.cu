@@ -130,6 +130,8 @@ struct GNode {
   int cap = 0;             // buffer length in samples (slack included)
   int off_v = -1, off_a = -1;
   int R = 3, R1 = 3;       // run lengths: window / Until pass 2, Until pass 1
+  int level = 0;           // 0 for leaves, 1 + the largest level of the children
+  int off_s = -1;          // this node's window scratch (run aggregates)
 };
 
 struct GPlan {
@@ -276,10 +278,12 @@ bool build_plan(const FkFormula &f, bool bwd, int NT, int TILE, GPlan &P, std::s
   }
   // cells: value and aux at T-1 per node, adjoint of sample T-1 per predicate
   P.off_cells = take(4LL * n + 4LL * n + 8LL * std::max(1, P.npred));
-  int scr = 64;
+  // every window node has scratch of its own (run aggregates, then level-2 blocks: sliding for
+  // max / min, aligned for the clamps), so that nodes of one level run without a barrier
+  // between them
   for (int i = 0; i < n; ++i) {
-    const GNode &x = P.g[i];
-    // run aggregates, then level-2 blocks (sliding for max / min, aligned for the clamps)
+    GNode &x = P.g[i];
+    int scr = 0;
     auto need = [&](int K, int R, int eb, bool idem) {
       if (K < 2 * R) return;
       const int NF = K / R - 1;
@@ -292,8 +296,14 @@ bool build_plan(const FkFormula &f, bool bwd, int NT, int TILE, GPlan &P, std::s
       if (x.a + 1 > FK_UNTIL_FUSE_W) need(x.a + 1, x.R1, elem_bytes(x.op, bwd, false), true);
       need(x.b - x.a + 1, x.R, elem_bytes(x.op, bwd, true), false);
     }
+    if (scr > 0) x.off_s = take(scr);
   }
-  P.off_scr = take(scr);
+  P.off_scr = take(64);
+  for (int i = 0; i < n; ++i) {
+    GNode &x = P.g[i];
+    const int l0 = x.c0 >= 0 ? P.g[x.c0].level : -1, l1 = x.c1 >= 0 ? P.g[x.c1].level : -1;
+    x.level = (x.c0 < 0 && x.c1 < 0) ? 0 : 1 + std::max(l0, l1);
+  }
   P.smem = off;
   P.pw.assign((size_t)P.npred * P.D, 0.f);
   for (int k = 0; k < P.npred; ++k) {
@@ -388,12 +398,15 @@ struct Gen {
     }
   }
 
-  void node_pass(int i) {
+  // node i's pass; `barrier`: synchronise after it (the next pass reads it); without, the
+  // next pass belongs to the same level and reads neither this node nor its scratch
+  void node_pass(int i, bool barrier) {
     const GNode &x = P.g[i];
     const bool bwd = P.bwd;
     if (is_pred(x.op)) return;
     if (i == P.root && !x.has_val) return;   // elementwise root: written by the output / walk
-    l(fmt("  {  // node %d", i));
+    l(fmt("  {  // node %d (level %d)", i, x.level));
+    if (x.off_s >= 0) l(fmt("    void *const fk_scr = fk_sm + %d;", x.off_s));
     range(i);
     auto cb = [&](int c) { return fmt("t0 + %d", P.g[c].lo); };
     switch (x.op) {
@@ -483,9 +496,10 @@ struct Gen {
         break;
     }
     l("  }");
-    l("  __syncthreads();");
+    if (barrier) l("  __syncthreads();");
     if (x.tparent) {
       l(fmt("  if (t1 + %d >= T) {", x.hi));
+      if (!barrier) l("    __syncthreads();");
       l(fmt("    const int base = t0 + %d;", x.lo));
       l("    const bool inb = T - 1 >= base;");
       pad_fill_body(i);
@@ -709,21 +723,34 @@ struct Gen {
     }
     s += "      // ---- node passes\n";
     pred_pass();
-    for (int i = 0; i < P.n; ++i) node_pass(i);
+    {
+      // level by level (a node reads only lower levels); a barrier only where the level changes
+      std::vector<int> order;
+      for (int i = 0; i < P.n; ++i)
+        if (!is_pred(P.g[i].op) && !(i == P.root && !P.g[i].has_val)) order.push_back(i);
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P.g[a].level < P.g[b].level; });
+      for (size_t k = 0; k < order.size(); ++k) {
+        const bool last = k + 1 == order.size();
+        node_pass(order[k], last || P.g[order[k + 1]].level != P.g[order[k]].level);
+      }
+    }
     if (!P.bwd) {
       l("      for (int q = t0 + tid; q < t1; q += NT) orow[q] = " + root_value() + ";");
     } else {
       aux_pad_fills();
       // walk: a thread takes consecutive root samples, so that runs of equal targets add once
       const int RW = (TILE + NT - 1) / NT;
-      l("      {  // selection walk and fixed-point deposits");
+      if (P.npred > 0) l("      {  // selection walk and fixed-point deposits");
+      else l("      if (false) {  // no predicate: no gradient reaches the signal");
       l(fmt("        const int qa = t0 + tid * %d, qb = min(qa + %d, t1);", RW, RW));
       l("        int ck = -1, cp = 0;");
       l("        fk_i64 acc = 0;");
       l("        auto flush = [&]() {");
       l("          if (ck < 0 || acc == 0) return;");
       l(fmt("          if (cp >= T - 1) fk_red_add(fk_jcell + ck, acc);"));
-      if (P.gring)
+      if (P.npred == 0)
+        ;
+      else if (P.gring)
         l(fmt("          else atomicAdd(&fj[ck * %d + ((cp - %d) & %d)], (fk_u64)acc);", P.RING, P.LP, P.RING - 1));
       else
         l(fmt("          else fk_red_add(&fj[ck * %d + (cp - (t0 + %d))], acc);", P.capA, P.LP));
@@ -790,8 +817,11 @@ struct Gen {
         for (int d = 0; d < D; ++d) {
           l("            {");
           l("              float acc = 0.f;");
+          // a zero weight adds a zero to a finite sum (acc starts at +0): skipping it leaves the
+          // result's bits unchanged
           for (int k = 0; k < P.npred; ++k)
-            l(fmt("              acc = fmaf(%s, a%d, acc);", flit(P.pw[(size_t)k * D + d]).c_str(), k));
+            if (P.pw[(size_t)k * D + d] != 0.f)
+              l(fmt("              acc = fmaf(%s, a%d, acc);", flit(P.pw[(size_t)k * D + d]).c_str(), k));
           l(fmt("              gs[(long long)j * %d + %d] = acc;", D, d));
           l("            }");
         }
@@ -904,12 +934,15 @@ int default_tile(bool bwd, int NT) { return bwd ? NT * 9 : NT * 15; }
 // at B=1024, T=50000: 2.18 -> 1.53 ms).
 bool choose_plan(const FkFormula &f, bool bwd, int NT, int tile_req, int max_smem, GPlan &P, std::string *why) {
   const int want = tile_req > 0 ? tile_req : default_tile(bwd, NT);
-  if (!fit_tile(f, bwd, NT, want, max_smem, P, why, false)) return false;
-  if (!bwd || P.TILE >= want || P.npred == 0) return true;
+  const bool shared_ok = fit_tile(f, bwd, NT, want, max_smem, P, why, false);
+  if (!bwd || P.npred == 0 || (shared_ok && P.TILE >= want)) return shared_ok;
   GPlan G;
   std::string w2;
-  if (fit_tile(f, bwd, NT, want, max_smem, G, &w2, true) && G.TILE > P.TILE) P = G;
-  return true;
+  if (fit_tile(f, bwd, NT, want, max_smem, G, &w2, true) && (!shared_ok || G.TILE > P.TILE)) {
+    P = G;
+    return true;
+  }
+  return shared_ok;
 }
 
 // CTAs that can be resident at once (an upper bound on the grid) for this plan

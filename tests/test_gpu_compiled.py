@@ -124,6 +124,10 @@ EDGE = [
                                                                 pad=0.3)), 2, 260),
     ("windows_past_end", W.And(W.Eventually(500, 900, W.gt([1, 0], 0.0), pad=-0.5),
                                W.Always(3, 12, W.lt([0, 1], 1.0))), 2, 700),
+    ("T1", W.Or(W.Always(0, 40, W.gt([1, 0], 0.0)), W.Until(0, 9, W.gt([0, 1], 0.1), W.lt([1, 1], 0.0))), 2, 1),
+    ("true_root", W.true(), 1, 90),
+    ("not_true_or", W.Or(W.Not(W.true()), W.Eventually(0, 30, W.gt([1], 0.2))), 1, 120),
+    ("D7", W.Until(2, 50, W.gt([1, -1, 0, 0.5, 0, 0, 2], 0.1), W.lt([0, 0, 1, 1, 1, -1, 0], 0.3)), 7, 400),
 ]
 
 
@@ -131,6 +135,24 @@ EDGE = [
 @pytest.mark.parametrize("launch", [dict(tile=512), dict(threads=256, tile=512, segment=300)])
 def test_degenerate(stl, name, tree, D, T, launch):
     check(stl, tree, W.random_walk(3, T, D, seed=5), launch=launch, fused=True)
+
+
+def test_long_interval_shrinks_the_tile(stl):
+    """Spans of 12,000 samples: the tile shrinks until the buffers fit in shared memory."""
+    tree = W.And(W.Eventually(0, 12000, W.gt([1, 0], 0.3)), W.Always(100, 4000, W.lt([0, 1], 0.5)))
+    check(stl, tree, W.random_walk(2, 30000, 2, seed=8), oracle_traces=[1])
+
+
+def test_automatic_choice_falls_back_when_buffers_do_not_fit(stl):
+    """Nested windows whose spans add to 45,000 samples fit no compiled tile: the automatic
+    choice runs the interpreter (and the call succeeds)."""
+    tree = W.Eventually(0, 15000, W.Always(0, 15000, W.Eventually(0, 15000, W.gt([1], 0.0))))
+    p = stl.params("hard")
+    f = stl.Formula(tree, D=1)
+    assert f.get_launch(64, 60000, p, False)["kernel"] == "interpreter"
+    x = torch.from_numpy(W.random_walk(2, 1000, 1, seed=3)).cuda().repeat(32, 40, 1)
+    rho = stl.robustness(f, x, p=p)
+    assert rho.shape == (64, 40000)
 
 
 def test_ties_follow_the_oracle(stl):
