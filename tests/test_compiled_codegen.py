@@ -66,3 +66,14 @@ def test_outside_the_compiled_set_is_refused(stl, tree, D):
     f = stl.Formula(tree, D=D, n_slots=1)
     with pytest.raises(stl.StlError):
         f.compile_kernel(backward=False)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_formulas_compile(stl, seed):
+    """Seed-generated formulas of depth 4 (static intervals, Not nodes, constant pads)."""
+    import numpy as np
+    tree = W.static_random_formula(np.random.default_rng(200 + seed), 3, 4, 300)
+    f = stl.Formula(tree, D=3)
+    for backward in (False, True):
+        tile, smem = f.compile_kernel(backward=backward, T=20000)
+        assert tile >= 512 and smem <= 227 * 1024

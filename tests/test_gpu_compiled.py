@@ -251,3 +251,14 @@ def test_bounds_checked_build(stl, monkeypatch):
     check(stl, W.config1_formula(), W.config1_inputs(B=4, T=50000, seed=2), oracle_traces=[0])
     torch.cuda.synchronize()
     assert device_status() == 0
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_random_formulas(stl, seed):
+    """Seed-generated formulas of depth <= 4 (static intervals up to 300, Not nodes, constant
+    pads), several tiles and a ragged tail: compiled == interpreter bit for bit, and the oracle."""
+    rng = np.random.default_rng(200 + seed)
+    tree = W.static_random_formula(rng, 3, 3 + seed % 2, 300)
+    T = int(rng.integers(1500, 4000))
+    launch = dict(tile=512) if seed % 3 == 0 else dict(threads=256, tile=1024, segment=T // 2) if seed % 3 == 1 else {}
+    check(stl, tree, W.random_walk(3, T, 3, seed=seed), launch=launch, fused=seed % 2 == 0)

@@ -220,6 +220,36 @@ def random_formula(rng, D, depth, slot_counter, b_cap):
     return build(depth)
 
 
+def static_random_formula(rng, D, depth, b_cap, not_prob=0.15, const_pad_prob=0.2):
+    """A seed-generated formula of operator depth <= ``depth`` like ``random_formula``, but with
+    static integer intervals 0 <= a <= b <= ``b_cap`` drawn per temporal node, occasional Not
+    nodes and occasional constant pads (the shapes the formula-compiled kernels serve)."""
+    def pred():
+        w = onehot(D, int(rng.integers(D))) if rng.random() < 0.5 else \
+            [float(rng.choice([-1.0, 1.0])) if rng.random() < 0.6 else 0.0 for _ in range(D)]
+        if all(v == 0.0 for v in w):
+            w[int(rng.integers(D))] = 1.0
+        c = float(np.float32(rng.normal()))
+        return gt(w, c) if rng.random() < 0.5 else lt(w, c)
+
+    def build(d):
+        if d == 0:
+            f = pred()
+        else:
+            op = str(rng.choice(["and", "or", "always", "eventually", "until"], p=[0.15, 0.15, 0.25, 0.25, 0.2]))
+            if op in ("and", "or"):
+                f = (op, build(d - 1), build(int(rng.integers(0, d))))
+            else:
+                a = int(rng.integers(0, b_cap // 3 + 1))
+                b = a + int(rng.integers(0, b_cap - a + 1))
+                pad = float(np.float32(rng.normal())) if rng.random() < const_pad_prob else None
+                iv = interval(a, b, None, pad)
+                f = ("until", iv, build(d - 1), build(int(rng.integers(0, d)))) if op == "until" else (op, iv, build(d - 1))
+        return Not(f) if rng.random() < not_prob else f
+
+    return build(depth)
+
+
 def config3_workload(n_traces=10000, t_lo=50, t_hi=20000, D=4, n_formulas=16, max_depth=4, seed=0):
     """Ragged batch: lengths ~ U[t_lo, t_hi], random-walk signals packed as [sum T, D],
     16 seed-generated formulas (seed+1) and per-trace integer bounds a < b ~ U[0, 0.2 T_b]."""
