@@ -65,6 +65,8 @@ def recorded_traffic(kernel, B, T, launch=None):
         e = d.get(kernel)
         if not e or e.get("source_sha") != kernel_source_sha():
             return None
+        # (entries taken with one launch shape are valid for that shape only; entries without one
+        # hold a per-trace-step figure that does not depend on it)
         if launch and "tile" in e and (launch.get("tile"), launch.get("threads")) != (e["tile"], e["threads"]):
             return None
         # captured on a smaller case: scale by trace-steps

@@ -686,7 +686,13 @@ struct Gen {
       // fixed-point scale from the largest root gradient of the whole trace
       l("    if (tid == 0) s_gmax = 0u;");
       if (P.npred > 0) {
-        if (P.gring) l(fmt("    for (int i = tid; i < %d; i += NT) __stcg(&fj[i], 0ull);", P.npred * P.RING));
+        if (P.gring) {
+          // the first step's slots; later steps clear their new slots as they become live
+          l(fmt("    for (int j = R0 + %d + tid; j < min(R0 + %d, s1) + %d; j += NT) {", P.LP, P.TILE, P.HP));
+          l(fmt("      const int js = (j - %d) & %d;", P.LP, P.RING - 1));
+          for (int k = 0; k < P.npred; ++k) l(fmt("      __stcg(&fj[%d + js], 0ull);", k * P.RING));
+          l("    }");
+        }
         else l(fmt("    fk_zero<NT>(reinterpret_cast<float *>(FK_PTR(fj)), 0, %d);", 2 * P.capA * P.npred));
         l(fmt("    if (tid < %d) fk_jcell[tid] = 0ull;", P.npred));
       }
