@@ -123,7 +123,13 @@ typedef struct {
  *                           and gradients are bit-identical to the interpreter's.  Needs no
  *                           workspace and sets no device status.
  *   STL_KERNEL_AUTO         the compiled kernel where it applies, B*T >= 2^20 samples and
- *                           tile, threads and segment are all 0; else the interpreter. */
+ *                           tile, threads and segment are all 0; else the interpreter.
+ * Environment (read when a compiled kernel is generated): STL_FK_CHECK=1 generates it with
+ * every shared-memory index compared with its buffer's length (an index outside is not
+ * performed and sets the device status word to STL_ERR_DEVICE_CHECK; slower, for testing);
+ * STL_FK_DUMP=<directory> writes each generated source there.  A compiled backward whose 64-bit
+ * adjoint rings would not fit in shared memory beside the node buffers keeps them in the
+ * workspace (stl_workspace_size reports the bytes); the compiled forward needs none. */
 typedef enum { STL_KERNEL_AUTO = 0, STL_KERNEL_INTERPRETER = 1, STL_KERNEL_COMPILED = 2 } stl_kernel;
 
 /* Launch shape.  Zero fields mean "choose automatically" (the autotuner's cached choice if
