@@ -3,8 +3,8 @@
 //
 // The interpreter (stl_interp.cuh) reads the compiled program at run time, so every window
 // length, buffer offset and loop bound is a register value and every child read goes through
-// an index clamp; measured on the headline formula, about 400 instructions per sample and
-// direction, nearly all integer bookkeeping.  Here the program becomes source code: one
+// an index clamp; measured on the nested Until/Always/Eventually formula, about 400
+// instructions per sample and direction, nearly all integer bookkeeping.  Here the program becomes source code: one
 // __global__ function per (formula, direction, CTA size, tile) whose node passes are
 // instantiations of the templates in stl_fk_dev.cuh with compile-time constants, a walk of
 // the selections unrolled over the tree, and literal predicate weights.  NVRTC compiles it for
@@ -930,13 +930,14 @@ bool fit_tile(const FkFormula &f, bool bwd, int NT, int want, int max_smem, GPla
 }
 
 // one window pass per step (tile = threads x run length); backward runs of 9 measured best
-// (config 1 at B=1024 T=50000: runs of 7 / 9 / 11 at 512 threads, 1.59 / 1.53 / 1.67 ms)
+// (the nested Until/Always/Eventually formula at B=1024 T=50000: runs of 7 / 9 / 11 at 512
+// threads, 1.59 / 1.53 / 1.67 ms)
 int default_tile(bool bwd, int NT) { return bwd ? NT * 9 : NT * 15; }
 
 // The plan of one call shape.  Backward launches keep their 64-bit predicate adjoint rings in
 // shared memory when the requested tile fits with them, else in the caller's workspace (L2:
 // global 64-bit reductions, L2-only reads), which leaves shared memory to the node buffers: for
-// the nested formula of config 1 this allows a tile of 4608 instead of 3072 (measured backward
+// the nested Until/Always/Eventually formula this allows a tile of 4608 instead of 3072 (backward
 // at B=1024, T=50000: 2.18 -> 1.53 ms).
 bool choose_plan(const FkFormula &f, bool bwd, int NT, int tile_req, int max_smem, GPlan &P, std::string *why) {
   const int want = tile_req > 0 ? tile_req : default_tile(bwd, NT);
