@@ -77,3 +77,25 @@ def test_random_formulas_compile(stl, seed):
     for backward in (False, True):
         tile, smem = f.compile_kernel(backward=backward, T=20000)
         assert tile >= 512 and smem <= 227 * 1024
+
+
+def test_kernel_choice_and_launch_validation(stl):
+    """Host logic of the kernel selector: the automatic choice takes the compiled kernel for a
+    large hard call with static intervals and no explicit shape; launch shapes are validated
+    before anything runs (768 / 1024 threads only for the compiled kernels, 64 never)."""
+    p = stl.params("hard")
+    f = stl.Formula(W.config1_formula(), D=3)
+    assert f.get_launch(1024, 50000, p, False)["kernel"] == "compiled"
+    assert f.get_launch(1024, 50000, p, True)["kernel"] == "compiled"
+    for kernel, threads in (("compiled", 64), ("interpreter", 768), ("auto", 1024)):
+        with pytest.raises(stl.StlError):
+            f.set_launch(kernel=kernel, threads=threads)
+    f.set_launch(kernel="compiled", threads=768, tile=768 * 7)
+    assert f.get_launch(1024, 50000, p, False) == dict(tile=768 * 7, threads=768, segment=0, kernel="compiled")
+    with pytest.raises(stl.StlError):
+        f.set_launch(kernel=5)
+    # a forced compiled launch of a formula outside the compiled set fails on the host
+    g = stl.Formula(W.Eventually(0, 10, W.gt([1], 0.0), slot=0), D=1, n_slots=1)
+    g.set_launch(kernel="compiled")
+    with pytest.raises(stl.StlError):
+        g.get_launch(1024, 50000, p, False)
